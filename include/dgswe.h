@@ -1,0 +1,206 @@
+/*
+ * dgswe.h -- C interface of the GB300 (sm_103a) library that advances the rainfall-augmented
+ * 2D shallow water equations with the discontinuous Galerkin method of Wichitrnithed et al.,
+ * "A Discontinuous Galerkin Finite Element Model for Compound Flood Simulations"
+ * (arXiv 2307.14302).
+ *
+ * The calls follow the paper's problem statement (Sec. 2.1, Eq. SWE): find (zeta, q = H u) on a
+ * triangulated domain whose boundary is split into ocean (specified elevation) and land (zero
+ * normal flow) parts, given bathymetry h_b (positive downward), a Manning field, nodal rainfall
+ * (Sec. 2.3, Eq. rain) and tidal boundary data.  The state is advanced by the DG right-hand side
+ * (Eq. elem_weak_form, Eq. RKSSP) and an SSP Runge-Kutta scheme (Sec. 2.2) with the positive-
+ * depth operator of Sec. 2.4 applied after every stage.
+ *
+ * Conventions shared by every entry point
+ *   - Return value: 0 on success, a negative DGSWE_E* code otherwise; dgswe_last_error() then
+ *     holds a message for the calling thread.
+ *   - All input pointers are borrowed for the duration of the call and copied before return
+ *     (host pointers unless the name says _device).  Output pointers are written before return
+ *     (host) or enqueued on the context's stream (device).  Nothing is retained.
+ *   - Units are SI: metres, seconds, m/s for rain (the grid helper alone takes mm/h).
+ *   - Triangles are given counter-clockwise; a clockwise triangle is made counter-clockwise by
+ *     swapping its second and third vertices (modal outputs then refer to that order).
+ *   - Element order in every output is the caller's input order; internal renumbering for L2
+ *     locality is invisible.
+ *   - Modal arrays are [Np][E] per variable (mode-major), Np = (p+1)(p+2)/2, in the orthonormal
+ *     Dubiner basis on the reference triangle (-1,-1),(1,-1),(-1,1) (Eq. dubiner), local
+ *     vertex order as given, modes ordered by total degree then by the second index.
+ *   - Calls on one context must not overlap from several host threads.
+ *   - Call order: create, set_params, set_mesh, set_fields, forcing setters (any order),
+ *     set_state, then step / get_* freely.  Out-of-order calls return DGSWE_ESTATE.
+ */
+#ifndef DGSWE_H
+#define DGSWE_H
+#include <stddef.h>
+#include <stdint.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  DGSWE_OK = 0,
+  DGSWE_EINVAL = -1,     /* bad argument */
+  DGSWE_ENOMEM = -2,     /* device or host allocation failed */
+  DGSWE_ECUDA = -3,      /* a CUDA call failed; message in dgswe_last_error() */
+  DGSWE_ENONFINITE = -4, /* a stage produced a non-finite value (device error word) */
+  DGSWE_ENEGDEPTH = -5,  /* an element mean depth fell below zero (device error word) */
+  DGSWE_ETIMEOUT = -6,   /* a bounded device-side wait ran out */
+  DGSWE_ESTATE = -7,     /* call out of order */
+  DGSWE_ENOLIB = -8      /* the CUDA device or kernel image is unavailable */
+};
+
+enum { DGSWE_FLUX_ROE = 0, DGSWE_FLUX_LLF = 1 };             /* Sec. 2.3 numerical fluxes */
+enum { DGSWE_FP64 = 0, DGSWE_MIXED = 1 };                    /* arithmetic of the device path */
+enum { DGSWE_MANNING = 0, DGSWE_QUADRATIC = 1, DGSWE_NOFRICTION = 2 };
+enum { DGSWE_BT_LAND = 0, DGSWE_BT_OCEAN = 1 };              /* boundary types, Sec. 2.1 */
+enum { DGSWE_LAYOUT_MODAL = 0, DGSWE_LAYOUT_NODAL = 1 };
+
+typedef struct dgswe_ctx* dgswe_h;
+
+/* Run parameters (Sec. 2.2-2.4, Sec. 3).
+ *   p           polynomial degree 0, 1 or 2 (Eq. dubiner);
+ *   flux        DGSWE_FLUX_ROE or DGSWE_FLUX_LLF;
+ *   ssp_stages  1, 2 or 3: SSP(1,1), SSP(2,2), SSP(3,3) in Shu-Osher form (Sec. 2.2);
+ *   precision   DGSWE_FP64 (every operation in double) or DGSWE_MIXED (FP32 bulk; float-float
+ *               element means; FP64 for the depth test near H0 and the global ledger);
+ *   g           gravity [m/s^2];  H0 thin-layer depth threshold [m] (Sec. 2.4);
+ *   cfl, dt     dt > 0 is used as given, otherwise dt = cfl * min_e(2 r_in) / ((2p+1) lambda_e)
+ *               with lambda_e = max over vertices of |u| + sqrt(g max(H, H0)) of the state
+ *               passed to dgswe_set_state (fixed for the run);
+ *   friction    DGSWE_MANNING (tau = g n^2 |u| / H^{4/3}), DGSWE_QUADRATIC (tau = cf |u| / H,
+ *               Sec. 3.1) or none;  cf quadratic coefficient. */
+typedef struct {
+  int32_t p;
+  int32_t flux;
+  int32_t ssp_stages;
+  int32_t precision;
+  double g;
+  double H0;
+  double cfl;
+  double dt;
+  int32_t friction;
+  double cf;
+} dgswe_params;
+
+/* Moving radially symmetric rain cell (stand-in for the parametric model of Sec. 2.5):
+ * centre (x0, y0) + speed * (t - t0) * (cos heading, sin heading); rate at distance r:
+ * rpeak (1/2 + r / (2 rm)) for r < rm, rpeak exp(-(r - rm) / re) beyond.  m, s, rad, m/s. */
+typedef struct {
+  double x0, y0, heading, speed, rpeak, rm, re, t0;
+} dgswe_storm;
+
+/* Gaussian surface set-up eta_p = peak exp(-|x - x0|^2 / (2 sigma^2)) entering the momentum
+ * source as F = g H grad(eta_p) (the F_x, F_y of Eq. SWE). */
+typedef struct {
+  double x0, y0, sigma, peak;
+} dgswe_gauss_setup;
+
+/* Mass ledger (Eq. SWE integrated over the domain):  V = sum_e A_e mean(zeta_e);
+ * rain_in = sum over stages of b_s dt sum_e A_e R_e;  bdry_in = inflow through ocean edges;
+ * rel_err = |V - V0 - rain_in - bdry_in| / VH0 with VH0 the initial water volume. */
+typedef struct {
+  double t;
+  int64_t steps;
+  double V0, V, rain_in, bdry_in, VH0, rel_err, wet_frac;
+} dgswe_ledger;
+
+/* Creates a context on CUDA device `device`; `cuda_stream` is a cudaStream_t (NULL: the legacy
+ * default stream) on which all device work of this context is enqueued.  *out receives the
+ * handle.  Errors: EINVAL (null out), ENOLIB (no device / no kernel image), ECUDA. */
+int dgswe_create(dgswe_h* out, int device, void* cuda_stream);
+
+/* Sets the run parameters (copied).  EINVAL on values outside the ranges above. */
+int dgswe_set_params(dgswe_h, const dgswe_params* params);
+
+/* Sets the triangulation (Sec. 2.1, ADCIRC-style arrays).
+ *   xy [n_nodes][2] float64 coordinates;  tri [n_tri][3] int32 node indices;
+ *   bedge [n_bedge][2] node pairs of boundary edges with btype (DGSWE_BT_*) and bseg (tidal
+ *   segment of ocean edges, 0 <= bseg < n_tide_segments); boundary edges not listed are land.
+ * Builds edge connectivity, renumbers elements and nodes along a space-filling curve and
+ * computes geometry.  EINVAL on out-of-range indices, degenerate triangles, an edge shared by
+ * more than two triangles, or an unknown boundary type. */
+int dgswe_set_mesh(dgswe_h, int32_t n_nodes, const double* xy, int32_t n_tri, const int32_t* tri, int32_t n_bedge,
+                   const int32_t* bedge, const int32_t* btype, const int32_t* bseg);
+
+/* Sets nodal bathymetry hb [n_nodes] (positive downward, m; continuous piecewise linear) and
+ * Manning n, per element [n_tri] (manning_nodal = 0) or per node [n_nodes] (element value = mean
+ * of its nodes).  manning may be NULL when friction is not Manning. */
+int dgswe_set_fields(dgswe_h, const double* hb_nodal, const double* manning, int32_t manning_nodal);
+
+/* Rain sources (Sec. 2.3, Eq. rain): the element rate is the mean of its three nodal rates and
+ * is added to every element, wet or dry.  Each setter replaces the previous rain source. */
+int dgswe_set_rain_nodal(dgswe_h, const double* r_nodal); /* constant in time [n_nodes] m/s */
+int dgswe_set_rain_parametric(dgswe_h, const dgswe_storm* storm);
+/* Gridded records [nt][ny][nx] float32 in mm/h on x0 + i dx, y0 + j dy, times t0 + k dt_rec:
+ * bilinear in space, linear in time, clamped at the grid and record ends (Sec. 2.5). */
+int dgswe_set_rain_grid(dgswe_h, int32_t nx, int32_t ny, int32_t nt, double x0, double y0, double dx, double dy,
+                        double t0, double dt_rec, const float* mm_per_h);
+
+/* Tidal elevation on ocean edges of segment s: amp[s] sin(2 pi t / period[s] + phase[s]). */
+int dgswe_set_tide(dgswe_h, int32_t n_seg, const double* amp, const double* period, const double* phase);
+
+/* Gaussian pressure set-up forcing (F_x, F_y of Eq. SWE); NULL removes it. */
+int dgswe_set_pressure_setup(dgswe_h, const dgswe_gauss_setup* setup);
+
+/* Sets the state at t = t0.  layout MODAL: zeta, qx, qy are [Np][n_tri] modal coefficients;
+ * NODAL: [n_nodes] nodal values, interpolated linearly on each element.  The positive-depth
+ * operator is applied once (it defines the wet/dry flags), the ledger is reset (V0, VH0) and,
+ * when params.dt <= 0, dt is fixed from the CFL condition. */
+int dgswe_set_state(dgswe_h, const double* zeta, const double* qx, const double* qy, int32_t layout, double t0);
+
+/* Enqueues n_steps SSP-RK steps on the context's stream (CUDA graph replay) and returns
+ * without waiting.  Device errors surface in dgswe_sync. */
+int dgswe_step(dgswe_h, int64_t n_steps);
+
+/* Waits for the stream and returns the first device error word (ENONFINITE, ENEGDEPTH) or 0. */
+int dgswe_sync(dgswe_h);
+
+/* The fixed time step [s] in *dt. */
+int dgswe_get_dt(dgswe_h, double* dt);
+
+/* Copies the modal state to host arrays [Np][n_tri] (synchronises the stream). */
+int dgswe_get_state(dgswe_h, double* zeta, double* qx, double* qy);
+
+/* Copies the modal state into caller-owned device memory: each pointer to Np*n_tri doubles,
+ * written on the context's stream (no host round trip). */
+int dgswe_get_state_device(dgswe_h, double* zeta_dev, double* qx_dev, double* qy_dev);
+
+/* Per-element dry flags (Sec. 2.4) [n_tri] as 0/1 bytes. */
+int dgswe_get_dry(dgswe_h, uint8_t* dry);
+
+/* Mass ledger (synchronises the stream). */
+int dgswe_get_ledger(dgswe_h, dgswe_ledger* out);
+
+/* Total water volume sum_e A_e mean(zeta_e) of the current state, reduced on the device in
+ * FP64 with Neumaier compensation over per-block partial sums held in library-allocated scratch
+ * memory; *out receives the value (synchronises the stream). */
+int dgswe_volume(dgswe_h, double* out);
+
+/* Ensemble of independent scenarios (different meshes, forcing, Manning fields) advanced
+ * together: one persistent launch per RK stage, the whole step captured in a CUDA graph.  The
+ * members must share p, flux, ssp_stages, precision, g and H0 and have their state set; their
+ * data is copied (members keep ownership and are not modified).  Each scenario keeps its own
+ * dt and time. */
+int dgswe_ensemble_create(dgswe_h* out, int32_t n, const dgswe_h* members, int device, void* cuda_stream);
+int dgswe_ensemble_step(dgswe_h ens, int64_t n_steps);
+int dgswe_ensemble_get_state(dgswe_h ens, int32_t member, double* zeta, double* qx, double* qy);
+int dgswe_ensemble_get_ledger(dgswe_h ens, int32_t member, dgswe_ledger* out);
+
+/* Launch tuning: block size (64, 128, 256 or 0 = autotune on the next step) and persistent
+ * grid (1: one CTA pass per SM slot with an atomic tile counter, 0: one CTA per tile). */
+int dgswe_set_launch(dgswe_h, int32_t block, int32_t persistent);
+int dgswe_get_launch(dgswe_h, int32_t* block, int32_t* persistent);
+
+/* Number of kernel launches this context enqueued so far (all kinds). */
+int64_t dgswe_launch_count(dgswe_h);
+
+/* Releases the context and its device memory (NULL is ignored). */
+void dgswe_destroy(dgswe_h);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* dgswe_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

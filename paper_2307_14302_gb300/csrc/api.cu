@@ -1,0 +1,1067 @@
+// api.cu -- C interface and host runtime of libdgswe (declarations and contracts: dgswe.h).
+//
+// A context holds one or more scenarios (host copies of preprocessed mesh, fields, forcing and
+// initial state).  At dgswe_set_state (or dgswe_ensemble_create) the scenarios are packed into
+// one device layout: element records, static geometry, connectivity and per-scenario parameter
+// blocks, scenario element ranges aligned to 256 so tiles never straddle two scenarios.  A step
+// is one launch of the fused stage kernel per Runge-Kutta stage; steps are replayed from CUDA
+// graphs (1 step and 8 steps) captured on a private stream and launched on the caller's.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "args.h"
+#include "dgswe.h"
+#include "host.h"
+#include "layout.h"
+
+using namespace dg;
+
+static thread_local std::string g_err;
+
+static int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CU(call)                                                                                 \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess) return fail(DGSWE_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+namespace {
+
+struct Scenario {
+  HostMesh m;
+  std::vector<double> hb;          // nodal bathymetry, new node order
+  std::vector<double> man;         // element Manning n, new element order
+  int rain_kind = 0;               // 0 none, 1 nodal constant, 2 storm, 3 grid
+  std::vector<double> rain_n;      // nodal constant rain, new node order
+  dgswe_storm storm{};
+  int gnx = 0, gny = 0, gnt = 0;
+  double gx0 = 0, gy0 = 0, gdx = 1, gdy = 1, gt0 = 0, gdt = 1;
+  std::vector<float> grid;
+  std::vector<double> tamp, tper, tpha;
+  bool press = false;
+  dgswe_gauss_setup ps{};
+  std::vector<double> w;           // caller's state, modal [ne][3][np], new element order
+  double t0 = 0.0;
+  double dt = 0.0;                 // fixed time step (known after set_state)
+  int level = 0;                   // 1 mesh, 2 fields, 3 state
+};
+
+struct Stage {
+  double a_n, a_in, beta, c, bw;
+};
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t n = 0;
+  ~DevBuf() { if (p) cudaFree(p); }
+  int alloc(size_t bytes) {
+    if (p) { cudaFree(p); p = nullptr; }
+    n = bytes;
+    if (bytes == 0) return 0;
+    return cudaMalloc(&p, bytes) == cudaSuccess ? 0 : -1;
+  }
+  template <class T>
+  T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() { if (prev >= 0) cudaSetDevice(prev); }
+};
+
+}  // namespace
+
+struct dgswe_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;   // caller's stream (launches)
+  cudaStream_t cap = nullptr;      // private stream (graph capture)
+  bool own_stream = false;
+  dgswe_params prm{};
+  bool has_params = false;
+  std::vector<Scenario> sc;
+  bool ensemble = false;
+  // device layout
+  bool ready = false;
+  int np = 0, rv = 0, gv = 0;      // modes, record and geometry sizes (16-byte units)
+  long long E = 0, N = 0;          // padded element count, node count
+  std::vector<long long> eoff, noff;
+  DevBuf rec[3], nbr, geo, nodes, node_xy, xy64, hbn, rain_e, scen, tile_scen, ledger, ctl, eorig, grids, scratch,
+      gather_buf;
+  int ntiles = 0;
+  std::vector<double> led_rain, led_bdry;  // host-folded ledger of retired tilings
+  std::vector<double> V0, VH0;
+  std::vector<Stage> stages;
+  // launch configuration
+  int block = 128, persistent = 0;
+  bool autotune = true;
+  int grid_persistent = 0;
+  cudaGraphExec_t g1 = nullptr, gK = nullptr;
+  int K = 8;
+  long long launches = 0;
+
+  ~dgswe_ctx() {
+    DeviceGuard dg_(device);
+    DevBuf* bufs[] = {&rec[0], &rec[1], &rec[2], &nbr, &geo, &nodes, &node_xy, &xy64, &hbn, &rain_e, &scen,
+                      &tile_scen, &ledger, &ctl, &eorig, &grids, &scratch, &gather_buf};
+    for (DevBuf* b : bufs) b->alloc(0);
+    if (g1) cudaGraphExecDestroy(g1);
+    if (gK) cudaGraphExecDestroy(gK);
+    if (cap) cudaStreamDestroy(cap);
+    if (own_stream && stream) cudaStreamDestroy(stream);
+  }
+};
+
+// ------------------------------------------------------------------------------ helpers --
+// Neumaier-compensated sum of per-block (sum, compensation) pairs, one CTA, fixed order
+__global__ void __launch_bounds__(256) reduce_pairs_kernel(const double* part, int nblk, int npairs, double* out) {
+  __shared__ double sh[2][8];
+  for (int k = 0; k < npairs; ++k) {
+    double s = 0.0, c = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+      const double v = part[4 * b + 2 * k], t = s + v;
+      c += (fabs(s) >= fabs(v)) ? (s - t) + v : (v - t) + s;
+      s = t;
+      c += part[4 * b + 2 * k + 1];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double v = __shfl_xor_sync(0xffffffffu, s, o), vc = __shfl_xor_sync(0xffffffffu, c, o);
+      const double t = s + v;
+      c += ((fabs(s) >= fabs(v)) ? (s - t) + v : (v - t) + s) + vc;
+      s = t;
+    }
+    if ((threadIdx.x & 31) == 0) { sh[0][threadIdx.x >> 5] = s; sh[1][threadIdx.x >> 5] = c; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+        const double v = sh[0][w], t = s + v;
+        c += ((fabs(s) >= fabs(v)) ? (s - t) + v : (v - t) + s) + sh[1][w];
+        s = t;
+      }
+      out[2 * k] = s;
+      out[2 * k + 1] = c;
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t dg::launch_reduce_pairs(const double* partials, int nblk, int npairs, double* out, cudaStream_t s) {
+  reduce_pairs_kernel<<<1, 256, 0, s>>>(partials, nblk, npairs, out);
+  return cudaGetLastError();
+}
+
+static void split_ff(double v, float& hi, float& lo) {
+  hi = (float)v;
+  lo = (float)(v - (double)hi);
+}
+
+static bool mixed(const dgswe_ctx* h) { return h->prm.precision == DGSWE_MIXED; }
+
+static std::vector<Stage> ssp_table(int s) {
+  std::vector<Stage> t;
+  if (s == 2) {
+    t = {{0.0, 1.0, 1.0, 0.0, 0}, {0.5, 0.5, 0.5, 1.0, 0}};
+  } else {
+    t = {{0.0, 1.0, 1.0, 0.0, 0}, {0.75, 0.25, 0.25, 1.0, 0}, {1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, 0.5, 0}};
+  }
+  // weight of dt L(w^(s)) in the final stage: c_{i+1} = a_n c_0 + a_in c_i + beta_i e_i, c_0 = 0
+  const int n = (int)t.size();
+  std::vector<std::vector<double>> c(n + 1, std::vector<double>(n, 0.0));
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < n; ++k) c[i + 1][k] = t[i].a_n * c[0][k] + t[i].a_in * c[i][k] + (k == i ? t[i].beta : 0.0);
+  for (int k = 0; k < n; ++k) t[k].bw = c[n][k];
+  return t;
+}
+
+static int check_handle(dgswe_h h) {
+  if (!h) return fail(DGSWE_EINVAL, "null handle");
+  return 0;
+}
+
+static RefTab<double> g_tabd[3];
+static RefTab<float> g_tabf[3];
+static bool g_tab_built[3] = {false, false, false};
+
+static int upload_all_tables(int p) {
+  if (!g_tab_built[p]) {
+    build_tables(p, g_tabd[p]);
+    tables_to_float(g_tabd[p], g_tabf[p]);
+    g_tab_built[p] = true;
+  }
+  CU(upload_tables<Mixed>(p, g_tabf[p], g_tabd[p]));
+  CU(upload_tables<Fp64>(p, g_tabf[p], g_tabd[p]));
+  return 0;
+}
+
+// --------------------------------------------------------------------- device layout -------
+template <class T>
+static void put(std::vector<uint32_t>& w, size_t at, T v) {
+  std::memcpy(&w[at], &v, sizeof(T));
+}
+
+static int build_layout(dgswe_h h) {
+  DeviceGuard dg_(h->device);
+  const int p = h->prm.p, np = np_of(p);
+  const bool mx = mixed(h);
+  h->np = np;
+  h->rv = mx ? rec_vec_mixed(p) : rec_vec_fp64(p);
+  h->gv = mx ? 3 : 5;
+  const size_t ns = h->sc.size();
+  h->eoff.assign(ns, 0);
+  h->noff.assign(ns, 0);
+  long long E = 0, N = 0;
+  for (size_t s = 0; s < ns; ++s) {
+    h->eoff[s] = E;
+    h->noff[s] = N;
+    E += (h->sc[s].m.ne + TILE_ALIGN - 1) / TILE_ALIGN * TILE_ALIGN;
+    N += h->sc[s].m.nn;
+  }
+  h->E = E;
+  h->N = N;
+  if (upload_all_tables(p)) return DGSWE_ECUDA;
+  const RefTab<double>& tb = g_tabd[p];
+  // host images
+  const size_t rw = 4 * (size_t)h->rv, gw = 4 * (size_t)h->gv;  // 32-bit words per element
+  std::vector<uint32_t> rec(rw * E, 0u), geo(gw * E, 0u);
+  std::vector<int32_t> nbr(4 * E, -1), nodes(4 * E, 0), eorig(E, 0);
+  std::vector<double> xy64(2 * N), hbn(N);
+  std::vector<float> xyf(mx ? 2 * N : 0), rainf(mx ? E : 0);
+  std::vector<double> rain64(mx ? 0 : E);
+  std::vector<float> grids;
+  std::vector<size_t> grid_off(ns, 0);
+  for (size_t s = 0; s < ns; ++s) {
+    const Scenario& S = h->sc[s];
+    const HostMesh& M = S.m;
+    const long long eo = h->eoff[s], no = h->noff[s];
+    for (int i = 0; i < M.nn; ++i) {
+      xy64[2 * (no + i)] = M.x[i];
+      xy64[2 * (no + i) + 1] = M.y[i];
+      hbn[no + i] = S.hb[i];
+      if (mx) { xyf[2 * (no + i)] = (float)M.x[i]; xyf[2 * (no + i) + 1] = (float)M.y[i]; }
+    }
+    if (S.rain_kind == 3) { grid_off[s] = grids.size(); grids.insert(grids.end(), S.grid.begin(), S.grid.end()); }
+    for (int e = 0; e < M.ne; ++e) {
+      const long long ge = eo + e;
+      const int32_t* v = &M.tri[3 * (size_t)e];
+      eorig[ge] = M.eorig[e];
+      for (int j = 0; j < 3; ++j) {
+        const int32_t c = M.code[3 * (size_t)e + j];
+        nbr[4 * ge + j] = c >= 0 ? (int32_t)((((c >> 2) + eo) << 2) | (c & 3)) : c;
+        nodes[4 * ge + j] = (int32_t)(v[j] + no);
+      }
+      const double hv[3] = {S.hb[v[0]], S.hb[v[1]], S.hb[v[2]]};
+      const double hbm = (hv[0] + hv[1] + hv[2]) / 3.0;
+      const double hb1 = tb.vinv[0][0] * hv[0] + tb.vinv[0][1] * hv[1] + tb.vinv[0][2] * hv[2];
+      const double hb2 = tb.vinv[1][0] * hv[0] + tb.vinv[1][1] * hv[1] + tb.vinv[1][2] * hv[2];
+      const double A = M.area[e], invA = 1.0 / A;
+      const double man = S.man.empty() ? 0.0 : S.man[e];
+      double re = 0.0;
+      if (S.rain_kind == 1) re = (S.rain_n[v[0]] + S.rain_n[v[1]] + S.rain_n[v[2]]) / 3.0;
+      // state record
+      const double* w = &S.w[(size_t)e * 3 * np];
+      const double s2 = 1.0 / std::sqrt(2.0);
+      uint32_t* R = &rec[rw * ge];
+      uint32_t* Gm = &geo[gw * ge];
+      const int NS = np - 1;
+      if (mx) {
+        float hi, lo;
+        for (int var = 0; var < 3; ++var) {
+          split_ff(w[var * np] * s2, hi, lo);
+          put(rec, rw * ge + 2 * var, hi);
+          put(rec, rw * ge + 2 * var + 1, lo);
+          for (int m = 0; m < NS; ++m) put(rec, rw * ge + 6 + var * NS + m, (float)w[var * np + m + 1]);
+        }
+        const size_t o = rw * ge + 6 + 3 * NS;
+        put(rec, o + 2, (float)hb1);
+        put(rec, o + 3, (float)hb2);
+        for (int j = 0; j < 3; ++j) {
+          put(geo, gw * ge + 2 * j, (float)M.lnx[3 * (size_t)e + j]);
+          put(geo, gw * ge + 2 * j + 1, (float)M.lny[3 * (size_t)e + j]);
+        }
+        split_ff(hbm, hi, lo); put(geo, gw * ge + 6, hi); put(geo, gw * ge + 7, lo);
+        split_ff(A, hi, lo); put(geo, gw * ge + 8, hi); put(geo, gw * ge + 9, lo);
+        split_ff(invA, hi, lo); put(geo, gw * ge + 10, hi); put(geo, gw * ge + 11, lo);
+        float mf = (float)man;
+        std::memcpy(&nbr[4 * ge + 3], &mf, 4);
+        rainf[ge] = (float)re;
+      } else {
+        for (int var = 0; var < 3; ++var) {
+          put(rec, rw * ge + 2 * var, w[var * np] * s2);
+          for (int m = 0; m < NS; ++m) put(rec, rw * ge + 2 * (3 + var * NS + m), w[var * np + m + 1]);
+        }
+        const size_t o = rw * ge + 2 * (3 + 3 * NS);
+        put(rec, o + 4, hb1);
+        put(rec, o + 6, hb2);
+        for (int j = 0; j < 3; ++j) {
+          put(geo, gw * ge + 4 * j, M.lnx[3 * (size_t)e + j]);
+          put(geo, gw * ge + 4 * j + 2, M.lny[3 * (size_t)e + j]);
+        }
+        put(geo, gw * ge + 12, hbm);
+        put(geo, gw * ge + 14, A);
+        put(geo, gw * ge + 16, invA);
+        put(geo, gw * ge + 18, man);
+        nbr[4 * ge + 3] = 0;
+        rain64[ge] = re;
+      }
+      (void)R;
+      (void)Gm;
+    }
+  }
+  // upload
+  const size_t rbytes = 16 * (size_t)h->rv * E;
+  for (int b = 0; b < 3; ++b)
+    if (h->rec[b].alloc(rbytes)) return fail(DGSWE_ENOMEM, "device allocation of %zu bytes failed", rbytes);
+  if (h->geo.alloc(16 * (size_t)h->gv * E) || h->nbr.alloc(16 * (size_t)E) || h->nodes.alloc(16 * (size_t)E) ||
+      h->xy64.alloc(16 * (size_t)N) || h->hbn.alloc(8 * (size_t)N) || h->eorig.alloc(4 * (size_t)E) ||
+      h->node_xy.alloc(mx ? 8 * (size_t)N : 16 * (size_t)N) || h->rain_e.alloc(mx ? 4 * (size_t)E : 8 * (size_t)E) ||
+      h->ctl.alloc(sizeof(Ctl)) || h->scen.alloc(sizeof(ScenDev) * ns) || h->ledger.alloc(16 * (size_t)(E / 64 + 1)) ||
+      h->tile_scen.alloc(4 * (size_t)(E / 64 + 1)) || h->grids.alloc(4 * grids.size()) ||
+      h->scratch.alloc(sizeof(double) * 4 * 4096))
+    return fail(DGSWE_ENOMEM, "device allocation failed");
+  CU(cudaMemcpy(h->rec[0].p, rec.data(), rbytes, cudaMemcpyHostToDevice));
+  CU(cudaMemset(h->rec[1].p, 0, rbytes));
+  CU(cudaMemset(h->rec[2].p, 0, rbytes));
+  CU(cudaMemcpy(h->geo.p, geo.data(), 4 * geo.size(), cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(h->nbr.p, nbr.data(), 4 * nbr.size(), cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(h->nodes.p, nodes.data(), 4 * nodes.size(), cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(h->xy64.p, xy64.data(), 8 * xy64.size(), cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(h->hbn.p, hbn.data(), 8 * hbn.size(), cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(h->eorig.p, eorig.data(), 4 * eorig.size(), cudaMemcpyHostToDevice));
+  if (mx) {
+    CU(cudaMemcpy(h->node_xy.p, xyf.data(), 4 * xyf.size(), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(h->rain_e.p, rainf.data(), 4 * rainf.size(), cudaMemcpyHostToDevice));
+  } else {
+    CU(cudaMemcpy(h->node_xy.p, xy64.data(), 8 * xy64.size(), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(h->rain_e.p, rain64.data(), 8 * rain64.size(), cudaMemcpyHostToDevice));
+  }
+  if (!grids.empty()) CU(cudaMemcpy(h->grids.p, grids.data(), 4 * grids.size(), cudaMemcpyHostToDevice));
+  CU(cudaMemset(h->ctl.p, 0, sizeof(Ctl)));
+  // per-scenario parameter blocks (dt filled in later)
+  std::vector<ScenDev> sd(ns);
+  for (size_t s = 0; s < ns; ++s) {
+    const Scenario& S = h->sc[s];
+    ScenDev& D = sd[s];
+    std::memset(&D, 0, sizeof D);
+    D.t0 = S.t0;
+    D.elem_begin = (int32_t)h->eoff[s];
+    D.elem_end = (int32_t)(h->eoff[s] + S.m.ne);
+    D.rain_kind = S.rain_kind;
+    const double st[8] = {S.storm.x0, S.storm.y0, S.storm.heading, S.storm.speed, S.storm.rpeak, S.storm.rm,
+                          S.storm.re, S.storm.t0};
+    std::memcpy(D.storm, st, sizeof st);
+    D.gnx = S.gnx; D.gny = S.gny; D.gnt = S.gnt;
+    D.gx0 = S.gx0; D.gy0 = S.gy0; D.gdx = S.gdx; D.gdy = S.gdy; D.gt0 = S.gt0; D.gdt = S.gdt;
+    D.grid = S.rain_kind == 3 ? h->grids.as<float>() + grid_off[s] : nullptr;
+    D.nseg = (int32_t)S.tamp.size();
+    for (size_t k = 0; k < S.tamp.size() && k < (size_t)MAXSEG; ++k) {
+      D.tamp[k] = S.tamp[k]; D.tper[k] = S.tper[k]; D.tpha[k] = S.tpha[k];
+    }
+    D.press = S.press ? 1 : 0;
+    D.ps[0] = S.ps.x0; D.ps[1] = S.ps.y0; D.ps[2] = S.ps.sigma; D.ps[3] = S.ps.peak;
+  }
+  CU(cudaMemcpy(h->scen.p, sd.data(), sizeof(ScenDev) * ns, cudaMemcpyHostToDevice));
+  h->led_rain.assign(ns, 0.0);
+  h->led_bdry.assign(ns, 0.0);
+  h->V0.assign(ns, 0.0);
+  h->VH0.assign(ns, 0.0);
+  h->stages = ssp_table(h->prm.ssp_stages);
+  return 0;
+}
+
+// fill the per-scenario time-step fields once dt is known
+static int upload_dt(dgswe_h h) {
+  std::vector<ScenDev> sd(h->sc.size());
+  CU(cudaMemcpy(sd.data(), h->scen.p, sizeof(ScenDev) * sd.size(), cudaMemcpyDeviceToHost));
+  for (size_t s = 0; s < sd.size(); ++s) {
+    ScenDev& D = sd[s];
+    D.dt = h->sc[s].dt;
+    split_ff(D.dt, D.dt_hi, D.dt_lo);
+    for (size_t k = 0; k < h->stages.size(); ++k) {
+      D.bdt[k] = h->stages[k].beta * D.dt;
+      split_ff(D.bdt[k], D.bdt_hi[k], D.bdt_lo[k]);
+      D.bw[k] = h->stages[k].bw;
+    }
+  }
+  CU(cudaMemcpy(h->scen.p, sd.data(), sizeof(ScenDev) * sd.size(), cudaMemcpyHostToDevice));
+  return 0;
+}
+
+// tile -> scenario map for the current block size
+static int set_tiling(dgswe_h h, int block) {
+  // fold the ledger partials of the current tiling into the host accumulators
+  if (h->ntiles > 0) {
+    std::vector<double> part(2 * (size_t)h->ntiles);
+    CU(cudaMemcpy(part.data(), h->ledger.p, 16 * (size_t)h->ntiles, cudaMemcpyDeviceToHost));
+    for (size_t s = 0; s < h->sc.size(); ++s) {
+      const long long t0 = h->eoff[s] / h->block, t1 = (h->eoff[s] + h->sc[s].m.ne + h->block - 1) / h->block;
+      for (long long t = t0; t < t1; ++t) { h->led_rain[s] += part[2 * t]; h->led_bdry[s] += part[2 * t + 1]; }
+    }
+  }
+  h->block = block;
+  h->ntiles = (int)(h->E / block);
+  std::vector<int32_t> ts(h->ntiles, 0);
+  for (size_t s = 0; s < h->sc.size(); ++s) {
+    const long long t0 = h->eoff[s] / block, t1 = (h->eoff[s] + TILE_ALIGN - 1 + h->sc[s].m.ne) / TILE_ALIGN * TILE_ALIGN / block;
+    for (long long t = t0; t < t1 && t < h->ntiles; ++t) ts[t] = (int32_t)s;
+  }
+  CU(cudaMemcpy(h->tile_scen.p, ts.data(), 4 * ts.size(), cudaMemcpyHostToDevice));
+  CU(cudaMemset(h->ledger.p, 0, 16 * (size_t)h->ntiles));
+  // tile ranges in the scenario blocks
+  std::vector<ScenDev> sd(h->sc.size());
+  CU(cudaMemcpy(sd.data(), h->scen.p, sizeof(ScenDev) * sd.size(), cudaMemcpyDeviceToHost));
+  for (size_t s = 0; s < sd.size(); ++s) {
+    sd[s].tile_begin = (int32_t)(h->eoff[s] / block);
+    sd[s].tile_end = (int32_t)((h->eoff[s] + h->sc[s].m.ne + block - 1) / block);
+  }
+  CU(cudaMemcpy(h->scen.p, sd.data(), sizeof(ScenDev) * sd.size(), cudaMemcpyHostToDevice));
+  if (h->g1) { cudaGraphExecDestroy(h->g1); h->g1 = nullptr; }
+  if (h->gK) { cudaGraphExecDestroy(h->gK); h->gK = nullptr; }
+  return 0;
+}
+
+template <class Pol>
+static StageArgs<Pol> make_args(dgswe_h h, int stage, int tune) {
+  using T = typename PolT<Pol>::T;
+  StageArgs<Pol> a;
+  std::memset(&a, 0, sizeof a);
+  const int S = (int)h->stages.size();
+  const Stage& st = h->stages[stage];
+  a.in = h->rec[stage].as<uint4>();
+  a.wn = h->rec[0].as<uint4>();
+  a.out = (stage == S - 1) ? h->rec[0].as<uint4>() : h->rec[stage + 1].as<uint4>();
+  a.nbr = h->nbr.as<int4>();
+  a.geo = h->geo.as<uint4>();
+  a.nodes = h->nodes.as<int4>();
+  a.node_xy = h->node_xy.as<T>();
+  a.hb_nodal = h->hbn.as<double>();
+  a.rain_e = h->rain_e.as<T>();
+  a.scen = h->scen.as<ScenDev>();
+  a.tile_scen = h->tile_scen.as<int32_t>();
+  a.ledger = h->ledger.as<double>();
+  a.ctl = h->ctl.as<Ctl>();
+  a.ntiles = h->ntiles;
+  a.stage = stage;
+  a.last = (stage == S - 1) ? 1 : 0;
+  a.persistent = h->persistent;
+  a.tune = tune;
+  a.friction = h->prm.friction;
+  split_ff(st.a_n, a.a_n_hi, a.a_n_lo);
+  split_ff(st.a_in, a.a_in_hi, a.a_in_lo);
+  a.a_n = st.a_n;
+  a.a_in = st.a_in;
+  a.cst = st.c;
+  a.g = (T)h->prm.g;
+  a.H0 = (T)h->prm.H0;
+  a.cf = (T)h->prm.cf;
+  return a;
+}
+
+static int grid_size(dgswe_h h) {
+  if (!h->persistent) return h->ntiles;
+  return std::max(1, std::min(h->ntiles, h->grid_persistent));
+}
+
+static int launch_stage_once(dgswe_h h, int stage, int tune, cudaStream_t s) {
+  const int grid = grid_size(h);
+  cudaError_t e;
+  if (mixed(h)) e = launch_stage<Mixed>(h->prm.p, h->prm.flux, make_args<Mixed>(h, stage, tune), grid, h->block, s);
+  else e = launch_stage<Fp64>(h->prm.p, h->prm.flux, make_args<Fp64>(h, stage, tune), grid, h->block, s);
+  if (e != cudaSuccess) return fail(DGSWE_ECUDA, "stage launch: %s", cudaGetErrorString(e));
+  h->launches++;
+  return 0;
+}
+
+static int occupancy(dgswe_h h, int block) {
+  return mixed(h) ? stage_blocks_per_sm<Mixed>(h->prm.p, h->prm.flux, block)
+                  : stage_blocks_per_sm<Fp64>(h->prm.p, h->prm.flux, block);
+}
+
+static int apply_launch(dgswe_h h, int block, int persistent) {
+  int sms = 0;
+  CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+  h->persistent = persistent;
+  h->grid_persistent = sms * std::max(1, occupancy(h, block));
+  return set_tiling(h, block);
+}
+
+// time the first stage (which reads w^n and writes a scratch buffer) for each launch shape
+static int autotune(dgswe_h h) {
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int bb = 128, bp = 0;
+  const int blocks[3] = {64, 128, 256};
+  for (int pi = 0; pi < 2; ++pi)
+    for (int bi = 0; bi < 3; ++bi) {
+      if (occupancy(h, blocks[bi]) < 1) continue;
+      if (int rc = apply_launch(h, blocks[bi], pi)) return rc;
+      for (int w = 0; w < 2; ++w)
+        if (int rc = launch_stage_once(h, 0, 1, h->stream)) return rc;
+      CU(cudaEventRecord(e0, h->stream));
+      for (int r = 0; r < 5; ++r)
+        if (int rc = launch_stage_once(h, 0, 1, h->stream)) return rc;
+      CU(cudaEventRecord(e1, h->stream));
+      CU(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CU(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) { best = ms; bb = blocks[bi]; bp = pi; }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->autotune = false;
+  return apply_launch(h, bb, bp);
+}
+
+static int build_graphs(dgswe_h h) {
+  for (int which = 0; which < 2; ++which) {
+    const int nsteps = which == 0 ? 1 : h->K;
+    cudaGraph_t g;
+    CU(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+    int rc = 0;
+    for (int k = 0; k < nsteps && !rc; ++k)
+      for (size_t s = 0; s < h->stages.size() && !rc; ++s) rc = launch_stage_once(h, (int)s, 0, h->cap);
+    cudaError_t ce = cudaStreamEndCapture(h->cap, &g);
+    if (rc) return rc;
+    if (ce != cudaSuccess) return fail(DGSWE_ECUDA, "graph capture: %s", cudaGetErrorString(ce));
+    h->launches -= nsteps * (long long)h->stages.size();  // counted when the graph runs
+    cudaGraphExec_t ex;
+    ce = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) return fail(DGSWE_ECUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+    (which == 0 ? h->g1 : h->gK) = ex;
+  }
+  return 0;
+}
+
+static int reduce_volume(dgswe_h h, size_t s, double& V, double& VH) {
+  const long long b = h->eoff[s], e = b + h->sc[s].m.ne;
+  const int nblk = (int)std::min<long long>(1024, std::max<long long>(1, (e - b + 255) / 256));
+  double* part = h->scratch.as<double>();
+  cudaError_t ce = mixed(h) ? launch_volume<Mixed>(h->prm.p, h->rec[0].as<uint4>(), h->geo.as<uint4>(), b, e, part, nblk, h->stream)
+                            : launch_volume<Fp64>(h->prm.p, h->rec[0].as<uint4>(), h->geo.as<uint4>(), b, e, part, nblk, h->stream);
+  if (ce != cudaSuccess) return fail(DGSWE_ECUDA, "volume launch: %s", cudaGetErrorString(ce));
+  h->launches++;
+  ce = launch_reduce_pairs(part, nblk, 2, part + 4 * 1024, h->stream);
+  if (ce != cudaSuccess) return fail(DGSWE_ECUDA, "reduce launch: %s", cudaGetErrorString(ce));
+  h->launches++;
+  double out[4];
+  CU(cudaMemcpyAsync(out, part + 4 * 1024, sizeof out, cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  V = out[0] + out[1];
+  VH = out[2] + out[3];
+  return 0;
+}
+
+// positive-depth operator on the initial state, then dt and the initial volumes
+static int prepare(dgswe_h h) {
+  DeviceGuard dg_(h->device);
+  const double cfl = h->prm.cfl;
+  for (size_t s = 0; s < h->sc.size(); ++s) {
+    const long long b = h->eoff[s], e = b + h->sc[s].m.ne;
+    cudaError_t ce;
+    if (mixed(h)) {
+      StageArgs<Mixed> a = make_args<Mixed>(h, 0, 1);
+      a.in = h->rec[0].as<uint4>();
+      a.out = h->rec[0].as<uint4>();
+      ce = launch_prepare<Mixed>(h->prm.p, a, b, e, h->stream);
+    } else {
+      StageArgs<Fp64> a = make_args<Fp64>(h, 0, 1);
+      a.in = h->rec[0].as<uint4>();
+      a.out = h->rec[0].as<uint4>();
+      ce = launch_prepare<Fp64>(h->prm.p, a, b, e, h->stream);
+    }
+    if (ce != cudaSuccess) return fail(DGSWE_ECUDA, "prepare launch: %s", cudaGetErrorString(ce));
+    h->launches++;
+    if (h->sc[s].dt <= 0.0) {
+      if (h->prm.dt > 0.0) {
+        h->sc[s].dt = h->prm.dt;
+      } else {
+        if (!(cfl > 0.0)) return fail(DGSWE_EINVAL, "neither dt nor cfl is positive");
+        const int nblk = (int)std::min<long long>(1024, std::max<long long>(1, (e - b + 255) / 256));
+        double* part = h->scratch.as<double>();
+        ce = mixed(h) ? launch_dt<Mixed>(h->prm.p, h->rec[0].as<uint4>(), h->nodes.as<int4>(), h->xy64.as<double>(),
+                                         h->hbn.as<double>(), b, e, cfl, h->prm.g, h->prm.H0, part, nblk, h->stream)
+                      : launch_dt<Fp64>(h->prm.p, h->rec[0].as<uint4>(), h->nodes.as<int4>(), h->xy64.as<double>(),
+                                        h->hbn.as<double>(), b, e, cfl, h->prm.g, h->prm.H0, part, nblk, h->stream);
+        if (ce != cudaSuccess) return fail(DGSWE_ECUDA, "dt launch: %s", cudaGetErrorString(ce));
+        h->launches++;
+        std::vector<double> mins(nblk);
+        CU(cudaMemcpyAsync(mins.data(), part, 8 * (size_t)nblk, cudaMemcpyDeviceToHost, h->stream));
+        CU(cudaStreamSynchronize(h->stream));
+        h->sc[s].dt = *std::min_element(mins.begin(), mins.end());
+      }
+    }
+    if (int rc = reduce_volume(h, s, h->V0[s], h->VH0[s])) return rc;
+  }
+  if (int rc = upload_dt(h)) return rc;
+  Ctl zero{};
+  CU(cudaMemcpyAsync(h->ctl.p, &zero, sizeof zero, cudaMemcpyHostToDevice, h->stream));
+  h->ntiles = 0;
+  if (int rc = apply_launch(h, h->block, h->persistent)) return rc;
+  CU(cudaStreamSynchronize(h->stream));
+  h->ready = true;
+  return 0;
+}
+
+// ------------------------------------------------------------------------------ C ABI ---
+extern "C" {
+
+const char* dgswe_last_error(void) { return g_err.c_str(); }
+
+int dgswe_create(dgswe_h* out, int device, void* cuda_stream) {
+  if (!out) return fail(DGSWE_EINVAL, "null output handle");
+  *out = nullptr;
+  int n = 0;
+  cudaError_t ce = cudaGetDeviceCount(&n);
+  if (ce != cudaSuccess || n == 0) return fail(DGSWE_ENOLIB, "no CUDA device: %s", cudaGetErrorString(ce));
+  if (device < 0 || device >= n) return fail(DGSWE_EINVAL, "device %d outside [0,%d)", device, n);
+  int major = 0, minor = 0;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, device);
+  if (major != 10 || minor != 3)
+    return fail(DGSWE_ENOLIB, "device %d is sm_%d%d; this library is built for sm_103a only", device, major, minor);
+  std::unique_ptr<dgswe_ctx> h(new dgswe_ctx());
+  h->device = device;
+  DeviceGuard dg_(device);
+  if (cuda_stream) {
+    h->stream = (cudaStream_t)cuda_stream;
+  } else {
+    CU(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    h->own_stream = true;
+  }
+  CU(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+  *out = h.release();
+  return 0;
+}
+
+void dgswe_destroy(dgswe_h h) {
+  if (!h) return;
+  {
+    DeviceGuard dg_(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+  }
+  delete h;
+}
+
+int dgswe_set_params(dgswe_h h, const dgswe_params* p) {
+  if (int rc = check_handle(h)) return rc;
+  if (!p) return fail(DGSWE_EINVAL, "null params");
+  if (p->p < 1 || p->p > 2) return fail(DGSWE_EINVAL, "p = %d: the device path supports p = 1 and p = 2", p->p);
+  if (p->flux != DGSWE_FLUX_ROE && p->flux != DGSWE_FLUX_LLF) return fail(DGSWE_EINVAL, "unknown flux %d", p->flux);
+  if (p->ssp_stages != 2 && p->ssp_stages != 3) return fail(DGSWE_EINVAL, "ssp_stages must be 2 or 3");
+  if (p->precision != DGSWE_FP64 && p->precision != DGSWE_MIXED) return fail(DGSWE_EINVAL, "unknown precision");
+  if (!(p->g > 0) || !(p->H0 > 0)) return fail(DGSWE_EINVAL, "g and H0 must be positive");
+  if (p->friction < 0 || p->friction > 2) return fail(DGSWE_EINVAL, "unknown friction law");
+  if (!h->sc.empty() && h->sc[0].level > 0) return fail(DGSWE_ESTATE, "set_params must precede set_mesh");
+  h->prm = *p;
+  h->has_params = true;
+  return 0;
+}
+
+int dgswe_set_mesh(dgswe_h h, int32_t n_nodes, const double* xy, int32_t n_tri, const int32_t* tri, int32_t n_bedge,
+                   const int32_t* bedge, const int32_t* btype, const int32_t* bseg) {
+  if (int rc = check_handle(h)) return rc;
+  if (!h->has_params) return fail(DGSWE_ESTATE, "set_params must precede set_mesh");
+  if (h->ensemble) return fail(DGSWE_ESTATE, "an ensemble's members are fixed");
+  Scenario S;
+  std::string err;
+  int rc = build_mesh(n_nodes, xy, n_tri, tri, n_bedge, bedge, btype, bseg, S.m, err);
+  if (rc) return fail(rc, "%s", err.c_str());
+  S.level = 1;
+  h->sc.clear();
+  h->sc.push_back(std::move(S));
+  h->ready = false;
+  return 0;
+}
+
+static Scenario* scen_at(dgswe_h h, int level) {
+  if (h->sc.empty() || h->sc[0].level < level || h->ensemble) return nullptr;
+  return &h->sc[0];
+}
+
+int dgswe_set_fields(dgswe_h h, const double* hb, const double* man, int32_t manning_nodal) {
+  if (int rc = check_handle(h)) return rc;
+  Scenario* S = scen_at(h, 1);
+  if (!S) return fail(DGSWE_ESTATE, "set_mesh must precede set_fields");
+  if (!hb) return fail(DGSWE_EINVAL, "null bathymetry");
+  const HostMesh& M = S->m;
+  S->hb.resize(M.nn);
+  for (int i = 0; i < M.nn; ++i) {
+    S->hb[i] = hb[M.norig[i]];
+    if (!std::isfinite(S->hb[i])) return fail(DGSWE_EINVAL, "non-finite bathymetry at node %d", M.norig[i]);
+  }
+  S->man.assign(M.ne, 0.0);
+  if (man) {
+    for (int e = 0; e < M.ne; ++e) {
+      if (manning_nodal) {
+        const int32_t* v = &M.tri[3 * (size_t)e];
+        S->man[e] = (man[M.norig[v[0]]] + man[M.norig[v[1]]] + man[M.norig[v[2]]]) / 3.0;
+      } else {
+        S->man[e] = man[M.eorig[e]];
+      }
+    }
+  } else if (h->prm.friction == DGSWE_MANNING) {
+    return fail(DGSWE_EINVAL, "Manning friction needs a Manning field");
+  }
+  S->level = std::max(S->level, 2);
+  h->ready = false;
+  return 0;
+}
+
+int dgswe_set_rain_nodal(dgswe_h h, const double* r) {
+  if (int rc = check_handle(h)) return rc;
+  Scenario* S = scen_at(h, 1);
+  if (!S) return fail(DGSWE_ESTATE, "set_mesh must precede the rain source");
+  if (!r) return fail(DGSWE_EINVAL, "null rain");
+  S->rain_n.resize(S->m.nn);
+  for (int i = 0; i < S->m.nn; ++i) S->rain_n[i] = r[S->m.norig[i]];
+  S->rain_kind = 1;
+  h->ready = false;
+  return 0;
+}
+
+int dgswe_set_rain_parametric(dgswe_h h, const dgswe_storm* st) {
+  if (int rc = check_handle(h)) return rc;
+  Scenario* S = scen_at(h, 1);
+  if (!S) return fail(DGSWE_ESTATE, "set_mesh must precede the rain source");
+  if (!st || !(st->rm > 0) || !(st->re > 0)) return fail(DGSWE_EINVAL, "storm radii must be positive");
+  S->storm = *st;
+  S->rain_kind = 2;
+  h->ready = false;
+  return 0;
+}
+
+int dgswe_set_rain_grid(dgswe_h h, int32_t nx, int32_t ny, int32_t nt, double x0, double y0, double dx, double dy,
+                        double t0, double dt_rec, const float* mmh) {
+  if (int rc = check_handle(h)) return rc;
+  Scenario* S = scen_at(h, 1);
+  if (!S) return fail(DGSWE_ESTATE, "set_mesh must precede the rain source");
+  if (nx < 1 || ny < 1 || nt < 1 || !(dx > 0) || !(dy > 0) || !(dt_rec > 0) || !mmh)
+    return fail(DGSWE_EINVAL, "bad rain grid");
+  S->gnx = nx; S->gny = ny; S->gnt = nt; S->gx0 = x0; S->gy0 = y0; S->gdx = dx; S->gdy = dy; S->gt0 = t0; S->gdt = dt_rec;
+  S->grid.assign(mmh, mmh + (size_t)nx * ny * nt);
+  S->rain_kind = 3;
+  h->ready = false;
+  return 0;
+}
+
+int dgswe_set_tide(dgswe_h h, int32_t n, const double* amp, const double* per, const double* pha) {
+  if (int rc = check_handle(h)) return rc;
+  Scenario* S = scen_at(h, 1);
+  if (!S) return fail(DGSWE_ESTATE, "set_mesh must precede set_tide");
+  if (n < 0 || n > MAXSEG || (n > 0 && (!amp || !per || !pha))) return fail(DGSWE_EINVAL, "at most %d tidal segments", MAXSEG);
+  for (int k = 0; k < n; ++k)
+    if (!(per[k] > 0)) return fail(DGSWE_EINVAL, "tidal period must be positive");
+  S->tamp.assign(amp, amp + n);
+  S->tper.assign(per, per + n);
+  S->tpha.assign(pha, pha + n);
+  h->ready = false;
+  return 0;
+}
+
+int dgswe_set_pressure_setup(dgswe_h h, const dgswe_gauss_setup* ps) {
+  if (int rc = check_handle(h)) return rc;
+  Scenario* S = scen_at(h, 1);
+  if (!S) return fail(DGSWE_ESTATE, "set_mesh must precede set_pressure_setup");
+  if (ps && !(ps->sigma > 0)) return fail(DGSWE_EINVAL, "sigma must be positive");
+  S->press = ps != nullptr;
+  if (ps) S->ps = *ps;
+  h->ready = false;
+  return 0;
+}
+
+int dgswe_set_state(dgswe_h h, const double* zeta, const double* qx, const double* qy, int32_t layout, double t0) {
+  if (int rc = check_handle(h)) return rc;
+  Scenario* S = scen_at(h, 2);
+  if (!S) return fail(DGSWE_ESTATE, "set_fields must precede set_state");
+  if (!zeta || !qx || !qy) return fail(DGSWE_EINVAL, "null state array");
+  const int p = h->prm.p, np = np_of(p);
+  const HostMesh& M = S->m;
+  if (M.nseg > (int)S->tamp.size()) return fail(DGSWE_EINVAL, "ocean edges use %d tidal segments, %zu given", M.nseg, S->tamp.size());
+  S->w.assign((size_t)M.ne * 3 * np, 0.0);
+  const double* f[3] = {zeta, qx, qy};
+  if (layout == DGSWE_LAYOUT_MODAL) {
+    for (int e = 0; e < M.ne; ++e)
+      for (int v = 0; v < 3; ++v)
+        for (int m = 0; m < np; ++m) S->w[((size_t)e * 3 + v) * np + m] = f[v][(size_t)m * M.ne + M.eorig[e]];
+  } else if (layout == DGSWE_LAYOUT_NODAL) {
+    if (!g_tab_built[p]) {
+      build_tables(p, g_tabd[p]);
+      tables_to_float(g_tabd[p], g_tabf[p]);
+      g_tab_built[p] = true;
+    }
+    const RefTab<double>& tb = g_tabd[p];
+    for (int e = 0; e < M.ne; ++e) {
+      const int32_t* vt = &M.tri[3 * (size_t)e];
+      for (int v = 0; v < 3; ++v) {
+        const double fv[3] = {f[v][M.norig[vt[0]]], f[v][M.norig[vt[1]]], f[v][M.norig[vt[2]]]};
+        for (int m = 0; m < np; ++m) {  // projection of the linear interpolant (exact rule)
+          double s = 0.0;
+          for (int q = 0; q < tb.nq; ++q)
+            s += tb.qw[q] * (tb.ql[q][0] * fv[0] + tb.ql[q][1] * fv[1] + tb.ql[q][2] * fv[2]) * tb.qphi[q][m];
+          S->w[((size_t)e * 3 + v) * np + m] = s;
+        }
+      }
+    }
+  } else {
+    return fail(DGSWE_EINVAL, "unknown layout %d", layout);
+  }
+  for (double v : S->w)
+    if (!std::isfinite(v)) return fail(DGSWE_EINVAL, "non-finite initial state");
+  S->t0 = t0;
+  S->dt = 0.0;
+  S->level = 3;
+  h->ready = false;
+  if (int rc = build_layout(h)) return rc;
+  return prepare(h);
+}
+
+int dgswe_step(dgswe_h h, int64_t n) {
+  if (int rc = check_handle(h)) return rc;
+  if (!h->ready) return fail(DGSWE_ESTATE, "set_state must precede step");
+  if (n < 0) return fail(DGSWE_EINVAL, "negative step count");
+  if (n == 0) return 0;
+  DeviceGuard dg_(h->device);
+  if (h->autotune)
+    if (int rc = autotune(h)) return rc;
+  if (!h->g1)
+    if (int rc = build_graphs(h)) return rc;
+  const long long per = (long long)h->stages.size();
+  for (int64_t i = 0; i < n / h->K; ++i) CU(cudaGraphLaunch(h->gK, h->stream));
+  for (int64_t i = 0; i < n % h->K; ++i) CU(cudaGraphLaunch(h->g1, h->stream));
+  h->launches += n * per;
+  return 0;
+}
+
+int dgswe_sync(dgswe_h h) {
+  if (int rc = check_handle(h)) return rc;
+  if (!h->ready) return 0;
+  DeviceGuard dg_(h->device);
+  CU(cudaStreamSynchronize(h->stream));
+  Ctl c;
+  CU(cudaMemcpy(&c, h->ctl.p, sizeof c, cudaMemcpyDeviceToHost));
+  if (c.err & ERR_NONFINITE) return fail(DGSWE_ENONFINITE, "a stage produced a non-finite state");
+  if (c.err & ERR_NEGDEPTH) return fail(DGSWE_ENEGDEPTH, "an element mean depth fell below zero");
+  return 0;
+}
+
+int dgswe_get_dt(dgswe_h h, double* dt) {
+  if (int rc = check_handle(h)) return rc;
+  if (!h->ready || !dt) return fail(DGSWE_ESTATE, "no state");
+  *dt = h->sc[0].dt;
+  return 0;
+}
+
+static int gather_state(dgswe_h h, size_t s, double* z, double* x, double* y, bool device_out) {
+  DeviceGuard dg_(h->device);
+  const long long n = h->sc[s].m.ne, b = h->eoff[s];
+  const size_t cnt = (size_t)h->np * n;
+  double *dz = z, *dx = x, *dy = y;
+  if (!device_out) {
+    if (h->gather_buf.n < 3 * cnt * sizeof(double))
+      if (h->gather_buf.alloc(3 * cnt * sizeof(double))) return fail(DGSWE_ENOMEM, "gather buffer");
+    dz = h->gather_buf.as<double>();
+    dx = dz + cnt;
+    dy = dx + cnt;
+  }
+  cudaError_t ce = mixed(h) ? launch_gather<Mixed>(h->prm.p, h->rec[0].as<uint4>(), b, n, h->eorig.as<int32_t>() + b, dz, dx, dy, h->stream)
+                            : launch_gather<Fp64>(h->prm.p, h->rec[0].as<uint4>(), b, n, h->eorig.as<int32_t>() + b, dz, dx, dy, h->stream);
+  if (ce != cudaSuccess) return fail(DGSWE_ECUDA, "gather launch: %s", cudaGetErrorString(ce));
+  h->launches++;
+  if (!device_out) {
+    CU(cudaMemcpyAsync(z, dz, cnt * 8, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaMemcpyAsync(x, dx, cnt * 8, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaMemcpyAsync(y, dy, cnt * 8, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+  }
+  return 0;
+}
+
+int dgswe_get_state(dgswe_h h, double* z, double* x, double* y) {
+  if (int rc = check_handle(h)) return rc;
+  if (!h->ready) return fail(DGSWE_ESTATE, "no state");
+  if (!z || !x || !y) return fail(DGSWE_EINVAL, "null output");
+  if (h->ensemble) return fail(DGSWE_EINVAL, "use dgswe_ensemble_get_state");
+  return gather_state(h, 0, z, x, y, false);
+}
+
+int dgswe_get_state_device(dgswe_h h, double* z, double* x, double* y) {
+  if (int rc = check_handle(h)) return rc;
+  if (!h->ready) return fail(DGSWE_ESTATE, "no state");
+  if (!z || !x || !y) return fail(DGSWE_EINVAL, "null output");
+  if (h->ensemble) return fail(DGSWE_EINVAL, "use dgswe_ensemble_get_state");
+  return gather_state(h, 0, z, x, y, true);
+}
+
+int dgswe_get_dry(dgswe_h h, uint8_t* dry) {
+  if (int rc = check_handle(h)) return rc;
+  if (!h->ready) return fail(DGSWE_ESTATE, "no state");
+  if (!dry) return fail(DGSWE_EINVAL, "null output");
+  DeviceGuard dg_(h->device);
+  const HostMesh& M = h->sc[0].m;
+  const size_t rw = 4 * (size_t)h->rv;
+  std::vector<uint32_t> rec(rw * M.ne);
+  CU(cudaStreamSynchronize(h->stream));
+  CU(cudaMemcpy(rec.data(), h->rec[0].p, 4 * rec.size(), cudaMemcpyDeviceToHost));
+  const int NS = h->np - 1;
+  const size_t off = mixed(h) ? (size_t)(6 + 3 * NS + 1) : (size_t)2 * (3 + 3 * NS + 1);
+  for (int e = 0; e < M.ne; ++e) dry[M.eorig[e]] = (rec[rw * e + off] & FLAG_DRY) ? 1 : 0;
+  return 0;
+}
+
+static int ledger_of(dgswe_h h, size_t s, dgswe_ledger* out) {
+  DeviceGuard dg_(h->device);
+  CU(cudaStreamSynchronize(h->stream));
+  double V, VH;
+  if (int rc = reduce_volume(h, s, V, VH)) return rc;
+  (void)VH;
+  Ctl c;
+  CU(cudaMemcpy(&c, h->ctl.p, sizeof c, cudaMemcpyDeviceToHost));
+  std::vector<double> part(2 * (size_t)h->ntiles);
+  CU(cudaMemcpy(part.data(), h->ledger.p, 16 * (size_t)h->ntiles, cudaMemcpyDeviceToHost));
+  double rs = h->led_rain[s], rc_ = 0.0, bs = h->led_bdry[s], bc = 0.0;
+  auto neu = [](double& sum, double& comp, double v) {
+    const double t = sum + v;
+    comp += (std::fabs(sum) >= std::fabs(v)) ? (sum - t) + v : (v - t) + sum;
+    sum = t;
+  };
+  const long long t0 = h->eoff[s] / h->block, t1 = (h->eoff[s] + h->sc[s].m.ne + h->block - 1) / h->block;
+  for (long long t = t0; t < t1; ++t) {
+    neu(rs, rc_, part[2 * t]);
+    neu(bs, bc, part[2 * t + 1]);
+  }
+  out->steps = (int64_t)c.step;
+  out->t = h->sc[s].t0 + (double)c.step * h->sc[s].dt;
+  out->V0 = h->V0[s];
+  out->V = V;
+  out->rain_in = rs + rc_;
+  out->bdry_in = bs + bc;
+  out->VH0 = h->VH0[s];
+  out->rel_err = std::fabs(V - h->V0[s] - out->rain_in - out->bdry_in) / h->VH0[s];
+  // wet fraction from the dry flags
+  const HostMesh& M = h->sc[s].m;
+  const size_t rw = 4 * (size_t)h->rv;
+  std::vector<uint32_t> rec(rw * M.ne);
+  CU(cudaMemcpy(rec.data(), h->rec[0].as<uint32_t>() + rw * h->eoff[s], 4 * rec.size(), cudaMemcpyDeviceToHost));
+  const int NS = h->np - 1;
+  const size_t off = mixed(h) ? (size_t)(6 + 3 * NS + 1) : (size_t)2 * (3 + 3 * NS + 1);
+  long long wet = 0;
+  for (int e = 0; e < M.ne; ++e) wet += (rec[rw * e + off] & FLAG_DRY) ? 0 : 1;
+  out->wet_frac = (double)wet / M.ne;
+  return 0;
+}
+
+int dgswe_get_ledger(dgswe_h h, dgswe_ledger* out) {
+  if (int rc = check_handle(h)) return rc;
+  if (!h->ready) return fail(DGSWE_ESTATE, "no state");
+  if (!out) return fail(DGSWE_EINVAL, "null output");
+  return ledger_of(h, 0, out);
+}
+
+int dgswe_volume(dgswe_h h, double* out) {
+  if (int rc = check_handle(h)) return rc;
+  if (!h->ready) return fail(DGSWE_ESTATE, "no state");
+  if (!out) return fail(DGSWE_EINVAL, "null output");
+  DeviceGuard dg_(h->device);
+  double VH;
+  return reduce_volume(h, 0, *out, VH);
+}
+
+int dgswe_ensemble_create(dgswe_h* out, int32_t n, const dgswe_h* members, int device, void* stream) {
+  if (!out) return fail(DGSWE_EINVAL, "null output handle");
+  *out = nullptr;
+  if (n < 1 || !members) return fail(DGSWE_EINVAL, "empty ensemble");
+  for (int i = 0; i < n; ++i) {
+    if (!members[i] || !members[i]->ready || members[i]->ensemble)
+      return fail(DGSWE_ESTATE, "member %d has no state", i);
+    const dgswe_params& a = members[0]->prm;
+    const dgswe_params& b = members[i]->prm;
+    if (a.p != b.p || a.flux != b.flux || a.ssp_stages != b.ssp_stages || a.precision != b.precision || a.g != b.g ||
+        a.H0 != b.H0 || a.friction != b.friction || a.cf != b.cf)
+      return fail(DGSWE_EINVAL, "member %d differs in p, flux, ssp_stages, precision, g, H0 or friction", i);
+  }
+  dgswe_h h = nullptr;
+  if (int rc = dgswe_create(&h, device, stream)) return rc;
+  h->prm = members[0]->prm;
+  h->has_params = true;
+  h->ensemble = true;
+  for (int i = 0; i < n; ++i) h->sc.push_back(members[i]->sc[0]);
+  int rc = build_layout(h);
+  if (!rc) rc = prepare(h);
+  if (rc) {
+    dgswe_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return 0;
+}
+
+int dgswe_ensemble_step(dgswe_h ens, int64_t n) {
+  if (int rc = check_handle(ens)) return rc;
+  if (!ens->ensemble) return fail(DGSWE_EINVAL, "not an ensemble");
+  return dgswe_step(ens, n);
+}
+
+int dgswe_ensemble_get_state(dgswe_h ens, int32_t i, double* z, double* x, double* y) {
+  if (int rc = check_handle(ens)) return rc;
+  if (!ens->ensemble || i < 0 || i >= (int)ens->sc.size()) return fail(DGSWE_EINVAL, "bad member index");
+  if (!z || !x || !y) return fail(DGSWE_EINVAL, "null output");
+  return gather_state(ens, (size_t)i, z, x, y, false);
+}
+
+int dgswe_ensemble_get_ledger(dgswe_h ens, int32_t i, dgswe_ledger* out) {
+  if (int rc = check_handle(ens)) return rc;
+  if (!ens->ensemble || i < 0 || i >= (int)ens->sc.size()) return fail(DGSWE_EINVAL, "bad member index");
+  if (!out) return fail(DGSWE_EINVAL, "null output");
+  return ledger_of(ens, (size_t)i, out);
+}
+
+int dgswe_set_launch(dgswe_h h, int32_t block, int32_t persistent) {
+  if (int rc = check_handle(h)) return rc;
+  if (block != 0 && block != 64 && block != 128 && block != 256) return fail(DGSWE_EINVAL, "block must be 0, 64, 128 or 256");
+  if (block == 0) {
+    h->autotune = true;
+    return 0;
+  }
+  h->autotune = false;
+  if (!h->ready) {
+    h->block = block;
+    h->persistent = persistent ? 1 : 0;
+    return 0;
+  }
+  DeviceGuard dg_(h->device);
+  CU(cudaStreamSynchronize(h->stream));
+  return apply_launch(h, block, persistent ? 1 : 0);
+}
+
+int dgswe_get_launch(dgswe_h h, int32_t* block, int32_t* persistent) {
+  if (int rc = check_handle(h)) return rc;
+  if (block) *block = h->block;
+  if (persistent) *persistent = h->persistent;
+  return 0;
+}
+
+int64_t dgswe_launch_count(dgswe_h h) { return h ? h->launches : 0; }
+
+}  // extern "C"

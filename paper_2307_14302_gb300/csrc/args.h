@@ -1,0 +1,84 @@
+// args.h -- kernel argument blocks of libdgswe (plain structs shared by host and device code).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "layout.h"
+
+namespace dg {
+
+struct Mixed;
+struct Fp64;
+template <class Pol>
+struct PolT;
+template <>
+struct PolT<Mixed> {
+  using T = float;
+};
+template <>
+struct PolT<Fp64> {
+  using T = double;
+};
+
+// ----------------------------------------------------------------------- kernel arguments ---
+template <class Pol>
+struct StageArgs {
+  using T = typename PolT<Pol>::T;
+  const uint4* in;         // stage input records
+  const uint4* wn;         // step-initial records (Shu-Osher combination)
+  uint4* out;              // output records
+  const int4* nbr;         // per element: 3 neighbour codes (+ Manning bits in .w, mixed)
+  const uint4* geo;        // static geometry records
+  const int4* nodes;       // per element: 3 node indices
+  const T* node_xy;        // [2 * nodes] coordinates (rain, pressure set-up)
+  const double* hb_nodal;  // [nodes] FP64 bathymetry (depth test near H0)
+  const T* rain_e;         // [elements] constant element rain (rain_kind 1)
+  const ScenDev* scen;
+  const int32_t* tile_scen;
+  double* ledger;          // [tiles][2]: rain volume, boundary inflow volume
+  Ctl* ctl;
+  int ntiles;
+  int stage;               // Shu-Osher stage index
+  int last;                // 1 on the final stage of a step
+  int persistent;
+  int tune;                // 1: timing run, no ledger or step bookkeeping
+  int friction;            // 0 Manning, 1 quadratic, 2 none
+  float a_n_hi, a_n_lo, a_in_hi, a_in_lo;  // Shu-Osher coefficients as float-float
+  double a_n, a_in;
+  double cst;              // stage time as a fraction of dt
+  T g, H0, cf;
+};
+
+}  // namespace dg
+
+namespace dg {
+
+// host-side launchers, explicitly instantiated for Mixed (stage_mixed.cu) and Fp64 (stage_fp64.cu)
+template <class Pol>
+cudaError_t upload_tables(int p, const RefTab<float>& tf, const RefTab<double>& td);
+template <class Pol>
+cudaError_t launch_stage(int p, int flux, const StageArgs<Pol>& a, int grid, int block, cudaStream_t s);
+template <class Pol>
+int stage_blocks_per_sm(int p, int flux, int block);
+// positive-depth operator on records [begin, end) in place (a.in == a.out)
+template <class Pol>
+cudaError_t launch_prepare(int p, const StageArgs<Pol>& a, long long begin, long long end, cudaStream_t s);
+// partial FP64 sums of A*mean(zeta) and A*mean(H) over [begin, end): partials[4*block]
+template <class Pol>
+cudaError_t launch_volume(int p, const uint4* rec, const uint4* geo, long long begin, long long end,
+                          double* partials, int nblk, cudaStream_t s);
+// per-block minimum of the CFL time step over [begin, end): partials[block]
+template <class Pol>
+cudaError_t launch_dt(int p, const uint4* rec, const int4* nodes, const double* xy64, const double* hb_nodal,
+                      long long begin, long long end, double cfl, double g, double H0, double* partials, int nblk,
+                      cudaStream_t s);
+// modal state [Np][n] of scenario elements [begin, begin + n) in caller order (orig index)
+template <class Pol>
+cudaError_t launch_gather(int p, const uint4* rec, long long begin, long long n, const int32_t* orig, double* z,
+                          double* x, double* y, cudaStream_t s);
+
+// Neumaier-compensated reduction of per-block partial pairs (shared by all precisions)
+cudaError_t launch_reduce_pairs(const double* partials, int nblk, int npairs, double* out, cudaStream_t s);
+
+}  // namespace dg

@@ -1,0 +1,1159 @@
+// stage.cuh -- the fused DG stage kernel for sm_103a.
+//
+// One thread owns one triangle and, per Runge-Kutta stage (Sec. 2.2, Eq. RKSSP):
+//   1. evaluates the numerical flux on its three edges at p+1 Gauss points (Sec. 2.3: Roe or
+//      LLF; ghost states for land and ocean boundaries; the wet/dry closure of Sec. 2.4),
+//   2. integrates the area terms of Eq. elem_weak_form (flux divergence, balance term
+//      g zeta grad(hb), Manning friction, pressure set-up, element rain of Eq. rain),
+//   3. applies the diagonal inverse mass matrix of the orthonormal basis (Eq. dubiner),
+//   4. forms the Shu-Osher combination with the step's initial state,
+//   5. applies the positive-depth operator M Pi_h (Sec. 2.4) and stores the record,
+//   6. adds its rain and boundary volumes to per-tile ledger partials.
+// Interior edge fluxes are computed by both neighbours in one canonical orientation (the lower
+// element index is "left"), so both apply bitwise-opposite mass fluxes and mass is conserved.
+//
+// Pressure and balance terms are evaluated relative to the element's own mean elevation c:
+// the identity  <P_c n, v> - (grad v, P_c) - (g c grad hb, v) = 0  with P_c = g/2 c (c + 2 hb)
+// (exact for piecewise-linear hb and the degree-(2p+1) rule) is subtracted from Eq.
+// elem_weak_form.  Nothing changes in exact arithmetic; in floating point the large terms
+// g hb zeta cancel before rounding, which keeps lake-at-rest exact in FP32.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "args.h"
+#include "layout.h"
+
+namespace dg {
+
+// ------------------------------------------------------------ float-float (FP32 pairs) ---
+struct ff {
+  float hi, lo;
+};
+__device__ __forceinline__ ff two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ ff quick_two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  ff s = two_sum(a.hi, b.hi);
+  ff t = two_sum(a.lo, b.lo);
+  ff u = quick_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+  return quick_two_sum(u.hi, __fadd_rn(u.lo, t.lo));
+}
+__device__ __forceinline__ ff ff_add_f(ff a, float b) {
+  ff s = two_sum(a.hi, b);
+  return quick_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return quick_two_sum(p, e);
+}
+__device__ __forceinline__ ff ff_mul_f(ff a, float b) {
+  float p = __fmul_rn(a.hi, b);
+  float e = __fmaf_rn(a.hi, b, -p);
+  e = __fmaf_rn(a.lo, b, e);
+  return quick_two_sum(p, e);
+}
+__device__ __forceinline__ float ff_to_f(ff a) { return __fadd_rn(a.hi, a.lo); }
+// a - b rounded to float; exactly antisymmetric under swapping a and b
+__device__ __forceinline__ float ff_diff(ff a, ff b) {
+  ff s = two_sum(a.hi, -b.hi);
+  return __fadd_rn(s.hi, __fadd_rn(s.lo, __fsub_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ double ff_to_d(ff a) { return (double)a.hi + (double)a.lo; }
+
+// accumulator overloads: double (FP64 path) and ff (mixed path)
+__device__ __forceinline__ double acc_r(double a) { return a; }
+__device__ __forceinline__ float acc_r(ff a) { return ff_to_f(a); }
+__device__ __forceinline__ double acc_d(double a) { return a; }
+__device__ __forceinline__ double acc_d(ff a) { return ff_to_d(a); }
+__device__ __forceinline__ double acc_diff(double a, double b) { return a - b; }
+__device__ __forceinline__ float acc_diff(ff a, ff b) { return ff_diff(a, b); }
+__device__ __forceinline__ double acc_add(double a, double b) { return a + b; }
+__device__ __forceinline__ ff acc_add(ff a, ff b) { return ff_add(a, b); }
+__device__ __forceinline__ double acc_addr(double a, double b) { return a + b; }
+__device__ __forceinline__ ff acc_addr(ff a, float b) { return ff_add_f(a, b); }
+__device__ __forceinline__ double acc_mul(double a, double b) { return a * b; }
+__device__ __forceinline__ ff acc_mul(ff a, ff b) { return ff_mul(a, b); }
+__device__ __forceinline__ double acc_mulr(double a, double b) { return a * b; }
+__device__ __forceinline__ ff acc_mulr(ff a, float b) { return ff_mul_f(a, b); }
+__device__ __forceinline__ void acc_set(double& a, double v) { a = v; }
+__device__ __forceinline__ void acc_set(ff& a, double v) {
+  a.hi = (float)v;
+  a.lo = (float)(v - (double)a.hi);
+}
+__device__ __forceinline__ double acc_neg(double a) { return -a; }
+__device__ __forceinline__ ff acc_neg(ff a) { return {-a.hi, -a.lo}; }
+template <class Acc>
+__device__ __forceinline__ Acc acc_make(float hi, float lo, double d);
+template <>
+__device__ __forceinline__ double acc_make<double>(float, float, double d) { return d; }
+template <>
+__device__ __forceinline__ ff acc_make<ff>(float hi, float lo, double) { return {hi, lo}; }
+__device__ __forceinline__ bool acc_finite(double a) { return isfinite(a); }
+__device__ __forceinline__ bool acc_finite(ff a) { return isfinite(a.hi) && isfinite(a.lo); }
+
+__device__ __forceinline__ float sqrt_r(float x) { return sqrtf(x); }
+__device__ __forceinline__ double sqrt_r(double x) { return sqrt(x); }
+__device__ __forceinline__ float rcp_r(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_r(double x) { return 1.0 / x; }
+__device__ __forceinline__ float abs_r(float x) { return fabsf(x); }
+__device__ __forceinline__ double abs_r(double x) { return fabs(x); }
+__device__ __forceinline__ float max_r(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double max_r(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float exp_r(float x) { return __expf(x); }
+__device__ __forceinline__ double exp_r(double x) { return exp(x); }
+__device__ __forceinline__ float sin_r(float x) { return sinf(x); }
+__device__ __forceinline__ double sin_r(double x) { return sin(x); }
+__device__ __forceinline__ float cos_r(float x) { return cosf(x); }
+__device__ __forceinline__ double cos_r(double x) { return cos(x); }
+// H^{4/3} as H * cbrt(H)
+__device__ __forceinline__ float pow43_r(float h) { return h * cbrtf(h); }
+__device__ __forceinline__ double pow43_r(double h) { return h * cbrt(h); }
+
+// -------------------------------------------------------------------- precision policy ---
+struct Mixed {
+  using T = float;
+  using Acc = ff;
+  template <int P>
+  static constexpr int RV = rec_vec_mixed(P);
+  static constexpr int GV = 3;  // static geometry record, 16-byte units
+};
+struct Fp64 {
+  using T = double;
+  using Acc = double;
+  template <int P>
+  static constexpr int RV = rec_vec_fp64(P);
+  static constexpr int GV = 5;
+};
+
+template <int P, class Pol>
+struct Elem {
+  static constexpr int NP = np_of(P);
+  using T = typename Pol::T;
+  using Acc = typename Pol::Acc;
+  Acc zb, xb, yb;          // element means
+  T zs[NP - 1], xs[NP - 1], ys[NP - 1];  // modal coefficients 1..NP-1
+  T Hb;                    // mean depth
+  T hb1, hb2;              // bathymetry modes 1, 2
+  uint32_t flags;
+};
+
+template <int NV>
+struct Raw {
+  uint4 v[NV];
+};
+
+template <int NV>
+__device__ __forceinline__ void load_raw(const uint4* __restrict__ base, long long e, Raw<NV>& r) {
+  const uint4* p = base + e * NV;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) r.v[i] = __ldg(p + i);
+}
+template <int NV>
+__device__ __forceinline__ void store_raw(uint4* __restrict__ base, long long e, const Raw<NV>& r) {
+  uint4* p = base + e * NV;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) p[i] = r.v[i];
+}
+
+template <int P>
+__device__ __forceinline__ void unpack(const Raw<Mixed::RV<P>>& r, Elem<P, Mixed>& E) {
+  constexpr int NP = np_of(P), NS = NP - 1;
+  float f[4 * Mixed::RV<P>];
+#pragma unroll
+  for (int i = 0; i < Mixed::RV<P>; ++i) {
+    f[4 * i] = __uint_as_float(r.v[i].x);
+    f[4 * i + 1] = __uint_as_float(r.v[i].y);
+    f[4 * i + 2] = __uint_as_float(r.v[i].z);
+    f[4 * i + 3] = __uint_as_float(r.v[i].w);
+  }
+  E.zb = {f[0], f[1]};
+  E.xb = {f[2], f[3]};
+  E.yb = {f[4], f[5]};
+#pragma unroll
+  for (int m = 0; m < NS; ++m) {
+    E.zs[m] = f[6 + m];
+    E.xs[m] = f[6 + NS + m];
+    E.ys[m] = f[6 + 2 * NS + m];
+  }
+  constexpr int o = 6 + 3 * NS;
+  E.Hb = f[o];
+  E.flags = __float_as_uint(f[o + 1]);
+  E.hb1 = f[o + 2];
+  E.hb2 = f[o + 3];
+}
+template <int P>
+__device__ __forceinline__ void pack(const Elem<P, Mixed>& E, Raw<Mixed::RV<P>>& r) {
+  constexpr int NP = np_of(P), NS = NP - 1;
+  float f[4 * Mixed::RV<P>];
+#pragma unroll
+  for (int i = 0; i < 4 * Mixed::RV<P>; ++i) f[i] = 0.f;
+  f[0] = E.zb.hi; f[1] = E.zb.lo; f[2] = E.xb.hi; f[3] = E.xb.lo; f[4] = E.yb.hi; f[5] = E.yb.lo;
+#pragma unroll
+  for (int m = 0; m < NS; ++m) {
+    f[6 + m] = E.zs[m];
+    f[6 + NS + m] = E.xs[m];
+    f[6 + 2 * NS + m] = E.ys[m];
+  }
+  constexpr int o = 6 + 3 * NS;
+  f[o] = E.Hb;
+  f[o + 1] = __uint_as_float(E.flags);
+  f[o + 2] = E.hb1;
+  f[o + 3] = E.hb2;
+#pragma unroll
+  for (int i = 0; i < Mixed::RV<P>; ++i)
+    r.v[i] = make_uint4(__float_as_uint(f[4 * i]), __float_as_uint(f[4 * i + 1]), __float_as_uint(f[4 * i + 2]),
+                        __float_as_uint(f[4 * i + 3]));
+}
+
+__device__ __forceinline__ double u2d(unsigned lo, unsigned hi) {
+  return __hiloint2double((int)hi, (int)lo);
+}
+__device__ __forceinline__ void d2u(double d, unsigned& lo, unsigned& hi) {
+  lo = (unsigned)__double2loint(d);
+  hi = (unsigned)__double2hiint(d);
+}
+
+template <int P>
+__device__ __forceinline__ void unpack(const Raw<Fp64::RV<P>>& r, Elem<P, Fp64>& E) {
+  constexpr int NP = np_of(P), NS = NP - 1;
+  double f[2 * Fp64::RV<P>];
+#pragma unroll
+  for (int i = 0; i < Fp64::RV<P>; ++i) {
+    f[2 * i] = u2d(r.v[i].x, r.v[i].y);
+    f[2 * i + 1] = u2d(r.v[i].z, r.v[i].w);
+  }
+  E.zb = f[0];
+  E.xb = f[1];
+  E.yb = f[2];
+#pragma unroll
+  for (int m = 0; m < NS; ++m) {
+    E.zs[m] = f[3 + m];
+    E.xs[m] = f[3 + NS + m];
+    E.ys[m] = f[3 + 2 * NS + m];
+  }
+  constexpr int o = 3 + 3 * NS;
+  E.Hb = f[o];
+  E.flags = (uint32_t)__double2loint(f[o + 1]);
+  E.hb1 = f[o + 2];
+  E.hb2 = f[o + 3];
+}
+template <int P>
+__device__ __forceinline__ void pack(const Elem<P, Fp64>& E, Raw<Fp64::RV<P>>& r) {
+  constexpr int NP = np_of(P), NS = NP - 1;
+  double f[2 * Fp64::RV<P>];
+#pragma unroll
+  for (int i = 0; i < 2 * Fp64::RV<P>; ++i) f[i] = 0.0;
+  f[0] = E.zb; f[1] = E.xb; f[2] = E.yb;
+#pragma unroll
+  for (int m = 0; m < NS; ++m) {
+    f[3 + m] = E.zs[m];
+    f[3 + NS + m] = E.xs[m];
+    f[3 + 2 * NS + m] = E.ys[m];
+  }
+  constexpr int o = 3 + 3 * NS;
+  f[o] = E.Hb;
+  f[o + 1] = __hiloint2double(0, (int)E.flags);
+  f[o + 2] = E.hb1;
+  f[o + 3] = E.hb2;
+#pragma unroll
+  for (int i = 0; i < Fp64::RV<P>; ++i) {
+    d2u(f[2 * i], r.v[i].x, r.v[i].y);
+    d2u(f[2 * i + 1], r.v[i].z, r.v[i].w);
+  }
+}
+
+// static per-element geometry: scaled outward normals of the three local edges, mean
+// bathymetry, area and inverse area, Manning n
+template <class Pol>
+struct Geo {
+  using T = typename Pol::T;
+  using Acc = typename Pol::Acc;
+  T lnx[3], lny[3];
+  Acc hbm, A, invA;
+  T man;
+};
+__device__ __forceinline__ void load_geo(const uint4* __restrict__ g, long long e, const int4& nb, Geo<Mixed>& G) {
+  uint4 a = __ldg(g + 3 * e), b = __ldg(g + 3 * e + 1), c = __ldg(g + 3 * e + 2);
+  G.lnx[0] = __uint_as_float(a.x); G.lny[0] = __uint_as_float(a.y);
+  G.lnx[1] = __uint_as_float(a.z); G.lny[1] = __uint_as_float(a.w);
+  G.lnx[2] = __uint_as_float(b.x); G.lny[2] = __uint_as_float(b.y);
+  G.hbm = {__uint_as_float(b.z), __uint_as_float(b.w)};
+  G.A = {__uint_as_float(c.x), __uint_as_float(c.y)};
+  G.invA = {__uint_as_float(c.z), __uint_as_float(c.w)};
+  G.man = __int_as_float(nb.w);
+}
+__device__ __forceinline__ void load_geo(const uint4* __restrict__ g, long long e, const int4&, Geo<Fp64>& G) {
+  uint4 v[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) v[i] = __ldg(g + 5 * e + i);
+  G.lnx[0] = u2d(v[0].x, v[0].y); G.lny[0] = u2d(v[0].z, v[0].w);
+  G.lnx[1] = u2d(v[1].x, v[1].y); G.lny[1] = u2d(v[1].z, v[1].w);
+  G.lnx[2] = u2d(v[2].x, v[2].y); G.lny[2] = u2d(v[2].z, v[2].w);
+  G.hbm = u2d(v[3].x, v[3].y);
+  G.A = u2d(v[3].z, v[3].w);
+  G.invA = u2d(v[4].x, v[4].y);
+  G.man = u2d(v[4].z, v[4].w);
+}
+
+// reference tables per degree (index P): FP32 copy for the mixed path, FP64 for the FP64 path
+// and for the depth test near H0.  Uploaded once per device by upload_tables().
+static __constant__ RefTab<float> c_tab_f[3];
+static __constant__ RefTab<double> c_tab_d[3];
+
+template <class T, int P>
+__device__ __forceinline__ const RefTab<T>& ctab();
+template <>
+__device__ __forceinline__ const RefTab<float>& ctab<float, 1>() { return c_tab_f[1]; }
+template <>
+__device__ __forceinline__ const RefTab<float>& ctab<float, 2>() { return c_tab_f[2]; }
+template <>
+__device__ __forceinline__ const RefTab<double>& ctab<double, 1>() { return c_tab_d[1]; }
+template <>
+__device__ __forceinline__ const RefTab<double>& ctab<double, 2>() { return c_tab_d[2]; }
+
+// trace of an element at one point: d = zeta - mean(zeta), depth, discharge
+template <class T>
+struct Trace {
+  T d, H, qx, qy;
+};
+
+template <int P, class Pol>
+__device__ __forceinline__ Trace<typename Pol::T> trace_at(const Elem<P, Pol>& E, const typename Pol::T* phi) {
+  using T = typename Pol::T;
+  constexpr int NS = np_of(P) - 1;
+  Trace<T> t;
+  T d = 0, qx = acc_r(E.xb), qy = acc_r(E.yb);
+#pragma unroll
+  for (int m = 0; m < NS; ++m) {
+    d = fma(E.zs[m], phi[m + 1], d);
+    qx = fma(E.xs[m], phi[m + 1], qx);
+    qy = fma(E.ys[m], phi[m + 1], qy);
+  }
+  T hdev = fma(E.hb1, phi[1], E.hb2 * phi[2]);
+  t.d = d;
+  t.H = E.Hb + (d + hdev);
+  t.qx = qx;
+  t.qy = qy;
+  return t;
+}
+
+// canonical flux across an edge with unit normal n from L to R; returns the mass flux and the
+// advective + dissipative momentum flux (the pressure part is added per side)
+template <int FLUX, class T>
+__device__ __forceinline__ void edge_flux(const Trace<T>& L, const Trace<T>& R, T dcRL, T nx, T ny, T g, T H0, T& fz,
+                                          T& fx, T& fy) {
+  T HsL = max_r(L.H, H0), HsR = max_r(R.H, H0);
+  T iL = rcp_r(HsL), iR = rcp_r(HsR);
+  T uL = L.qx * iL, vL = L.qy * iL, uR = R.qx * iR, vR = R.qy * iR;
+  T unL = uL * nx + vL * ny, unR = uR * nx + vR * ny;
+  T mL = L.qx * nx + L.qy * ny, mR = R.qx * nx + R.qy * ny;
+  T dz = (R.d - L.d) + dcRL;
+  T dqx = R.qx - L.qx, dqy = R.qy - L.qy;
+  T cx = T(0.5) * (L.qx * unL + R.qx * unR);
+  T cy = T(0.5) * (L.qy * unL + R.qy * unR);
+  T cz = T(0.5) * (mL + mR);
+  if (FLUX == 1) {  // local Lax-Friedrichs
+    T lam = max_r(abs_r(unL) + sqrt_r(g * HsL), abs_r(unR) + sqrt_r(g * HsR));
+    fz = cz - T(0.5) * lam * dz;
+    fx = cx - T(0.5) * lam * dqx;
+    fy = cy - T(0.5) * lam * dqy;
+    return;
+  }
+  // Roe: averages (arithmetic depth, sqrt-depth-weighted velocity), eigen-decomposition
+  T sL = sqrt_r(HsL), sR = sqrt_r(HsR);
+  T is = rcp_r(sL + sR);
+  T ut = (sL * uL + sR * uR) * is, vt = (sL * vL + sR * vR) * is;
+  T c = sqrt_r(g * T(0.5) * (HsL + HsR));
+  T ic = rcp_r(c);
+  T utn = ut * nx + vt * ny, utt = vt * nx - ut * ny;
+  T dqn = dqx * nx + dqy * ny, dqt = dqy * nx - dqx * ny;
+  T w = (dqn - utn * dz) * ic;
+  T a1 = T(0.5) * (dz - w), a3 = T(0.5) * (dz + w), a2 = dqt - utt * dz;
+  T l1 = abs_r(utn - c) * a1, l2 = abs_r(utn) * a2, l3 = abs_r(utn + c) * a3;
+  T D0 = l1 + l3;
+  T D1 = l1 * (ut - c * nx) - l2 * ny + l3 * (ut + c * nx);
+  T D2 = l1 * (vt - c * ny) + l2 * nx + l3 * (vt + c * ny);
+  fz = cz - T(0.5) * D0;
+  fx = cx - T(0.5) * D1;
+  fy = cy - T(0.5) * D2;
+}
+
+// pressure difference P - P_c with P_c the pressure at the reference elevation c:
+// g/2 (zeta - c)(zeta + c + 2 hb) = g/2 d (2 H - d)
+template <class T>
+__device__ __forceinline__ T pdev(T d, T H, T g) {
+  return T(0.5) * g * d * (T(2) * H - d);
+}
+
+// FP64 positive-depth operator on the linear part (Sec. 2.4).  zs/xs/ys are modes 1.. of
+// zeta/qx/qy (double, in place); zbar/xbar/ybar means; returns true if the element is dry.
+template <int P>
+__device__ bool positivity_fp64(double zbar, double& xbar, double& ybar, double* zs, double* xs, double* ys,
+                                const double hbv[3], double H0, const RefTab<double>& tb, bool& changed) {
+  constexpr int NP = np_of(P), NS = NP - 1;
+  double H[3];
+  changed = false;
+  for (int pass = 0; pass < 2; ++pass) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      double z = zbar;
+#pragma unroll
+      for (int m = 0; m < NS; ++m) z = fma(zs[m], tb.vphi[i][m + 1], z);
+      H[i] = z + hbv[i];
+    }
+    if (pass == 0 && P >= 2 && (H[0] < H0 || H[1] < H0 || H[2] < H0)) {
+#pragma unroll
+      for (int m = 2; m < NS; ++m) zs[m] = xs[m] = ys[m] = 0.0;  // truncate to p = 1
+      changed = true;
+      continue;
+    }
+    break;
+  }
+  if (H[0] >= H0 && H[1] >= H0 && H[2] >= H0) return false;
+  changed = true;
+  double Hbar = (H[0] + H[1] + H[2]) / 3.0;
+  double Ho[3];
+  bool dry[3];
+  if (Hbar <= H0) {
+    Ho[0] = Ho[1] = Ho[2] = Hbar;
+    dry[0] = dry[1] = dry[2] = true;
+  } else {
+    int i0 = 0, i1 = 1, i2 = 2, t;
+    // stable sort of the three depths (ties by vertex index)
+    if (H[i1] < H[i0]) { t = i0; i0 = i1; i1 = t; }
+    if (H[i2] < H[i1]) { t = i1; i1 = i2; i2 = t; }
+    if (H[i1] < H[i0] || (H[i1] == H[i0] && i1 < i0)) { t = i0; i0 = i1; i1 = t; }
+    if (H[i2] == H[i1] && i2 < i1) { t = i1; i1 = i2; i2 = t; }
+    double d = H0 - H[i0];
+    Ho[i0] = H0;
+    if (H[i1] - 0.5 * d >= H0) {
+      Ho[i1] = H[i1] - 0.5 * d;
+      Ho[i2] = H[i2] - 0.5 * d;
+    } else {
+      Ho[i1] = H0;
+      Ho[i2] = H[i2] - (H0 - H[i0]) - (H0 - H[i1]);
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) dry[i] = Ho[i] < H0;
+  }
+  // rebuild the linear part of zeta from the redistributed vertex values; the mean is kept
+  double zv[3] = {Ho[0] - hbv[0], Ho[1] - hbv[1], Ho[2] - hbv[2]};
+  if (NS >= 2) {
+    zs[0] = tb.vinv[0][0] * zv[0] + tb.vinv[0][1] * zv[1] + tb.vinv[0][2] * zv[2];
+    zs[1] = tb.vinv[1][0] * zv[0] + tb.vinv[1][1] * zv[1] + tb.vinv[1][2] * zv[2];
+  }
+  int nd = (int)dry[0] + (int)dry[1] + (int)dry[2];
+  if (nd == 3) {
+    xbar = ybar = 0.0;
+#pragma unroll
+    for (int m = 0; m < NS; ++m) xs[m] = ys[m] = 0.0;
+  } else if (nd > 0 && NS >= 2) {
+    double qx[3], qy[3], sx = 0.0, sy = 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      qx[i] = xbar + xs[0] * tb.vphi[i][1] + xs[1] * tb.vphi[i][2];
+      qy[i] = ybar + ys[0] * tb.vphi[i][1] + ys[1] * tb.vphi[i][2];
+      if (dry[i]) { sx += qx[i]; sy += qy[i]; qx[i] = qy[i] = 0.0; }
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      if (!dry[i]) { qx[i] += sx / (3 - nd); qy[i] += sy / (3 - nd); }
+    xs[0] = tb.vinv[0][0] * qx[0] + tb.vinv[0][1] * qx[1] + tb.vinv[0][2] * qx[2];
+    xs[1] = tb.vinv[1][0] * qx[0] + tb.vinv[1][1] * qx[1] + tb.vinv[1][2] * qx[2];
+    ys[0] = tb.vinv[0][0] * qy[0] + tb.vinv[0][1] * qy[1] + tb.vinv[0][2] * qy[2];
+    ys[1] = tb.vinv[1][0] * qy[0] + tb.vinv[1][1] * qy[1] + tb.vinv[1][2] * qy[2];
+  }
+  return nd > 0;
+}
+
+// positive-depth operator on a freshly combined element; sets E.Hb and the dry flag
+template <int P, class Pol>
+__device__ __forceinline__ void apply_positivity(Elem<P, Pol>& E, const Geo<Pol>& G, long long e,
+                                                 const StageArgs<Pol>& a, int* err) {
+  using T = typename Pol::T;
+  constexpr int NS = np_of(P) - 1;
+  const RefTab<T>& tab = ctab<T, P>();
+  T H0 = a.H0;
+  bool need64 = true;
+  typename Pol::Acc Hbar = acc_add(E.zb, G.hbm);
+  T Hb = acc_r(Hbar);
+  if (sizeof(T) == 4) {
+    // FP32 filter: if every vertex depth is clearly above H0 the operator is the identity
+    T hmin = T(3.0e38), bound = abs_r(Hb);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      T s = Hb, b = 0;
+#pragma unroll
+      for (int m = 0; m < NS; ++m) {
+        s = fma(E.zs[m], tab.vphi[i][m + 1], s);
+        b += abs_r(E.zs[m] * tab.vphi[i][m + 1]);
+      }
+      s = fma(E.hb1, tab.vphi[i][1], s);
+      s = fma(E.hb2, tab.vphi[i][2], s);
+      b += abs_r(E.hb1 * tab.vphi[i][1]) + abs_r(E.hb2 * tab.vphi[i][2]);
+      hmin = fminf(hmin, s);
+      bound = fmaxf(bound, b);
+    }
+    need64 = !(hmin - T(4.0e-6) * (abs_r(Hb) + bound) > H0);
+  }
+  bool dry = false;
+  if (need64) {
+    double zs[NS], xs[NS], ys[NS];
+#pragma unroll
+    for (int m = 0; m < NS; ++m) {
+      zs[m] = (double)E.zs[m];
+      xs[m] = (double)E.xs[m];
+      ys[m] = (double)E.ys[m];
+    }
+    const int4 nd = __ldg(a.nodes + e);
+    double hbv[3] = {a.hb_nodal[nd.x], a.hb_nodal[nd.y], a.hb_nodal[nd.z]};
+    double xb = acc_d(E.xb), yb = acc_d(E.yb);
+    bool changed;
+    dry = positivity_fp64<P>(acc_d(E.zb), xb, yb, zs, xs, ys, hbv, (double)H0, c_tab_d[P], changed);
+    if (changed) {
+#pragma unroll
+      for (int m = 0; m < NS; ++m) {
+        E.zs[m] = (T)zs[m];
+        E.xs[m] = (T)xs[m];
+        E.ys[m] = (T)ys[m];
+      }
+      if (dry) {
+        acc_set(E.xb, xb);
+        acc_set(E.yb, yb);
+      }
+    }
+    if (acc_d(Hbar) < 0.0) atomicOr(err, ERR_NEGDEPTH);
+  }
+  E.Hb = Hb;
+  E.flags = dry ? FLAG_DRY : 0u;
+  if (!acc_finite(E.zb) || !acc_finite(E.xb) || !acc_finite(E.yb)) atomicOr(err, ERR_NONFINITE);
+}
+
+// --------------------------------------------------------------- block reduction helpers ---
+__device__ __forceinline__ void warp_reduce2(double& a, double& b) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+}
+__device__ __forceinline__ ff shfl_ff(ff v, int o) {
+  return {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+}
+__device__ __forceinline__ void warp_reduce2(ff& a, ff& b) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a = ff_add(a, shfl_ff(a, o));
+    b = ff_add(b, shfl_ff(b, o));
+  }
+}
+
+// ------------------------------------------------------------------------ stage kernel ----
+template <int P, int FLUX, class Pol>
+__global__ void __launch_bounds__(256) stage_kernel(const StageArgs<Pol> a) {
+  using T = typename Pol::T;
+  using Acc = typename Pol::Acc;
+  constexpr int NP = np_of(P), NS = NP - 1, NG = P + 1;
+  constexpr int RV = Pol::template RV<P>;
+  constexpr int NQ = (P == 0) ? 1 : 7;
+  const RefTab<T>& tab = ctab<T, P>();
+
+  __shared__ int s_tile;
+  __shared__ T s_zbc[MAXSEG];
+  __shared__ T s_storm[2];
+  __shared__ double s_t;
+  __shared__ Acc s_red[2][8];
+  __shared__ T s_ephi[3][NG][NP];  // edge basis values, read at neighbour-dependent indices
+
+  const int tid = threadIdx.x;
+  for (int i = tid; i < 3 * NG * NP; i += blockDim.x) {
+    const int j = i / (NG * NP), k = (i / NP) % NG, m = i % NP;
+    s_ephi[j][k][m] = tab.ephi[j][k][m];
+  }
+  for (int iter = 0;; ++iter) {
+    int tile;
+    if (a.persistent) {
+      if (tid == 0) s_tile = (int)atomicAdd(&a.ctl->tile_counter, 1u);
+      __syncthreads();
+      tile = s_tile;
+      __syncthreads();
+    } else {
+      if (iter > 0) break;
+      tile = blockIdx.x;
+    }
+    if (tile >= a.ntiles) break;
+    const ScenDev& S = a.scen[a.tile_scen[tile]];
+    // per-tile uniform quantities: stage time, storm centre, tidal elevations
+    if (tid == 0) {
+      const double t = S.t0 + ((double)a.ctl->step + a.cst) * S.dt;
+      s_t = t;
+      if (S.rain_kind == 2) {
+        const double tt = t - S.storm[7];
+        s_storm[0] = (T)(S.storm[0] + S.storm[3] * tt * cos(S.storm[2]));
+        s_storm[1] = (T)(S.storm[1] + S.storm[3] * tt * sin(S.storm[2]));
+      }
+      for (int k = 0; k < S.nseg && k < MAXSEG; ++k)
+        s_zbc[k] = (T)(S.tamp[k] * sin(6.283185307179586 * t / S.tper[k] + S.tpha[k]));
+    }
+    __syncthreads();
+
+    const long long e = (long long)tile * blockDim.x + tid;
+    Acc rain_vol = acc_make<Acc>(0.f, 0.f, 0.0), bdry_vol = acc_make<Acc>(0.f, 0.f, 0.0);
+    if (e < S.elem_end) {
+      const T g = a.g, H0 = a.H0;
+      const int4 nb = __ldg(a.nbr + e);
+      Geo<Pol> G;
+      load_geo(a.geo, e, nb, G);
+      Raw<RV> rme;
+      load_raw<RV>(a.in, e, rme);
+      Elem<P, Pol> E;
+      unpack<P>(rme, E);
+      const bool dry_me = (E.flags & FLAG_DRY) != 0;
+      const T detJ = T(0.5) * acc_r(G.A);
+      const T idetJ = T(2) * acc_r(G.invA);
+      // inverse Jacobian from the edge vectors: t0 = x1 - x0 = 2 (xr, yr), t2 = x0 - x2 = -2 (xs, ys)
+      // and ln_j = (t_j.y, -t_j.x)
+      const T xr = T(-0.5) * G.lny[0], yr = T(0.5) * G.lnx[0];
+      const T xs = T(0.5) * G.lny[2], ys = T(-0.5) * G.lnx[2];
+      const T rx = ys * idetJ, ry = -xs * idetJ, sx = -yr * idetJ, sy = xr * idetJ;
+
+      // right-hand side accumulators: integrals of the weak form against each basis function
+      T Rz[NP], Rx[NP], Ry[NP];
+#pragma unroll
+      for (int m = 0; m < NP; ++m) Rz[m] = Rx[m] = Ry[m] = 0;
+      Acc massout = acc_make<Acc>(0.f, 0.f, 0.0);  // edge mass outflow (volume per second)
+
+      // ---- 1. edge integrals
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const int code = (j == 0) ? nb.x : (j == 1 ? nb.y : nb.z);
+        const T lnx = G.lnx[j], lny = G.lny[j];
+        const T len = sqrt_r(lnx * lnx + lny * lny);
+        const T il = rcp_r(len);
+        const T nx = lnx * il, ny = lny * il;
+        T Fz[NG], Fx[NG], Fy[NG];  // flux along my outward normal at my edge points
+        Trace<T> tm[NG];
+#pragma unroll
+        for (int k = 0; k < NG; ++k) tm[k] = trace_at<P, Pol>(E, tab.ephi[j][k]);
+        if (code >= 0) {
+          const long long ne_ = code >> 2;
+          const int jn = code & 3;
+          Raw<RV> rnb;
+          load_raw<RV>(a.in, ne_, rnb);
+          Elem<P, Pol> N;
+          unpack<P>(rnb, N);
+          const bool me_L = e < ne_;
+          const T sgn = me_L ? T(1) : T(-1);
+          const T dc_nm = acc_diff(N.zb, E.zb);                 // c_nb - c_me
+          const T dcRL = me_L ? dc_nm : acc_diff(E.zb, N.zb);   // c_R - c_L
+          const T cnx = sgn * nx, cny = sgn * ny;               // L's outward normal
+          T fzc[NG], fxc[NG], fyc[NG];                          // canonical fluxes at my points
+          Trace<T> tn[NG];
+#pragma unroll
+          for (int k = 0; k < NG; ++k) {
+            tn[k] = trace_at<P, Pol>(N, s_ephi[jn][NG - 1 - k]);  // same physical point
+            const Trace<T> tL = me_L ? tm[k] : tn[k];
+            const Trace<T> tR = me_L ? tn[k] : tm[k];
+            edge_flux<FLUX, T>(tL, tR, dcRL, cnx, cny, g, H0, fzc[k], fxc[k], fyc[k]);
+          }
+          // edge mass flux integral in L's point order (identical bits on both sides)
+          T ecanon = 0;
+#pragma unroll
+          for (int kc = 0; kc < NG; ++kc) {
+            const T f = me_L ? fzc[kc] : fzc[NG - 1 - kc];
+            ecanon = fma(tab.gw[kc], f, ecanon);
+          }
+          ecanon = ecanon * (T(0.5) * len);
+          const bool dry_nb = (N.flags & FLAG_DRY) != 0;
+          const bool dry_L = me_L ? dry_me : dry_nb;
+          const bool dry_R = me_L ? dry_nb : dry_me;
+          const bool closed = (dry_L && ecanon > T(0)) || (dry_R && ecanon < T(0));
+          if (!closed) {
+            massout = acc_addr(massout, sgn * ecanon);
+#pragma unroll
+            for (int k = 0; k < NG; ++k) {
+              const T dn = tn[k].d + dc_nm;  // neighbour elevation relative to my mean
+              const T p = T(0.5) * (pdev(tm[k].d, tm[k].H, g) + pdev(dn, tn[k].H, g));
+              Fz[k] = sgn * fzc[k];
+              Fx[k] = sgn * fxc[k] + p * nx;
+              Fy[k] = sgn * fyc[k] + p * ny;
+            }
+          } else {
+#pragma unroll
+            for (int k = 0; k < NG; ++k) {  // closed edge: wall built from my own trace
+              const Trace<T> t = tm[k];
+              const T qn = t.qx * nx + t.qy * ny;
+              Trace<T> gh = t;
+              gh.qx = t.qx - T(2) * qn * nx;
+              gh.qy = t.qy - T(2) * qn * ny;
+              T fz, fx, fy;
+              edge_flux<FLUX, T>(t, gh, T(0), nx, ny, g, H0, fz, fx, fy);
+              const T p = pdev(t.d, t.H, g);
+              Fz[k] = 0;
+              Fx[k] = fx + p * nx;
+              Fy[k] = fy + p * ny;
+            }
+          }
+        } else {
+          // boundary: land (-1) mirrors the normal discharge and carries no mass; ocean
+          // (-2 - seg) takes the tidal elevation with the interior discharge
+          const bool land = (code == -1);
+          const int seg = -2 - code;
+          const T zbc = land ? T(0) : s_zbc[seg < MAXSEG ? seg : 0];
+          const T dgh = land ? T(0) : acc_r(acc_addr(acc_neg(E.zb), zbc));  // ghost zeta - c
+          T ebd = 0;
+#pragma unroll
+          for (int k = 0; k < NG; ++k) {
+            const Trace<T> t = tm[k];
+            Trace<T> gh = t;
+            if (land) {
+              const T qn = t.qx * nx + t.qy * ny;
+              gh.qx = t.qx - T(2) * qn * nx;
+              gh.qy = t.qy - T(2) * qn * ny;
+            } else {
+              gh.H = t.H + (dgh - t.d);
+              gh.d = dgh;
+            }
+            T fz, fx, fy;
+            edge_flux<FLUX, T>(t, gh, T(0), nx, ny, g, H0, fz, fx, fy);
+            const T p = T(0.5) * (pdev(t.d, t.H, g) + pdev(gh.d, gh.H, g));
+            Fz[k] = land ? T(0) : fz;
+            Fx[k] = fx + p * nx;
+            Fy[k] = fy + p * ny;
+            ebd = fma(tab.gw[k], Fz[k], ebd);
+          }
+          ebd = ebd * (T(0.5) * len);
+          if (!land && dry_me && ebd > T(0)) {  // closed: a dry element loses no water
+            ebd = 0;
+#pragma unroll
+            for (int k = 0; k < NG; ++k) {
+              const Trace<T> t = tm[k];
+              const T qn = t.qx * nx + t.qy * ny;
+              Trace<T> gh = t;
+              gh.qx = t.qx - T(2) * qn * nx;
+              gh.qy = t.qy - T(2) * qn * ny;
+              T fz, fx, fy;
+              edge_flux<FLUX, T>(t, gh, T(0), nx, ny, g, H0, fz, fx, fy);
+              const T p = pdev(t.d, t.H, g);
+              Fz[k] = 0;
+              Fx[k] = fx + p * nx;
+              Fy[k] = fy + p * ny;
+            }
+          }
+          massout = acc_addr(massout, ebd);
+          bdry_vol = acc_addr(bdry_vol, -ebd);
+        }
+        // lift: R_m -= sum_k w_k (len/2) F_k phi_m(edge j, point k)
+#pragma unroll
+        for (int k = 0; k < NG; ++k) {
+          const T wk = tab.gw[k] * (T(0.5) * len);
+#pragma unroll
+          for (int m = 0; m < NP; ++m) {
+            const T ph = wk * tab.ephi[j][k][m];
+            if (m > 0) Rz[m] = fma(-ph, Fz[k], Rz[m]);
+            Rx[m] = fma(-ph, Fx[k], Rx[m]);
+            Ry[m] = fma(-ph, Fy[k], Ry[m]);
+          }
+        }
+      }
+
+      // ---- 2. forcing: element rain = mean of the three nodal rates (Eq. rain)
+      T Re = 0;
+      if (S.rain_kind == 1) {
+        Re = a.rain_e[e];
+      } else if (S.rain_kind >= 2) {
+        const int4 nd = __ldg(a.nodes + e);
+        T acc = 0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          const int n = (i == 0) ? nd.x : (i == 1 ? nd.y : nd.z);
+          const T px = a.node_xy[2 * (long long)n], py = a.node_xy[2 * (long long)n + 1];
+          if (S.rain_kind == 2) {
+            const T dx = px - s_storm[0], dy = py - s_storm[1];
+            const T r = sqrt_r(dx * dx + dy * dy);
+            const T rp = (T)S.storm[4], rm = (T)S.storm[5], re = (T)S.storm[6];
+            acc += (r < rm) ? rp * (T(0.5) + T(0.5) * r / rm) : rp * exp_r(-(r - rm) / re);
+          } else {
+            T gx = (T)((px - S.gx0) / S.gdx), gy = (T)((py - S.gy0) / S.gdy);
+            T gt = (T)((s_t - S.gt0) / S.gdt);
+            gx = fmin(fmax(gx, T(0)), T(S.gnx - 1));
+            gy = fmin(fmax(gy, T(0)), T(S.gny - 1));
+            gt = fmin(fmax(gt, T(0)), T(S.gnt - 1));
+            const int ix = min(max((int)floor(gx), 0), max(S.gnx - 2, 0));
+            const int iy = min(max((int)floor(gy), 0), max(S.gny - 2, 0));
+            const int it = min(max((int)floor(gt), 0), max(S.gnt - 2, 0));
+            const T fx = gx - T(ix), fy = gy - T(iy), ft = gt - T(it);
+            const int ix1 = S.gnx > 1 ? ix + 1 : ix, iy1 = S.gny > 1 ? iy + 1 : iy;
+            T val[2];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+              const int kk = S.gnt > 1 ? it + q : 0;
+              const float* Gr = S.grid + (size_t)kk * S.gnx * S.gny;
+              const T v00 = Gr[(size_t)iy * S.gnx + ix], v10 = Gr[(size_t)iy * S.gnx + ix1];
+              const T v01 = Gr[(size_t)iy1 * S.gnx + ix], v11 = Gr[(size_t)iy1 * S.gnx + ix1];
+              val[q] = (T(1) - fy) * ((T(1) - fx) * v00 + fx * v10) + fy * ((T(1) - fx) * v01 + fx * v11);
+            }
+            acc += ((T(1) - ft) * val[0] + ft * val[1]) / T(3.6e6);
+          }
+        }
+        Re = acc / T(3);
+      }
+
+      // ---- 3. area integrals
+      // the linear modes have constant gradients: grad(hb) = hb1 grad(phi_1) + hb2 grad(phi_2)
+      const T g1x = tab.qdr[0][1] * rx + tab.qds[0][1] * sx, g1y = tab.qdr[0][1] * ry + tab.qds[0][1] * sy;
+      const T g2x = tab.qdr[0][2] * rx + tab.qds[0][2] * sx, g2y = tab.qdr[0][2] * ry + tab.qds[0][2] * sy;
+      const T hbx = E.hb1 * g1x + E.hb2 * g2x, hby = E.hb1 * g1y + E.hb2 * g2y;
+      const T cfm = (a.friction == 0) ? g * G.man * G.man : a.cf;
+      T vx[3] = {0, 0, 0}, vy[3] = {0, 0, 0};
+      if (S.press) {
+        const int4 nd = __ldg(a.nodes + e);
+        vx[0] = a.node_xy[2 * (long long)nd.x]; vy[0] = a.node_xy[2 * (long long)nd.x + 1];
+        vx[1] = a.node_xy[2 * (long long)nd.y]; vy[1] = a.node_xy[2 * (long long)nd.y + 1];
+        vx[2] = a.node_xy[2 * (long long)nd.z]; vy[2] = a.node_xy[2 * (long long)nd.z + 1];
+      }
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const Trace<T> t = trace_at<P, Pol>(E, tab.qphi[q]);
+        const T Hs = max_r(t.H, H0);
+        const T iH = rcp_r(Hs);
+        const T u = t.qx * iH, v = t.qy * iH;
+        const T pp = pdev(t.d, t.H, g);
+        T tau = 0;
+        if (a.friction == 0) tau = cfm * sqrt_r(u * u + v * v) / pow43_r(Hs);
+        else if (a.friction == 1) tau = cfm * sqrt_r(u * u + v * v) * iH;
+        T Fx = 0, Fy = 0;
+        if (S.press) {
+          const T px = tab.ql[q][0] * vx[0] + tab.ql[q][1] * vx[1] + tab.ql[q][2] * vx[2];
+          const T py = tab.ql[q][0] * vy[0] + tab.ql[q][1] * vy[1] + tab.ql[q][2] * vy[2];
+          const T dx = px - (T)S.ps[0], dy = py - (T)S.ps[1], s2 = (T)(S.ps[2] * S.ps[2]);
+          const T eta = (T)S.ps[3] * exp_r(-(dx * dx + dy * dy) / (T(2) * s2));
+          Fx = g * t.H * (-eta * dx / s2);
+          Fy = g * t.H * (-eta * dy / s2);
+        }
+        const T sx_ = g * t.d * hbx - tau * t.qx + Fx;
+        const T sy_ = g * t.d * hby - tau * t.qy + Fy;
+        const T fxx = t.qx * u + pp, fyx = t.qx * v;
+        const T fxy = t.qy * u, fyy = t.qy * v + pp;
+        const T wq = tab.qw[q] * detJ;
+#pragma unroll
+        for (int m = 0; m < NP; ++m) {
+          const T dxm = tab.qdr[q][m] * rx + tab.qds[q][m] * sx;
+          const T dym = tab.qdr[q][m] * ry + tab.qds[q][m] * sy;
+          const T ph = tab.qphi[q][m];
+          if (m > 0) Rz[m] = fma(wq, dxm * t.qx + dym * t.qy, Rz[m]);
+          Rx[m] = fma(wq, dxm * fxx + dym * fyx + ph * sx_, Rx[m]);
+          Ry[m] = fma(wq, dxm * fxy + dym * fyy + ph * sy_, Ry[m]);
+        }
+      }
+      if (dry_me) {  // the momentum equations are not advanced on dry elements
+#pragma unroll
+        for (int m = 0; m < NP; ++m) Rx[m] = Ry[m] = 0;
+      }
+
+      // ---- 4. Shu-Osher combination: out = a_n w^n + a_in w^in + beta dt M^{-1} R
+      const Acc an = acc_make<Acc>(a.a_n_hi, a.a_n_lo, a.a_n);
+      const Acc ain = acc_make<Acc>(a.a_in_hi, a.a_in_lo, a.a_in);
+      const Acc bdt = acc_make<Acc>(S.bdt_hi[a.stage], S.bdt_lo[a.stage], S.bdt[a.stage]);
+      // mean rates: d(zeta_bar)/dt = R_e - massout / A;  d(q_bar)/dt = phi_0 R_0 / detJ
+      const Acc zrate = acc_addr(acc_neg(acc_mul(massout, G.invA)), Re);
+      const T xrate = tab.phi0 * Rx[0] * idetJ, yrate = tab.phi0 * Ry[0] * idetJ;
+      Elem<P, Pol> O = E;
+      const bool has_n = (a.a_n != 0.0);
+      Elem<P, Pol> Wn = E;
+      if (has_n) {
+        Raw<RV> rn;
+        load_raw<RV>(a.wn, e, rn);
+        unpack<P>(rn, Wn);
+      }
+      {
+        Acc z = acc_mul(ain, E.zb), x = acc_mul(ain, E.xb), y = acc_mul(ain, E.yb);
+        if (has_n) {
+          z = acc_add(z, acc_mul(an, Wn.zb));
+          x = acc_add(x, acc_mul(an, Wn.xb));
+          y = acc_add(y, acc_mul(an, Wn.yb));
+        }
+        O.zb = acc_add(z, acc_mul(bdt, zrate));
+        O.xb = acc_addr(x, acc_r(bdt) * xrate);
+        O.yb = acc_addr(y, acc_r(bdt) * yrate);
+      }
+      const T an_r = (T)a.a_n, ain_r = (T)a.a_in, bdt_r = acc_r(bdt);
+#pragma unroll
+      for (int m = 0; m < NS; ++m) {
+        T z = ain_r * E.zs[m] + bdt_r * (Rz[m + 1] * idetJ);
+        T x = ain_r * E.xs[m] + bdt_r * (Rx[m + 1] * idetJ);
+        T y = ain_r * E.ys[m] + bdt_r * (Ry[m + 1] * idetJ);
+        if (has_n) {
+          z = fma(an_r, Wn.zs[m], z);
+          x = fma(an_r, Wn.xs[m], x);
+          y = fma(an_r, Wn.ys[m], y);
+        }
+        O.zs[m] = z;
+        O.xs[m] = x;
+        O.ys[m] = y;
+      }
+
+      // ---- 5. positive-depth operator, store
+      apply_positivity<P, Pol>(O, G, e, a, &a.ctl->err);
+      Raw<RV> ro;
+      pack<P>(O, ro);
+      store_raw<RV>(a.out, e, ro);
+
+      // ---- 6. ledger contribution of the element
+      rain_vol = acc_mulr(G.A, Re);
+    }
+    if (!a.tune) {
+      warp_reduce2(rain_vol, bdry_vol);
+      const int lane = tid & 31, wid = tid >> 5;
+      if (lane == 0) {
+        s_red[0][wid] = rain_vol;
+        s_red[1][wid] = bdry_vol;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        Acc r = s_red[0][0], b = s_red[1][0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+          r = acc_add(r, s_red[0][w]);
+          b = acc_add(b, s_red[1][w]);
+        }
+        const double wdt = S.bw[a.stage] * S.dt;
+        a.ledger[2 * tile] += wdt * acc_d(r);
+        a.ledger[2 * tile + 1] += wdt * acc_d(b);
+      }
+    }
+    __syncthreads();
+  }
+  // launch epilogue: the last CTA to finish resets the work counter and, after the final stage
+  // of a step, advances the step counter read by the next step's CTAs
+  if (tid == 0) {
+    __threadfence();
+    const unsigned t = atomicAdd(&a.ctl->ticket, 1u);
+    if (t == gridDim.x - 1) {
+      a.ctl->ticket = 0;
+      a.ctl->tile_counter = 0;
+      if (a.last && !a.tune) a.ctl->step += 1ull;
+      __threadfence();
+    }
+  }
+}
+
+}  // namespace dg
+
+namespace dg {
+
+// ------------------------------------------------------------------ auxiliary kernels ----
+template <int P, class Pol>
+__global__ void __launch_bounds__(256) prepare_kernel(const StageArgs<Pol> a, long long begin, long long end) {
+  constexpr int RV = Pol::template RV<P>;
+  for (long long e = begin + blockIdx.x * (long long)blockDim.x + threadIdx.x; e < end;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int4 nb = __ldg(a.nbr + e);
+    Geo<Pol> G;
+    load_geo(a.geo, e, nb, G);
+    Raw<RV> r;
+    load_raw<RV>(a.in, e, r);
+    Elem<P, Pol> E;
+    unpack<P>(r, E);
+    apply_positivity<P, Pol>(E, G, e, a, &a.ctl->err);
+    pack<P>(E, r);
+    store_raw<RV>(a.out, e, r);
+  }
+}
+
+__device__ __forceinline__ void neu_add(double& s, double& c, double v) {
+  const double t = s + v;
+  c += (fabs(s) >= fabs(v)) ? (s - t) + v : (v - t) + s;
+  s = t;
+}
+// merge two compensated sums (s, c) + (s2, c2)
+__device__ __forceinline__ void neu_merge(double& s, double& c, double s2, double c2) {
+  neu_add(s, c, s2);
+  c += c2;
+}
+
+template <int P, class Pol>
+__global__ void __launch_bounds__(256) volume_kernel(const uint4* rec, const uint4* geo, long long begin,
+                                                     long long end, double* partials) {
+  constexpr int RV = Pol::template RV<P>;
+  double s0 = 0, c0 = 0, s1 = 0, c1 = 0;
+  for (long long e = begin + blockIdx.x * (long long)blockDim.x + threadIdx.x; e < end;
+       e += (long long)gridDim.x * blockDim.x) {
+    Geo<Pol> G;
+    load_geo(geo, e, make_int4(0, 0, 0, 0), G);
+    Raw<RV> r;
+    load_raw<RV>(rec, e, r);
+    Elem<P, Pol> E;
+    unpack<P>(r, E);
+    const double A = acc_d(G.A), z = acc_d(E.zb);
+    neu_add(s0, c0, A * z);
+    neu_add(s1, c1, A * z + A * acc_d(G.hbm));
+  }
+  __shared__ double sh[4][8];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double a0 = __shfl_xor_sync(0xffffffffu, s0, o), b0 = __shfl_xor_sync(0xffffffffu, c0, o);
+    const double a1 = __shfl_xor_sync(0xffffffffu, s1, o), b1 = __shfl_xor_sync(0xffffffffu, c1, o);
+    neu_merge(s0, c0, a0, b0);
+    neu_merge(s1, c1, a1, b1);
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) { sh[0][w] = s0; sh[1][w] = c0; sh[2][w] = s1; sh[3][w] = c1; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+      neu_merge(s0, c0, sh[0][k], sh[1][k]);
+      neu_merge(s1, c1, sh[2][k], sh[3][k]);
+    }
+    partials[4 * blockIdx.x] = s0;
+    partials[4 * blockIdx.x + 1] = c0;
+    partials[4 * blockIdx.x + 2] = s1;
+    partials[4 * blockIdx.x + 3] = c1;
+  }
+}
+
+template <int P, class Pol>
+__global__ void __launch_bounds__(256) dt_kernel(const uint4* rec, const int4* nodes, const double* xy,
+                                                 const double* hbn, long long begin, long long end, double cfl,
+                                                 double g, double H0, double* partials) {
+  constexpr int RV = Pol::template RV<P>, NS = np_of(P) - 1;
+  const RefTab<double>& tb = c_tab_d[P];
+  double best = 1e300;
+  for (long long e = begin + blockIdx.x * (long long)blockDim.x + threadIdx.x; e < end;
+       e += (long long)gridDim.x * blockDim.x) {
+    Raw<RV> r;
+    load_raw<RV>(rec, e, r);
+    Elem<P, Pol> E;
+    unpack<P>(r, E);
+    const int4 nd = nodes[e];
+    const int v[3] = {nd.x, nd.y, nd.z};
+    double per = 0, lam = 0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int a0 = v[i], b0 = v[(i + 1) % 3];
+      const double dx = xy[2 * (long long)b0] - xy[2 * (long long)a0], dy = xy[2 * (long long)b0 + 1] - xy[2 * (long long)a0 + 1];
+      per += sqrt(dx * dx + dy * dy);
+      double z = acc_d(E.zb), qx = acc_d(E.xb), qy = acc_d(E.yb);
+#pragma unroll
+      for (int m = 0; m < NS; ++m) {
+        z += (double)E.zs[m] * tb.vphi[i][m + 1];
+        qx += (double)E.xs[m] * tb.vphi[i][m + 1];
+        qy += (double)E.ys[m] * tb.vphi[i][m + 1];
+      }
+      const double H = z + hbn[v[i]], Hs = H > H0 ? H : H0;
+      const double l = sqrt(qx * qx + qy * qy) / Hs + sqrt(g * Hs);
+      lam = l > lam ? l : lam;
+    }
+    const double x0 = xy[2 * (long long)v[0]], y0 = xy[2 * (long long)v[0] + 1];
+    const double A = 0.5 * ((xy[2 * (long long)v[1]] - x0) * (xy[2 * (long long)v[2] + 1] - y0) -
+                            (xy[2 * (long long)v[2]] - x0) * (xy[2 * (long long)v[1] + 1] - y0));
+    const double dt = cfl * (4.0 * A / per) / ((2.0 * P + 1.0) * lam);
+    best = dt < best ? dt : best;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_xor_sync(0xffffffffu, best, o));
+  __shared__ double sh[8];
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = best;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) best = fmin(best, sh[k]);
+    partials[blockIdx.x] = best;
+  }
+}
+
+template <int P, class Pol>
+__global__ void __launch_bounds__(256) gather_kernel(const uint4* rec, long long begin, long long n,
+                                                     const int32_t* orig, double* z, double* x, double* y) {
+  constexpr int RV = Pol::template RV<P>, NS = np_of(P) - 1;
+  const double s2 = 1.4142135623730951;  // mode-0 coefficient = sqrt(2) * mean
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    Raw<RV> r;
+    load_raw<RV>(rec, begin + i, r);
+    Elem<P, Pol> E;
+    unpack<P>(r, E);
+    const long long o = orig[i];
+    z[o] = s2 * acc_d(E.zb);
+    x[o] = s2 * acc_d(E.xb);
+    y[o] = s2 * acc_d(E.yb);
+#pragma unroll
+    for (int m = 0; m < NS; ++m) {
+      z[(m + 1) * n + o] = (double)E.zs[m];
+      x[(m + 1) * n + o] = (double)E.xs[m];
+      y[(m + 1) * n + o] = (double)E.ys[m];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- launcher instantiation ----
+static inline int grid_for(long long n, int block) {
+  long long g = (n + block - 1) / block;
+  return (int)(g < 1 ? 1 : (g > 65535 * 8 ? 65535 * 8 : g));
+}
+
+#define DG_DEFINE_LAUNCHERS(POL)                                                                             \
+  template <>                                                                                                \
+  cudaError_t upload_tables<POL>(int p, const RefTab<float>& tf, const RefTab<double>& td) {                 \
+    cudaError_t e = cudaMemcpyToSymbol(c_tab_f, &tf, sizeof(RefTab<float>), p * sizeof(RefTab<float>));     \
+    if (e != cudaSuccess) return e;                                                                          \
+    return cudaMemcpyToSymbol(c_tab_d, &td, sizeof(RefTab<double>), p * sizeof(RefTab<double>));            \
+  }                                                                                                          \
+  template <>                                                                                                \
+  cudaError_t launch_stage<POL>(int p, int flux, const StageArgs<POL>& a, int grid, int block, cudaStream_t s) { \
+    if (p == 1 && flux == 0) stage_kernel<1, 0, POL><<<grid, block, 0, s>>>(a);                               \
+    else if (p == 1) stage_kernel<1, 1, POL><<<grid, block, 0, s>>>(a);                                       \
+    else if (flux == 0) stage_kernel<2, 0, POL><<<grid, block, 0, s>>>(a);                                    \
+    else stage_kernel<2, 1, POL><<<grid, block, 0, s>>>(a);                                                  \
+    return cudaGetLastError();                                                                               \
+  }                                                                                                          \
+  template <>                                                                                                \
+  int stage_blocks_per_sm<POL>(int p, int flux, int block) {                                                 \
+    int n = 0;                                                                                               \
+    if (p == 1 && flux == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<1, 0, POL>, block, 0); \
+    else if (p == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<1, 1, POL>, block, 0);   \
+    else if (flux == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<2, 0, POL>, block, 0);\
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<2, 1, POL>, block, 0);               \
+    return n;                                                                                                \
+  }                                                                                                          \
+  template <>                                                                                                \
+  cudaError_t launch_prepare<POL>(int p, const StageArgs<POL>& a, long long b, long long e, cudaStream_t s) { \
+    int g = grid_for(e - b, 256);                                                                            \
+    if (p == 1) prepare_kernel<1, POL><<<g, 256, 0, s>>>(a, b, e);                                           \
+    else prepare_kernel<2, POL><<<g, 256, 0, s>>>(a, b, e);                                                  \
+    return cudaGetLastError();                                                                               \
+  }                                                                                                          \
+  template <>                                                                                                \
+  cudaError_t launch_volume<POL>(int p, const uint4* rec, const uint4* geo, long long b, long long e,        \
+                                 double* partials, int nblk, cudaStream_t s) {                               \
+    if (p == 1) volume_kernel<1, POL><<<nblk, 256, 0, s>>>(rec, geo, b, e, partials);                        \
+    else volume_kernel<2, POL><<<nblk, 256, 0, s>>>(rec, geo, b, e, partials);                               \
+    return cudaGetLastError();                                                                               \
+  }                                                                                                          \
+  template <>                                                                                                \
+  cudaError_t launch_dt<POL>(int p, const uint4* rec, const int4* nodes, const double* xy, const double* hbn, \
+                             long long b, long long e, double cfl, double g, double H0, double* partials,     \
+                             int nblk, cudaStream_t s) {                                                     \
+    if (p == 1) dt_kernel<1, POL><<<nblk, 256, 0, s>>>(rec, nodes, xy, hbn, b, e, cfl, g, H0, partials);      \
+    else dt_kernel<2, POL><<<nblk, 256, 0, s>>>(rec, nodes, xy, hbn, b, e, cfl, g, H0, partials);             \
+    return cudaGetLastError();                                                                               \
+  }                                                                                                          \
+  template <>                                                                                                \
+  cudaError_t launch_gather<POL>(int p, const uint4* rec, long long b, long long n, const int32_t* orig,      \
+                                 double* z, double* x, double* y, cudaStream_t s) {                          \
+    int g = grid_for(n, 256);                                                                                \
+    if (p == 1) gather_kernel<1, POL><<<g, 256, 0, s>>>(rec, b, n, orig, z, x, y);                           \
+    else gather_kernel<2, POL><<<g, 256, 0, s>>>(rec, b, n, orig, z, x, y);                                  \
+    return cudaGetLastError();                                                                               \
+  }
+
+}  // namespace dg

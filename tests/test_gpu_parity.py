@@ -1,0 +1,283 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 CPU oracle.
+
+Bars: FP64 device path within 1e-11 of the oracle (relative to the larger of the variable's
+maximum magnitude and 1); mixed path within 1e-4 m in zeta and 1e-4 m^2/s in q; relative mass
+balance within 1e-12 in both.  Inputs are the seeded workloads of
+paper_2307_14302_gb300.workloads; dt is fixed by the oracle and passed to the device so both
+integrate the same steps.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2307_14302_gb300 import dgswe as D
+from paper_2307_14302_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-11
+MIXED_TOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2307_14302_gb300 import build as B
+
+    B.build()
+    D.lib()
+
+
+def _pair(w, steps, precision, flux=O.ROE, ssp=None, friction=O.MANNING, cf=0.0, block=0, persistent=0, dt=None):
+    ref = O.from_workload(w, flux=flux, ssp=ssp, friction=friction, cf=cf, dt=dt)
+    dt = ref.cfl_dt(w.cfl) if dt is None else dt
+    ref.set_dt(dt)
+    ref.step(steps)
+    dev = D.from_workload(w, precision=precision, flux=flux, ssp_stages=ssp, dt=dt, friction=friction, cf=cf,
+                          block=block, persistent=persistent)
+    dev.step(steps)
+    dev.sync()
+    return ref, dev
+
+
+def _fp64_err(got, want):
+    errs = []
+    for v in range(3):
+        scale = max(1.0, np.abs(want[:, v]).max())
+        errs.append(np.abs(got[:, v] - want[:, v]).max() / scale)
+    return max(errs)
+
+
+def _mixed_err(got, want):
+    return np.abs(got[:, 0] - want[:, 0]).max(), np.abs(got[:, 1:] - want[:, 1:]).max()
+
+
+def _vertex(state, p):
+    """Vertex values [E, 3, 3] of a modal state from the oracle's (pinned) basis."""
+    V = []
+    for (r, s) in ((-1.0, -1.0), (1.0, -1.0), (-1.0, 1.0)):
+        V.append(O.basis(p, r, s)[0])
+    V = np.array(V)  # [3 vertices, Np]
+    return np.einsum("evm,im->evi", state, V)
+
+
+# ----------------------------------------------------------------------- basin (C1) ------
+def test_fp64_basin_200_steps_matches_oracle():
+    w = W.basin_c1()
+    ref, dev = _pair(w, 200, D.FP64)
+    assert _fp64_err(dev.state(), ref.state()) <= FP64_TOL
+    led = dev.ledger()
+    assert led["rel_err"] < 1e-12 and led["steps"] == 200
+    assert abs(dev.dt() - ref.cfl_dt(w.cfl)) <= 1e-15 * dev.dt()
+
+
+def test_mixed_basin_200_steps_within_tolerance_and_exact_mass():
+    w = W.basin_c1()
+    ref, dev = _pair(w, 200, D.MIXED)
+    ez, eq = _mixed_err(dev.state(), ref.state())
+    assert ez <= MIXED_TOL and eq <= MIXED_TOL, (ez, eq)
+    led = dev.ledger()
+    assert led["rel_err"] < 1e-12, led
+    lo = ref.ledger()
+    assert abs(led["rain_in"] - lo["rain_in"]) / lo["rain_in"] < 1e-6
+
+
+def test_device_cfl_dt_matches_oracle():
+    w = W.basin_c1()
+    ref = O.from_workload(w)
+    for prec, tol in ((D.FP64, 1e-13), (D.MIXED, 1e-6)):
+        dev = D.from_workload(w, precision=prec)
+        assert abs(dev.dt() - ref.cfl_dt(w.cfl)) <= tol * dev.dt()
+
+
+@pytest.mark.parametrize("prec", [D.FP64, D.MIXED])
+def test_lake_at_rest_is_exact(prec):
+    w = W.basin_c1(hump=False, rain=False)
+    ref, dev = _pair(w, 200, prec)
+    s = dev.state()
+    assert np.abs(s).max() <= 1e-12
+    w = W.basin_c1(hump=False, rain=True)
+    ref, dev = _pair(w, 200, prec)
+    v = _vertex(dev.state(), 1)
+    t = dev.ledger()["t"]
+    assert np.abs(v[:, 0] - w.rain_nodal[0] * t).max() < (1e-13 if prec == D.FP64 else 1e-7)
+    assert np.abs(v[:, 1:]).max() < 1e-12
+
+
+@pytest.mark.parametrize("prec", [D.FP64, D.MIXED])
+def test_p2_ssp33_basin(prec):
+    w = W.basin_c1()
+    w.p = 2
+    ref, dev = _pair(w, 100, prec, ssp=3)
+    if prec == D.FP64:
+        assert _fp64_err(dev.state(), ref.state()) <= FP64_TOL
+    else:
+        ez, eq = _mixed_err(dev.state(), ref.state())
+        assert ez <= MIXED_TOL and eq <= MIXED_TOL, (ez, eq)
+    assert dev.ledger()["rel_err"] < 1e-12
+
+
+@pytest.mark.parametrize("prec", [D.FP64, D.MIXED])
+def test_llf_flux(prec):
+    w = W.basin_c1()
+    ref, dev = _pair(w, 100, prec, flux=O.LLF)
+    if prec == D.FP64:
+        assert _fp64_err(dev.state(), ref.state()) <= FP64_TOL
+    else:
+        ez, eq = _mixed_err(dev.state(), ref.state())
+        assert ez <= MIXED_TOL and eq <= MIXED_TOL
+
+
+def test_mirror_symmetric_dam_break_on_device():
+    w = W.basin_c1(mirror=True)
+    ref, dev = _pair(w, 200, D.FP64)
+    assert _fp64_err(dev.state(), ref.state()) <= FP64_TOL
+
+
+# ------------------------------------------------------------- coastal wet/dry (C2) ------
+@pytest.mark.parametrize("prec", [D.FP64, D.MIXED])
+def test_coastal_wet_dry_small(prec):
+    w = W.coastal_c2(n_tri=6000, seed=21, steps=200)
+    ref, dev = _pair(w, 200, prec)
+    got, want = dev.state(), ref.state()
+    if prec == D.FP64:
+        assert _fp64_err(got, want) <= FP64_TOL
+        assert np.array_equal(dev.dry(), ref.dry())
+    else:
+        ez, eq = _mixed_err(got, want)
+        assert ez <= MIXED_TOL and eq <= MIXED_TOL, (ez, eq)
+    led = dev.ledger()
+    assert led["rel_err"] < 1e-12, led
+    assert led["bdry_in"] != 0.0
+
+
+def test_coastal_without_rain_dries_like_the_oracle():
+    w = W.coastal_c2(n_tri=4000, seed=9, steps=100)
+    w.storm = None
+    ref, dev = _pair(w, 100, D.FP64)
+    assert _fp64_err(dev.state(), ref.state()) <= FP64_TOL
+    assert np.array_equal(dev.dry(), ref.dry())
+    assert dev.dry().sum() > 100
+
+
+@pytest.mark.parametrize("prec", [D.FP64, D.MIXED])
+def test_coastal_full_size_short_run(prec):
+    """The full 250k-triangle coastal workload in the benchmark's launch configuration
+    (autotuned), 10 steps, every element compared."""
+    w = W.coastal_c2()
+    ref, dev = _pair(w, 10, prec)
+    got, want = dev.state(), ref.state()
+    if prec == D.FP64:
+        assert _fp64_err(got, want) <= FP64_TOL
+    else:
+        ez, eq = _mixed_err(got, want)
+        assert ez <= MIXED_TOL and eq <= MIXED_TOL, (ez, eq)
+    assert dev.ledger()["rel_err"] < 1e-12
+
+
+# -------------------------------------------------------------------- forcing paths ------
+@pytest.mark.parametrize("prec", [D.FP64, D.MIXED])
+def test_gridded_rain_and_pressure_setup(prec):
+    w = W.coastal_c2(n_tri=3000, seed=31, steps=50)
+    w.storm = None
+    rng = np.random.default_rng(3)
+    nx, ny, nt = 12, 9, 3
+    w.rain_grid = W.RainGrid(nx, ny, nt, 0.0, 0.0, 400_000.0 / (nx - 1), 300_000.0 / (ny - 1), 0.0, 60.0,
+                             rng.uniform(0, 80, (nt, ny, nx)).astype(np.float32))
+    w.pressure = (320_000.0, 150_000.0, 50_000.0, 1.0)
+    ref, dev = _pair(w, 50, prec)
+    got, want = dev.state(), ref.state()
+    if prec == D.FP64:
+        assert _fp64_err(got, want) <= FP64_TOL
+    else:
+        ez, eq = _mixed_err(got, want)
+        assert ez <= MIXED_TOL and eq <= MIXED_TOL, (ez, eq)
+    assert dev.ledger()["rel_err"] < 1e-12
+
+
+def test_quadratic_friction_bathtub_short():
+    w = W.bathtub()
+    ref, dev = _pair(w, 500, D.FP64, friction=O.QUADRATIC, cf=0.001, dt=5.0)
+    assert _fp64_err(dev.state(), ref.state()) <= FP64_TOL
+
+
+# ----------------------------------------------------------- launch shapes, edge cases ----
+@pytest.mark.parametrize("prec", [D.FP64, D.MIXED])
+def test_launch_shapes_give_identical_bits(prec):
+    w = W.coastal_c2(n_tri=5000, seed=5, steps=30)
+    outs = []
+    for block, pers in ((64, 0), (128, 1), (256, 0), (256, 1)):
+        dev = D.from_workload(w, precision=prec, block=block, persistent=pers)
+        dev.step(30)
+        dev.sync()
+        assert dev.launch() == (block, pers)
+        outs.append(dev.state())
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+
+
+def test_ragged_and_tiny_meshes():
+    # 2 triangles (one partial tile) and a mesh whose size is not a multiple of any block
+    for w in (W.basin_c1(nx=1, ny=1), W.basin_c1(nx=13, ny=7)):
+        ref, dev = _pair(w, 50, D.FP64)
+        assert _fp64_err(dev.state(), ref.state()) <= FP64_TOL
+
+
+def test_modal_state_round_trip_and_nonfinite_rejected():
+    w = W.basin_c1()
+    dev = D.from_workload(w, precision=D.FP64)
+    s = dev.state()
+    dev2 = D.Solver(precision=D.FP64, H0=w.h0, cfl=w.cfl)
+    dev2.set_mesh(w.mesh)
+    dev2.set_fields(w.hb, w.manning)
+    dev2.set_rain_nodal(w.rain_nodal)
+    dev2.set_state(np.ascontiguousarray(s[:, 0].T), np.ascontiguousarray(s[:, 1].T),
+                   np.ascontiguousarray(s[:, 2].T), layout=D.LAYOUT_MODAL)
+    assert np.array_equal(dev2.state(), s)
+    bad = w.zeta0.copy()
+    bad[3] = np.nan
+    with pytest.raises(D.DgsweError) as ei:
+        dev2.set_state(bad)
+    assert ei.value.code == -1
+
+
+def test_negative_mean_depth_is_reported_not_trapped():
+    w = W.basin_c1()
+    z = w.zeta0.copy()
+    z[:] = -w.hb - 0.5  # every element well below its bed: a host-made invalid state
+    dev = D.Solver(precision=D.MIXED, H0=w.h0, cfl=0.0, dt=1.0)
+    dev.set_mesh(w.mesh)
+    dev.set_fields(w.hb, w.manning)
+    dev.set_state(z)
+    with pytest.raises(D.DgsweError) as ei:
+        dev.sync()
+    assert ei.value.code == -5
+
+
+# --------------------------------------------------------------------------- ensemble ----
+@pytest.mark.parametrize("prec", [D.FP64, D.MIXED])
+def test_ensemble_members_match_solo_runs(prec):
+    ws = W.ensemble_c4(n_scen=3, lo=1500, hi=6000, seed=8, steps=40)
+    solos, members = [], []
+    for w in ws:
+        s = D.from_workload(w, precision=prec)
+        members.append(s)
+        solo = D.from_workload(w, precision=prec)
+        solo.step(40)
+        solo.sync()
+        solos.append((solo.state(), solo.ledger()))
+    ens = D.Ensemble(members)
+    ens.step(40)
+    ens.sync()
+    for i, (st, led) in enumerate(solos):
+        assert np.array_equal(ens.state(i), st)
+        le = ens.ledger(i)
+        assert le["rel_err"] < 1e-12 and le["steps"] == 40
+        assert abs(le["t"] - led["t"]) == 0.0
+    # and the FP64 members against the oracle
+    if prec == D.FP64:
+        w = ws[0]
+        ref = O.from_workload(w)
+        ref.step(40)
+        assert _fp64_err(ens.state(0), ref.state()) <= FP64_TOL
