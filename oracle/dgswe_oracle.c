@@ -19,7 +19,8 @@
  *   Sec. 2.4            positive-depth operator M Pi_h = (M Pi^d, M Pi^f) after every stage.
  *
  * Readings of points the paper leaves open (each also listed in the design notes):
- *   - pressure flux is g/2 (H^2 - hb^2) (Eq. SWE); the flux-matrix display drops the 1/2;
+ *   - pressure flux is g/2 (H^2 - hb^2) (Eq. SWE); the flux-matrix display drops the 1/2; it is
+ *     evaluated as g/2 zeta (zeta + 2 hb), the same value with H = zeta + hb (Sec. 2.1);
  *   - Manning: tau_b = g n^2 |u| / H^{4/3}; quadratic (bathtub, Sec. 3.1): tau_b = Cf |u| / H;
  *     velocities and celerities use Hs = max(H, H0);
  *   - Roe flux with Roe averages (arithmetic Hs, sqrt(Hs)-weighted velocity), no entropy fix;
@@ -484,12 +485,14 @@ static double tide_at(const orc_t* o, int seg, double t) {
   return o->tamp[seg] * sin(2.0 * M_PI * t / o->tper[seg] + o->tpha[seg]);
 }
 
-/* normal physical flux F(w).n with pressure g/2 (H^2 - hb^2) (Eq. SWE) */
+/* normal physical flux F(w).n with pressure g/2 (H^2 - hb^2) (Eq. SWE), evaluated as
+ * g/2 zeta (zeta + 2 hb) -- the same quantity since H = zeta + hb (Sec. 2.1), without the
+ * cancellation of two ~H^2 terms in deep water */
 static void phys_flux(const orc_t* o, const double* w, double hb, double nx, double ny, double* f, double* un_out,
                       double* Hs_out) {
   double H = w[0] + hb, Hs = H > o->H0 ? H : o->H0;
   double u = w[1] / Hs, v = w[2] / Hs, un = u * nx + v * ny;
-  double P = 0.5 * o->g * (H * H - hb * hb);
+  double P = 0.5 * o->g * w[0] * (w[0] + 2.0 * hb);
   f[0] = w[1] * nx + w[2] * ny;
   f[1] = w[1] * un + P * nx;
   f[2] = w[2] * un + P * ny;
@@ -668,7 +671,7 @@ static void compute_L(orc_t* o, const double* W, double t, double* rain_out, dou
       double hb = interp_nodal(o, o->hb, e, o->lq[q]);
       double H = wq[0] + hb, Hs = H > o->H0 ? H : o->H0;
       double u = wq[1] / Hs, v = wq[2] / Hs;
-      double P = 0.5 * g * (H * H - hb * hb);
+      double P = 0.5 * g * wq[0] * (wq[0] + 2.0 * hb); /* = g/2 (H^2 - hb^2) */
       double fx[3] = {wq[1], wq[1] * u + P, wq[2] * u};
       double fy[3] = {wq[2], wq[1] * v, wq[2] * v + P};
       double tau = 0.0, sp = sqrt(u * u + v * v);
