@@ -615,8 +615,6 @@ static int prepare(dgswe_h h) {
     if (int rc = reduce_volume(h, s, h->V0[s], h->VH0[s])) return rc;
   }
   if (int rc = upload_dt(h)) return rc;
-  Ctl zero{};
-  CU(cudaMemcpyAsync(h->ctl.p, &zero, sizeof zero, cudaMemcpyHostToDevice, h->stream));
   h->ntiles = 0;
   if (int rc = apply_launch(h, h->block, h->persistent)) return rc;
   CU(cudaStreamSynchronize(h->stream));

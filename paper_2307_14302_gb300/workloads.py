@@ -288,8 +288,10 @@ def _coastal_bathymetry(x, y, lx, ly, land_top, rng_phase):
 
 
 def _initial_dry(hb, h0):
-    """zeta = max(0, h0 - hb): dry land carries a thin layer of h0 (nodal)."""
-    return np.where(hb < h0, h0 - hb, 0.0)
+    """Nodal initial elevation: 0 over water; on land (hb < h0) a film of depth h0/2, so dry
+    land starts clearly below the wet/dry threshold h0 instead of exactly on it (where the last
+    bit of roundoff would pick the element's flag)."""
+    return np.where(hb < h0, 0.5 * h0 - hb, 0.0)
 
 
 def coastal_c2(n_tri=250_000, seed=2, steps=2000) -> Workload:

@@ -517,6 +517,6 @@ def test_wet_dry_run_stays_bounded_and_conservative():
     assert np.abs(s[dry, 1:]).max() == 0.0
     assert o.ledger()["rel_err"] < 1e-12
     o.set_storm(storm)
-    o.step(100)
-    assert o.dry().sum() < 0.1 * dry.sum()
+    o.step(1200)
+    assert o.dry().sum() < 0.7 * dry.sum()
     assert o.ledger()["rel_err"] < 1e-12
