@@ -58,9 +58,10 @@ enum { DGSWE_LAYOUT_MODAL = 0, DGSWE_LAYOUT_NODAL = 1 };
 typedef struct dgswe_ctx* dgswe_h;
 
 /* Run parameters (Sec. 2.2-2.4, Sec. 3).
- *   p           polynomial degree 0, 1 or 2 (Eq. dubiner);
+ *   p           polynomial degree 1 or 2 (Eq. dubiner);
  *   flux        DGSWE_FLUX_ROE or DGSWE_FLUX_LLF;
- *   ssp_stages  1, 2 or 3: SSP(1,1), SSP(2,2), SSP(3,3) in Shu-Osher form (Sec. 2.2);
+ *   ssp_stages  2 or 3: SSP(2,2) or SSP(3,3) in Shu-Osher form (Sec. 2.2; order p+1 is the
+ *               usual choice);
  *   precision   DGSWE_FP64 (every operation in double) or DGSWE_MIXED (FP32 bulk; float-float
  *               element means; FP64 for the depth test near H0 and the global ledger);
  *   g           gravity [m/s^2];  H0 thin-layer depth threshold [m] (Sec. 2.4);
@@ -104,9 +105,10 @@ typedef struct {
   double V0, V, rain_in, bdry_in, VH0, rel_err, wet_frac;
 } dgswe_ledger;
 
-/* Creates a context on CUDA device `device`; `cuda_stream` is a cudaStream_t (NULL: the legacy
- * default stream) on which all device work of this context is enqueued.  *out receives the
- * handle.  Errors: EINVAL (null out), ENOLIB (no device / no kernel image), ECUDA. */
+/* Creates a context on CUDA device `device`; `cuda_stream` is a cudaStream_t on which all device
+ * work of this context is enqueued (NULL: the library creates a private non-blocking stream).
+ * *out receives the handle.  Errors: EINVAL (null out), ENOLIB (no device, or a device other
+ * than sm_103a), ECUDA. */
 int dgswe_create(dgswe_h* out, int device, void* cuda_stream);
 
 /* Sets the run parameters (copied).  EINVAL on values outside the ranges above. */
@@ -147,6 +149,14 @@ int dgswe_set_pressure_setup(dgswe_h, const dgswe_gauss_setup* setup);
  * operator is applied once (it defines the wet/dry flags), the ledger is reset (V0, VH0) and,
  * when params.dt <= 0, dt is fixed from the CFL condition. */
 int dgswe_set_state(dgswe_h, const double* zeta, const double* qx, const double* qy, int32_t layout, double t0);
+
+/* Replaces the state at the current time with modal host arrays [Np][n_tri] (the layout of
+ * dgswe_get_state): copied to the device, packed into the element records there, and passed
+ * through the positive-depth operator (Sec. 2.4).  Mesh, fields, forcing, dt, time and ledger
+ * are kept (the ledger then also contains the injected change).  Returns after the stream has
+ * consumed the arrays.  Intended for restarts and coupling, where a caller exchanges the state
+ * every step. */
+int dgswe_load_state(dgswe_h, const double* zeta, const double* qx, const double* qy);
 
 /* Enqueues n_steps SSP-RK steps on the context's stream (CUDA graph replay) and returns
  * without waiting.  Device errors surface in dgswe_sync. */

@@ -912,6 +912,42 @@ int dgswe_get_state_device(dgswe_h h, double* z, double* x, double* y) {
   return gather_state(h, 0, z, x, y, true);
 }
 
+int dgswe_load_state(dgswe_h h, const double* z, const double* x, const double* y) {
+  if (int rc = check_handle(h)) return rc;
+  if (!h->ready) return fail(DGSWE_ESTATE, "set_state must precede load_state");
+  if (!z || !x || !y) return fail(DGSWE_EINVAL, "null state array");
+  if (h->ensemble) return fail(DGSWE_EINVAL, "not available on an ensemble");
+  DeviceGuard dg_(h->device);
+  const long long n = h->sc[0].m.ne, b = h->eoff[0];
+  const size_t cnt = (size_t)h->np * n;
+  if (h->gather_buf.n < 3 * cnt * sizeof(double))
+    if (h->gather_buf.alloc(3 * cnt * sizeof(double))) return fail(DGSWE_ENOMEM, "staging buffer");
+  double* dz = h->gather_buf.as<double>();
+  CU(cudaMemcpyAsync(dz, z, cnt * 8, cudaMemcpyHostToDevice, h->stream));
+  CU(cudaMemcpyAsync(dz + cnt, x, cnt * 8, cudaMemcpyHostToDevice, h->stream));
+  CU(cudaMemcpyAsync(dz + 2 * cnt, y, cnt * 8, cudaMemcpyHostToDevice, h->stream));
+  cudaError_t ce;
+  if (mixed(h)) {
+    ce = launch_scatter<Mixed>(h->prm.p, h->rec[0].as<uint4>(), b, n, h->eorig.as<int32_t>() + b, dz, dz + cnt, dz + 2 * cnt, h->stream);
+    if (ce == cudaSuccess) {
+      StageArgs<Mixed> a = make_args<Mixed>(h, 0, 1);
+      a.in = a.out = h->rec[0].as<uint4>();
+      ce = launch_prepare<Mixed>(h->prm.p, a, b, b + n, h->stream);
+    }
+  } else {
+    ce = launch_scatter<Fp64>(h->prm.p, h->rec[0].as<uint4>(), b, n, h->eorig.as<int32_t>() + b, dz, dz + cnt, dz + 2 * cnt, h->stream);
+    if (ce == cudaSuccess) {
+      StageArgs<Fp64> a = make_args<Fp64>(h, 0, 1);
+      a.in = a.out = h->rec[0].as<uint4>();
+      ce = launch_prepare<Fp64>(h->prm.p, a, b, b + n, h->stream);
+    }
+  }
+  if (ce != cudaSuccess) return fail(DGSWE_ECUDA, "load_state launch: %s", cudaGetErrorString(ce));
+  h->launches += 2;
+  CU(cudaStreamSynchronize(h->stream));
+  return 0;
+}
+
 int dgswe_get_dry(dgswe_h h, uint8_t* dry) {
   if (int rc = check_handle(h)) return rc;
   if (!h->ready) return fail(DGSWE_ESTATE, "no state");

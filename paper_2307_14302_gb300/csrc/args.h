@@ -78,6 +78,11 @@ template <class Pol>
 cudaError_t launch_gather(int p, const uint4* rec, long long begin, long long n, const int32_t* orig, double* z,
                           double* x, double* y, cudaStream_t s);
 
+// modal state [Np][n] (caller order) into the records of [begin, begin + n)
+template <class Pol>
+cudaError_t launch_scatter(int p, uint4* rec, long long begin, long long n, const int32_t* orig, const double* z,
+                           const double* x, const double* y, cudaStream_t s);
+
 // Neumaier-compensated reduction of per-block partial pairs (shared by all precisions)
 cudaError_t launch_reduce_pairs(const double* partials, int nblk, int npairs, double* out, cudaStream_t s);
 

@@ -1095,6 +1095,33 @@ __global__ void __launch_bounds__(256) gather_kernel(const uint4* rec, long long
   }
 }
 
+// modal state [Np][n] in caller order -> records of elements [begin, begin + n); bathymetry
+// modes are kept, depth and flags are recomputed by the positive-depth pass that follows
+template <int P, class Pol>
+__global__ void __launch_bounds__(256) scatter_kernel(uint4* rec, long long begin, long long n, const int32_t* orig,
+                                                      const double* z, const double* x, const double* y) {
+  constexpr int RV = Pol::template RV<P>, NS = np_of(P) - 1;
+  const double is2 = 0.7071067811865476;  // mean = mode-0 coefficient / sqrt(2)
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    Raw<RV> r;
+    load_raw<RV>(rec, begin + i, r);
+    Elem<P, Pol> E;
+    unpack<P>(r, E);
+    const long long o = orig[i];
+    acc_set(E.zb, is2 * z[o]);
+    acc_set(E.xb, is2 * x[o]);
+    acc_set(E.yb, is2 * y[o]);
+#pragma unroll
+    for (int m = 0; m < NS; ++m) {
+      E.zs[m] = (typename Pol::T)z[(m + 1) * n + o];
+      E.xs[m] = (typename Pol::T)x[(m + 1) * n + o];
+      E.ys[m] = (typename Pol::T)y[(m + 1) * n + o];
+    }
+    pack<P>(E, r);
+    store_raw<RV>(rec, begin + i, r);
+  }
+}
+
 // ---------------------------------------------------------------- launcher instantiation ----
 static inline int grid_for(long long n, int block) {
   long long g = (n + block - 1) / block;
@@ -1153,6 +1180,14 @@ static inline int grid_for(long long n, int block) {
     int g = grid_for(n, 256);                                                                                \
     if (p == 1) gather_kernel<1, POL><<<g, 256, 0, s>>>(rec, b, n, orig, z, x, y);                           \
     else gather_kernel<2, POL><<<g, 256, 0, s>>>(rec, b, n, orig, z, x, y);                                  \
+    return cudaGetLastError();                                                                               \
+  }                                                                                                          \
+  template <>                                                                                                \
+  cudaError_t launch_scatter<POL>(int p, uint4* rec, long long b, long long n, const int32_t* orig,          \
+                                  const double* z, const double* x, const double* y, cudaStream_t s) {       \
+    int g = grid_for(n, 256);                                                                                \
+    if (p == 1) scatter_kernel<1, POL><<<g, 256, 0, s>>>(rec, b, n, orig, z, x, y);                          \
+    else scatter_kernel<2, POL><<<g, 256, 0, s>>>(rec, b, n, orig, z, x, y);                                 \
     return cudaGetLastError();                                                                               \
   }
 

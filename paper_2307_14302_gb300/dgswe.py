@@ -58,7 +58,7 @@ class Ledger(C.Structure):
 EXPORTS = [
     "dgswe_create", "dgswe_set_params", "dgswe_set_mesh", "dgswe_set_fields", "dgswe_set_rain_nodal",
     "dgswe_set_rain_parametric", "dgswe_set_rain_grid", "dgswe_set_tide", "dgswe_set_pressure_setup",
-    "dgswe_set_state", "dgswe_step", "dgswe_sync", "dgswe_get_dt", "dgswe_get_state", "dgswe_get_state_device",
+    "dgswe_set_state", "dgswe_load_state", "dgswe_step", "dgswe_sync", "dgswe_get_dt", "dgswe_get_state", "dgswe_get_state_device",
     "dgswe_get_dry", "dgswe_get_ledger", "dgswe_volume", "dgswe_ensemble_create", "dgswe_ensemble_step",
     "dgswe_ensemble_get_state", "dgswe_ensemble_get_ledger", "dgswe_set_launch", "dgswe_get_launch",
     "dgswe_launch_count", "dgswe_destroy", "dgswe_last_error",
@@ -93,6 +93,7 @@ def lib():
         "dgswe_set_tide": ([_h, C.c_int32, _d, _d, _d], C.c_int),
         "dgswe_set_pressure_setup": ([_h, C.POINTER(GaussSetup)], C.c_int),
         "dgswe_set_state": ([_h, _d, _d, _d, C.c_int32, C.c_double], C.c_int),
+        "dgswe_load_state": ([_h, _d, _d, _d], C.c_int),
         "dgswe_step": ([_h, C.c_int64], C.c_int),
         "dgswe_sync": ([_h], C.c_int),
         "dgswe_get_dt": ([_h, _d], C.c_int),
@@ -200,11 +201,22 @@ class Solver:
         qy = _f64(qy if qy is not None else np.zeros_like(z))
         _check(lib().dgswe_set_state(self.h, _p(z), _p(qx), _p(qy), layout, t0))
 
+    def load_state(self, z, x, y):
+        """Modal arrays [Np][E] (caller order), e.g. from state_arrays()."""
+        _check(lib().dgswe_load_state(self.h, _p(z), _p(x), _p(y)))
+
     def step(self, n):
         _check(lib().dgswe_step(self.h, int(n)))
 
     def sync(self):
         _check(lib().dgswe_sync(self.h))
+
+    def state_arrays(self, z=None, x=None, y=None):
+        """Modal state as three [Np][E] arrays (filled in place when given, e.g. pinned)."""
+        if z is None:
+            z, x, y = (np.empty((self.np_, self.ne)) for _ in range(3))
+        _check(lib().dgswe_get_state(self.h, _p(z), _p(x), _p(y)))
+        return z, x, y
 
     def dt(self):
         v = C.c_double()
