@@ -151,11 +151,12 @@ int dgswe_set_pressure_setup(dgswe_h, const dgswe_gauss_setup* setup);
 int dgswe_set_state(dgswe_h, const double* zeta, const double* qx, const double* qy, int32_t layout, double t0);
 
 /* Replaces the state at the current time with modal host arrays [Np][n_tri] (the layout of
- * dgswe_get_state): copied to the device, packed into the element records there, and passed
- * through the positive-depth operator (Sec. 2.4).  Mesh, fields, forcing, dt, time and ledger
- * are kept (the ledger then also contains the injected change).  Returns after the stream has
- * consumed the arrays.  Intended for restarts and coupling, where a caller exchanges the state
- * every step. */
+ * dgswe_get_state): copied to the device and packed into the element records there, bit for
+ * bit.  The state is kept as given (a state read back from the solver satisfies the positive-
+ * depth constraints of Sec. 2.4 already); only the mean depths and wet/dry flags are derived
+ * from it.  Mesh, fields, forcing, dt, time and ledger are kept (the ledger then also holds the
+ * injected change).  Returns after the stream has consumed the arrays.  For restarts and for
+ * couplings that exchange the state every step. */
 int dgswe_load_state(dgswe_h, const double* zeta, const double* qx, const double* qy);
 
 /* Enqueues n_steps SSP-RK steps on the context's stream (CUDA graph replay) and returns

@@ -932,6 +932,7 @@ int dgswe_load_state(dgswe_h h, const double* z, const double* x, const double* 
     if (ce == cudaSuccess) {
       StageArgs<Mixed> a = make_args<Mixed>(h, 0, 1);
       a.in = a.out = h->rec[0].as<uint4>();
+      a.classify_only = 1;
       ce = launch_prepare<Mixed>(h->prm.p, a, b, b + n, h->stream);
     }
   } else {
@@ -939,6 +940,7 @@ int dgswe_load_state(dgswe_h h, const double* z, const double* x, const double* 
     if (ce == cudaSuccess) {
       StageArgs<Fp64> a = make_args<Fp64>(h, 0, 1);
       a.in = a.out = h->rec[0].as<uint4>();
+      a.classify_only = 1;
       ce = launch_prepare<Fp64>(h->prm.p, a, b, b + n, h->stream);
     }
   }

@@ -43,6 +43,7 @@ struct StageArgs {
   int last;                // 1 on the final stage of a step
   int persistent;
   int tune;                // 1: timing run, no ledger or step bookkeeping
+  int classify_only;       // prepare pass: derive depth and dry flag, keep the state as given
   int friction;            // 0 Manning, 1 quadratic, 2 none
   float a_n_hi, a_n_lo, a_in_hi, a_in_lo;  // Shu-Osher coefficients as float-float
   double a_n, a_in;

@@ -966,8 +966,14 @@ __global__ void __launch_bounds__(256) prepare_kernel(const StageArgs<Pol> a, lo
     load_raw<RV>(a.in, e, r);
     Elem<P, Pol> E;
     unpack<P>(r, E);
-    apply_positivity<P, Pol>(E, G, e, a, &a.ctl->err);
-    pack<P>(E, r);
+    Elem<P, Pol> O = E;
+    apply_positivity<P, Pol>(O, G, e, a, &a.ctl->err);
+    if (a.classify_only) {
+      E.Hb = O.Hb;
+      E.flags = O.flags;
+      O = E;
+    }
+    pack<P>(O, r);
     store_raw<RV>(a.out, e, r);
   }
 }
