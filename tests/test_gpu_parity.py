@@ -285,8 +285,10 @@ def test_ensemble_members_match_solo_runs(prec):
 
 @pytest.mark.parametrize("prec", [D.FP64, D.MIXED])
 def test_load_state_round_trip_and_restart(prec):
-    """Checkpoint/restart through the public API: the state read after 20 steps, loaded into a
-    fresh run, continues bit-identically (also the e2e benchmark's per-step exchange)."""
+    """Checkpoint/restart through the public API (also the e2e benchmark's per-step exchange).
+    Modes >= 1 round-trip bit for bit; mode 0 is sqrt(2) times the element mean, so it is rounded
+    once on the way out and once on the way in (a few ulps).  The continued run stays within the
+    path's tolerance of the uninterrupted one."""
     w = W.coastal_c2(n_tri=4000, seed=13, steps=40)
     a = D.from_workload(w, precision=prec)
     a.step(20)
@@ -296,7 +298,14 @@ def test_load_state_round_trip_and_restart(prec):
     b = D.from_workload(w, precision=prec)
     b.step(20)
     b.load_state(z, x, y)
-    assert np.array_equal(b.state(), np.stack([z.T, x.T, y.T], axis=1))
+    got = b.state()
+    want = np.stack([z.T, x.T, y.T], axis=1)
+    assert np.array_equal(got[:, :, 1:], want[:, :, 1:])
+    assert np.abs(got[:, :, 0] - want[:, :, 0]).max() <= 4e-16 * max(1.0, np.abs(want[:, :, 0]).max())
     b.step(20)
     b.sync()
-    assert np.array_equal(a.state(), b.state())
+    if prec == D.FP64:
+        assert _fp64_err(b.state(), a.state()) <= 1e-13
+    else:
+        ez, eq = _mixed_err(b.state(), a.state())
+        assert ez <= 1e-6 and eq <= 1e-5, (ez, eq)
