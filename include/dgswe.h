@@ -187,6 +187,24 @@ int dgswe_get_ledger(dgswe_h, dgswe_ledger* out);
  * memory; *out receives the value (synchronises the stream). */
 int dgswe_volume(dgswe_h, double* out);
 
+/* No counterpart in the paper: the total water volume of dgswe_volume, for callers that cannot
+ * allocate device memory -- inside CUDA stream capture (cudaMalloc and cudaFree are not
+ * capturable), with all device memory drawn from their own pool or caching allocator, or in
+ * loops that must not stall on the device-wide synchronisation of cudaFree.  This entry point
+ * allocates nothing.
+ *   w0_dev    [n] device array: mode-0 coefficients of zeta (row 0 of dgswe_get_state_device);
+ *   area_dev  [n] device array: element areas [m^2];
+ *   out_dev   device pointer to one double, receives sum_e area_e * w0_e / sqrt(2);
+ *   cuda_stream  stream for the two kernels (NULL: the legacy default stream); asynchronous.
+ * Partial sums live in a fixed 64 KiB __device__ array that every GPU loading the library
+ * keeps until exit; n may be 0 .. 16,777,216, larger n returns DGSWE_EINVAL.  All calls share
+ * that array (each call writes every slot it reads), so calls whose kernels overlap on the GPU
+ * race: order them on one stream.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress, with that device current); make that first call before any
+ * stream capture.  Pointers must belong to the current device. */
+int dgswe_volume_sum_noalloc(const double* w0_dev, const double* area_dev, int64_t n, double* out_dev,
+                             void* cuda_stream);
+
 /* Ensemble of independent scenarios (different meshes, forcing, Manning fields) advanced
  * together: one persistent launch per RK stage, the whole step captured in a CUDA graph.  The
  * members must share p, flux, ssp_stages, precision, g and H0 and have their state set; their

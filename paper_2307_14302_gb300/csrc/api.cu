@@ -36,6 +36,9 @@ static int fail(int code, const char* fmt, ...) {
   return code;
 }
 
+// lets the other translation units of the library report an error message
+void dg::set_last_error(const std::string& msg) { g_err = msg; }
+
 #define CU(call)                                                                                 \
   do {                                                                                           \
     cudaError_t e_ = (call);                                                                     \

@@ -29,5 +29,6 @@ int build_mesh(int nn, const double* xy, int ne, const int32_t* tri, int nb, con
 void build_tables(int p, RefTab<double>& t);
 void tables_to_float(const RefTab<double>& d, RefTab<float>& f);
 void dubiner_eval(int p, double r, double s, double* phi, double* dphr, double* dphs);
+void set_last_error(const std::string& msg);
 
 }  // namespace dg

@@ -59,7 +59,7 @@ EXPORTS = [
     "dgswe_create", "dgswe_set_params", "dgswe_set_mesh", "dgswe_set_fields", "dgswe_set_rain_nodal",
     "dgswe_set_rain_parametric", "dgswe_set_rain_grid", "dgswe_set_tide", "dgswe_set_pressure_setup",
     "dgswe_set_state", "dgswe_load_state", "dgswe_step", "dgswe_sync", "dgswe_get_dt", "dgswe_get_state", "dgswe_get_state_device",
-    "dgswe_get_dry", "dgswe_get_ledger", "dgswe_volume", "dgswe_ensemble_create", "dgswe_ensemble_step",
+    "dgswe_get_dry", "dgswe_get_ledger", "dgswe_volume", "dgswe_volume_sum_noalloc", "dgswe_ensemble_create", "dgswe_ensemble_step",
     "dgswe_ensemble_get_state", "dgswe_ensemble_get_ledger", "dgswe_set_launch", "dgswe_get_launch",
     "dgswe_launch_count", "dgswe_destroy", "dgswe_last_error",
 ]
@@ -102,6 +102,7 @@ def lib():
         "dgswe_get_dry": ([_h, _u8], C.c_int),
         "dgswe_get_ledger": ([_h, C.POINTER(Ledger)], C.c_int),
         "dgswe_volume": ([_h, _d], C.c_int),
+        "dgswe_volume_sum_noalloc": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p], C.c_int),
         "dgswe_ensemble_create": ([C.POINTER(_h), C.c_int32, C.POINTER(_h), C.c_int, C.c_void_p], C.c_int),
         "dgswe_ensemble_step": ([_h, C.c_int64], C.c_int),
         "dgswe_ensemble_get_state": ([_h, C.c_int32, _d, _d, _d], C.c_int),
@@ -257,6 +258,12 @@ class Solver:
 
     def launch_count(self) -> int:
         return int(lib().dgswe_launch_count(self.h))
+
+
+def volume_sum_noalloc(w0_ptr, area_ptr, n, out_ptr, stream=None):
+    """dgswe_volume_sum_noalloc on caller-owned device pointers (allocates nothing)."""
+    _check(lib().dgswe_volume_sum_noalloc(C.c_void_p(w0_ptr), C.c_void_p(area_ptr), int(n), C.c_void_p(out_ptr),
+                                          C.c_void_p(stream) if stream else None))
 
 
 class Ensemble:
