@@ -215,10 +215,11 @@ int dgswe_ensemble_step(dgswe_h ens, int64_t n_steps);
 int dgswe_ensemble_get_state(dgswe_h ens, int32_t member, double* zeta, double* qx, double* qy);
 int dgswe_ensemble_get_ledger(dgswe_h ens, int32_t member, dgswe_ledger* out);
 
-/* Launch tuning: block size (64, 128, 256 or 0 = autotune on the next step) and persistent
- * grid (1: one CTA pass per SM slot with an atomic tile counter, 0: one CTA per tile). */
-int dgswe_set_launch(dgswe_h, int32_t block, int32_t persistent);
-int dgswe_get_launch(dgswe_h, int32_t* block, int32_t* persistent);
+/* Launch shape of the stage kernel: block size (64, 128, 256, or 0 = autotune on the next step)
+ * and waves (1 or 2): the grid holds waves x (CTAs resident per SM) x (SMs) CTAs, and its warps
+ * take the 32-element tiles of all scenarios round-robin.  Results do not depend on the shape. */
+int dgswe_set_launch(dgswe_h, int32_t block, int32_t waves);
+int dgswe_get_launch(dgswe_h, int32_t* block, int32_t* waves);
 
 /* Number of kernel launches this context enqueued so far (all kinds). */
 int64_t dgswe_launch_count(dgswe_h);

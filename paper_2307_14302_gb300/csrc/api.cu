@@ -111,14 +111,16 @@ struct dgswe_ctx {
   std::vector<long long> eoff, noff;
   DevBuf rec[3], nbr, geo, nodes, node_xy, xy64, hbn, rain_e, scen, tile_scen, ledger, ctl, eorig, grids, scratch,
       gather_buf;
-  int ntiles = 0;
-  std::vector<double> led_rain, led_bdry;  // host-folded ledger of retired tilings
+  int ntiles = 0;                          // 32-element tiles
+  int wslots = 0;                          // ledger slots per scenario
+  int wcur = 0;                            // warps of the current launch shape
+  std::vector<double> led_rain, led_bdry;  // host-folded ledger of retired launch shapes
   std::vector<double> V0, VH0;
   std::vector<Stage> stages;
   // launch configuration
-  int block = 128, persistent = 0;
+  int block = 128, waves = 1;
   bool autotune = true;
-  int grid_persistent = 0;
+  int grid = 0;
   cudaGraphExec_t g1 = nullptr, gK = nullptr;
   int K = 8;
   long long launches = 0;
@@ -337,8 +339,7 @@ static int build_layout(dgswe_h h) {
   if (h->geo.alloc(16 * (size_t)h->gv * E) || h->nbr.alloc(16 * (size_t)E) || h->nodes.alloc(16 * (size_t)E) ||
       h->xy64.alloc(16 * (size_t)N) || h->hbn.alloc(8 * (size_t)N) || h->eorig.alloc(4 * (size_t)E) ||
       h->node_xy.alloc(mx ? 8 * (size_t)N : 16 * (size_t)N) || h->rain_e.alloc(mx ? 4 * (size_t)E : 8 * (size_t)E) ||
-      h->ctl.alloc(sizeof(Ctl)) || h->scen.alloc(sizeof(ScenDev) * ns) || h->ledger.alloc(16 * (size_t)(E / 64 + 1)) ||
-      h->tile_scen.alloc(4 * (size_t)(E / 64 + 1)) || h->grids.alloc(4 * grids.size()) ||
+      h->ctl.alloc(sizeof(Ctl)) || h->scen.alloc(sizeof(ScenDev) * ns) || h->grids.alloc(4 * grids.size()) ||
       h->scratch.alloc(sizeof(double) * 4 * 4096))
     return fail(DGSWE_ENOMEM, "device allocation failed");
   CU(cudaMemcpy(h->rec[0].p, rec.data(), rbytes, cudaMemcpyHostToDevice));
@@ -369,19 +370,43 @@ static int build_layout(dgswe_h h) {
     D.elem_begin = (int32_t)h->eoff[s];
     D.elem_end = (int32_t)(h->eoff[s] + S.m.ne);
     D.rain_kind = S.rain_kind;
-    const double st[8] = {S.storm.x0, S.storm.y0, S.storm.heading, S.storm.speed, S.storm.rpeak, S.storm.rm,
-                          S.storm.re, S.storm.t0};
-    std::memcpy(D.storm, st, sizeof st);
     D.gnx = S.gnx; D.gny = S.gny; D.gnt = S.gnt;
-    D.gx0 = S.gx0; D.gy0 = S.gy0; D.gdx = S.gdx; D.gdy = S.gdy; D.gt0 = S.gt0; D.gdt = S.gdt;
     D.grid = S.rain_kind == 3 ? h->grids.as<float>() + grid_off[s] : nullptr;
     D.nseg = (int32_t)S.tamp.size();
-    for (size_t k = 0; k < S.tamp.size() && k < (size_t)MAXSEG; ++k) {
-      D.tamp[k] = S.tamp[k]; D.tper[k] = S.tper[k]; D.tpha[k] = S.tpha[k];
-    }
     D.press = S.press ? 1 : 0;
-    D.ps[0] = S.ps.x0; D.ps[1] = S.ps.y0; D.ps[2] = S.ps.sigma; D.ps[3] = S.ps.peak;
+    const double st[8] = {S.storm.x0, S.storm.y0, S.storm.speed * std::cos(S.storm.heading),
+                          S.storm.speed * std::sin(S.storm.heading), S.storm.rpeak, S.storm.rm, S.storm.re, S.storm.t0};
+    const double gr[6] = {S.gx0, S.gy0, 1.0 / S.gdx, 1.0 / S.gdy, S.gt0, 1.0 / S.gdt};
+    const double ps[4] = {S.ps.x0, S.ps.y0, S.ps.sigma, S.ps.peak};
+    for (int k = 0; k < 8; ++k) { D.d.storm[k] = st[k]; D.f.storm[k] = (float)st[k]; }
+    for (int k = 0; k < 6; ++k) { D.d.grid[k] = gr[k]; D.f.grid[k] = (float)gr[k]; }
+    for (int k = 0; k < 4; ++k) { D.d.ps[k] = ps[k]; D.f.ps[k] = (float)ps[k]; }
+    for (size_t k = 0; k < S.tamp.size() && k < (size_t)MAXSEG; ++k) {
+      // FP64: amp sin(omega t + phase); FP32: amp sin(2 pi frac(t / period + phase / (2 pi)))
+      D.d.tide[k][0] = S.tamp[k];
+      D.d.tide[k][1] = 2.0 * M_PI / S.tper[k];
+      D.d.tide[k][2] = S.tpha[k];
+      D.f.tide[k][0] = (float)S.tamp[k];
+      D.f.tide[k][1] = (float)(1.0 / S.tper[k]);
+      D.f.tide[k][2] = (float)(S.tpha[k] / (2.0 * M_PI));
+    }
   }
+  // scenario of each 32-element tile; ledger slots per scenario cover the widest launch
+  h->ntiles = (int)(E / TILE);
+  std::vector<int32_t> ts(h->ntiles, 0);
+  for (size_t s = 0; s < ns; ++s) {
+    const long long t0 = h->eoff[s] / TILE;
+    const long long t1 = (h->eoff[s] + (h->sc[s].m.ne + TILE_ALIGN - 1) / TILE_ALIGN * TILE_ALIGN) / TILE;
+    for (long long t = t0; t < t1 && t < h->ntiles; ++t) ts[t] = (int32_t)s;
+  }
+  int sms = 0;
+  CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+  h->wslots = sms * 64 * 2;
+  if (h->tile_scen.alloc(4 * (size_t)h->ntiles) || h->ledger.alloc(16 * (size_t)h->wslots * ns))
+    return fail(DGSWE_ENOMEM, "device allocation failed");
+  CU(cudaMemcpy(h->tile_scen.p, ts.data(), 4 * ts.size(), cudaMemcpyHostToDevice));
+  CU(cudaMemset(h->ledger.p, 0, 16 * (size_t)h->wslots * ns));
+  h->wcur = 0;
   CU(cudaMemcpy(h->scen.p, sd.data(), sizeof(ScenDev) * ns, cudaMemcpyHostToDevice));
   h->led_rain.assign(ns, 0.0);
   h->led_bdry.assign(ns, 0.0);
@@ -398,7 +423,10 @@ static int upload_dt(dgswe_h h) {
   for (size_t s = 0; s < sd.size(); ++s) {
     ScenDev& D = sd[s];
     D.dt = h->sc[s].dt;
-    split_ff(D.dt, D.dt_hi, D.dt_lo);
+    D.d.t0 = D.t0;
+    D.d.dt = D.dt;
+    D.f.t0 = (float)D.t0;
+    D.f.dt = (float)D.dt;
     for (size_t k = 0; k < h->stages.size(); ++k) {
       D.bdt[k] = h->stages[k].beta * D.dt;
       split_ff(D.bdt[k], D.bdt_hi[k], D.bdt_lo[k]);
@@ -409,34 +437,19 @@ static int upload_dt(dgswe_h h) {
   return 0;
 }
 
-// tile -> scenario map for the current block size
-static int set_tiling(dgswe_h h, int block) {
-  // fold the ledger partials of the current tiling into the host accumulators
-  if (h->ntiles > 0) {
-    std::vector<double> part(2 * (size_t)h->ntiles);
-    CU(cudaMemcpy(part.data(), h->ledger.p, 16 * (size_t)h->ntiles, cudaMemcpyDeviceToHost));
-    for (size_t s = 0; s < h->sc.size(); ++s) {
-      const long long t0 = h->eoff[s] / h->block, t1 = (h->eoff[s] + h->sc[s].m.ne + h->block - 1) / h->block;
-      for (long long t = t0; t < t1; ++t) { h->led_rain[s] += part[2 * t]; h->led_bdry[s] += part[2 * t + 1]; }
-    }
+// launch shape change: fold the ledger slots of the old shape into the host accumulators
+static int fold_ledger(dgswe_h h) {
+  if (h->wcur > 0) {
+    const size_t ns = h->sc.size();
+    std::vector<double> part(2 * (size_t)h->wslots * ns);
+    CU(cudaMemcpy(part.data(), h->ledger.p, 8 * part.size(), cudaMemcpyDeviceToHost));
+    for (size_t s = 0; s < ns; ++s)
+      for (int w = 0; w < h->wcur; ++w) {
+        h->led_rain[s] += part[2 * (s * h->wslots + w)];
+        h->led_bdry[s] += part[2 * (s * h->wslots + w) + 1];
+      }
+    CU(cudaMemset(h->ledger.p, 0, 8 * part.size()));
   }
-  h->block = block;
-  h->ntiles = (int)(h->E / block);
-  std::vector<int32_t> ts(h->ntiles, 0);
-  for (size_t s = 0; s < h->sc.size(); ++s) {
-    const long long t0 = h->eoff[s] / block, t1 = (h->eoff[s] + TILE_ALIGN - 1 + h->sc[s].m.ne) / TILE_ALIGN * TILE_ALIGN / block;
-    for (long long t = t0; t < t1 && t < h->ntiles; ++t) ts[t] = (int32_t)s;
-  }
-  CU(cudaMemcpy(h->tile_scen.p, ts.data(), 4 * ts.size(), cudaMemcpyHostToDevice));
-  CU(cudaMemset(h->ledger.p, 0, 16 * (size_t)h->ntiles));
-  // tile ranges in the scenario blocks
-  std::vector<ScenDev> sd(h->sc.size());
-  CU(cudaMemcpy(sd.data(), h->scen.p, sizeof(ScenDev) * sd.size(), cudaMemcpyDeviceToHost));
-  for (size_t s = 0; s < sd.size(); ++s) {
-    sd[s].tile_begin = (int32_t)(h->eoff[s] / block);
-    sd[s].tile_end = (int32_t)((h->eoff[s] + h->sc[s].m.ne + block - 1) / block);
-  }
-  CU(cudaMemcpy(h->scen.p, sd.data(), sizeof(ScenDev) * sd.size(), cudaMemcpyHostToDevice));
   if (h->g1) { cudaGraphExecDestroy(h->g1); h->g1 = nullptr; }
   if (h->gK) { cudaGraphExecDestroy(h->gK); h->gK = nullptr; }
   return 0;
@@ -463,9 +476,11 @@ static StageArgs<Pol> make_args(dgswe_h h, int stage, int tune) {
   a.ledger = h->ledger.as<double>();
   a.ctl = h->ctl.as<Ctl>();
   a.ntiles = h->ntiles;
+  a.wslots = h->wslots;
   a.stage = stage;
   a.last = (stage == S - 1) ? 1 : 0;
-  a.persistent = h->persistent;
+  a.has_n = st.a_n != 0.0 ? 1 : 0;
+  a.cst_f = (float)st.c;
   a.tune = tune;
   a.friction = h->prm.friction;
   split_ff(st.a_n, a.a_n_hi, a.a_n_lo);
@@ -479,13 +494,8 @@ static StageArgs<Pol> make_args(dgswe_h h, int stage, int tune) {
   return a;
 }
 
-static int grid_size(dgswe_h h) {
-  if (!h->persistent) return h->ntiles;
-  return std::max(1, std::min(h->ntiles, h->grid_persistent));
-}
-
 static int launch_stage_once(dgswe_h h, int stage, int tune, cudaStream_t s) {
-  const int grid = grid_size(h);
+  const int grid = h->grid;
   cudaError_t e;
   if (mixed(h)) e = launch_stage<Mixed>(h->prm.p, h->prm.flux, make_args<Mixed>(h, stage, tune), grid, h->block, s);
   else e = launch_stage<Fp64>(h->prm.p, h->prm.flux, make_args<Fp64>(h, stage, tune), grid, h->block, s);
@@ -499,12 +509,19 @@ static int occupancy(dgswe_h h, int block) {
                   : stage_blocks_per_sm<Fp64>(h->prm.p, h->prm.flux, block);
 }
 
-static int apply_launch(dgswe_h h, int block, int persistent) {
+// grid = SMs x resident CTAs per SM x waves; its warps take the 32-element tiles round-robin
+static int apply_launch(dgswe_h h, int block, int waves) {
   int sms = 0;
   CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
-  h->persistent = persistent;
-  h->grid_persistent = sms * std::max(1, occupancy(h, block));
-  return set_tiling(h, block);
+  if (int rc = fold_ledger(h)) return rc;
+  h->block = block;
+  h->waves = waves;
+  const int want = sms * std::max(1, occupancy(h, block)) * waves;
+  const int need = (h->ntiles + block / 32 - 1) / (block / 32);  // one tile per warp
+  h->grid = std::max(1, std::min(want, need));
+  h->wcur = h->grid * (block / 32);
+  if (h->wcur > h->wslots) return fail(DGSWE_EINVAL, "launch shape needs %d ledger slots, %d allocated", h->wcur, h->wslots);
+  return 0;
 }
 
 // time the first stage (which reads w^n and writes a scratch buffer) for each launch shape
@@ -515,7 +532,7 @@ static int autotune(dgswe_h h) {
   float best = 1e30f;
   int bb = 128, bp = 0;
   const int blocks[3] = {64, 128, 256};
-  for (int pi = 0; pi < 2; ++pi)
+  for (int pi = 1; pi <= 2; ++pi)
     for (int bi = 0; bi < 3; ++bi) {
       if (occupancy(h, blocks[bi]) < 1) continue;
       if (int rc = apply_launch(h, blocks[bi], pi)) return rc;
@@ -618,8 +635,7 @@ static int prepare(dgswe_h h) {
     if (int rc = reduce_volume(h, s, h->V0[s], h->VH0[s])) return rc;
   }
   if (int rc = upload_dt(h)) return rc;
-  h->ntiles = 0;
-  if (int rc = apply_launch(h, h->block, h->persistent)) return rc;
+  if (int rc = apply_launch(h, h->block, h->waves)) return rc;
   CU(cudaStreamSynchronize(h->stream));
   h->ready = true;
   return 0;
@@ -977,18 +993,18 @@ static int ledger_of(dgswe_h h, size_t s, dgswe_ledger* out) {
   (void)VH;
   Ctl c;
   CU(cudaMemcpy(&c, h->ctl.p, sizeof c, cudaMemcpyDeviceToHost));
-  std::vector<double> part(2 * (size_t)h->ntiles);
-  CU(cudaMemcpy(part.data(), h->ledger.p, 16 * (size_t)h->ntiles, cudaMemcpyDeviceToHost));
+  std::vector<double> part(2 * (size_t)h->wcur);
+  CU(cudaMemcpy(part.data(), h->ledger.as<double>() + 2 * (size_t)s * h->wslots, 16 * (size_t)h->wcur,
+                cudaMemcpyDeviceToHost));
   double rs = h->led_rain[s], rc_ = 0.0, bs = h->led_bdry[s], bc = 0.0;
   auto neu = [](double& sum, double& comp, double v) {
     const double t = sum + v;
     comp += (std::fabs(sum) >= std::fabs(v)) ? (sum - t) + v : (v - t) + sum;
     sum = t;
   };
-  const long long t0 = h->eoff[s] / h->block, t1 = (h->eoff[s] + h->sc[s].m.ne + h->block - 1) / h->block;
-  for (long long t = t0; t < t1; ++t) {
-    neu(rs, rc_, part[2 * t]);
-    neu(bs, bc, part[2 * t + 1]);
+  for (int w = 0; w < h->wcur; ++w) {
+    neu(rs, rc_, part[2 * w]);
+    neu(bs, bc, part[2 * w + 1]);
   }
   out->steps = (int64_t)c.step;
   out->t = h->sc[s].t0 + (double)c.step * h->sc[s].dt;
@@ -1076,28 +1092,29 @@ int dgswe_ensemble_get_ledger(dgswe_h ens, int32_t i, dgswe_ledger* out) {
   return ledger_of(ens, (size_t)i, out);
 }
 
-int dgswe_set_launch(dgswe_h h, int32_t block, int32_t persistent) {
+int dgswe_set_launch(dgswe_h h, int32_t block, int32_t waves) {
   if (int rc = check_handle(h)) return rc;
   if (block != 0 && block != 64 && block != 128 && block != 256) return fail(DGSWE_EINVAL, "block must be 0, 64, 128 or 256");
   if (block == 0) {
     h->autotune = true;
     return 0;
   }
+  if (waves < 1 || waves > 2) return fail(DGSWE_EINVAL, "waves must be 1 or 2");
   h->autotune = false;
   if (!h->ready) {
     h->block = block;
-    h->persistent = persistent ? 1 : 0;
+    h->waves = waves;
     return 0;
   }
   DeviceGuard dg_(h->device);
   CU(cudaStreamSynchronize(h->stream));
-  return apply_launch(h, block, persistent ? 1 : 0);
+  return apply_launch(h, block, waves);
 }
 
-int dgswe_get_launch(dgswe_h h, int32_t* block, int32_t* persistent) {
+int dgswe_get_launch(dgswe_h h, int32_t* block, int32_t* waves) {
   if (int rc = check_handle(h)) return rc;
   if (block) *block = h->block;
-  if (persistent) *persistent = h->persistent;
+  if (waves) *waves = h->waves;
   return 0;
 }
 

@@ -35,19 +35,21 @@ struct StageArgs {
   const double* hb_nodal;  // [nodes] FP64 bathymetry (depth test near H0)
   const T* rain_e;         // [elements] constant element rain (rain_kind 1)
   const ScenDev* scen;
-  const int32_t* tile_scen;
-  double* ledger;          // [tiles][2]: rain volume, boundary inflow volume
+  const int32_t* tile_scen;  // scenario of each 32-element tile
+  double* ledger;          // [scenario][wslots][2]: rain volume, boundary inflow volume per warp
   Ctl* ctl;
-  int ntiles;
+  int ntiles;              // 32-element tiles, processed round-robin by the launch's warps
+  int wslots;              // ledger slots per scenario (>= warps of the launch)
   int stage;               // Shu-Osher stage index
   int last;                // 1 on the final stage of a step
-  int persistent;
   int tune;                // 1: timing run, no ledger or step bookkeeping
   int classify_only;       // prepare pass: derive depth and dry flag, keep the state as given
   int friction;            // 0 Manning, 1 quadratic, 2 none
+  int has_n;               // the stage combines with the step-initial state
   float a_n_hi, a_n_lo, a_in_hi, a_in_lo;  // Shu-Osher coefficients as float-float
   double a_n, a_in;
-  double cst;              // stage time as a fraction of dt
+  float cst_f;             // stage time as a fraction of dt
+  double cst;
   T g, H0, cf;
 };
 

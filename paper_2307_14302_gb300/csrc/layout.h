@@ -27,6 +27,7 @@ constexpr int MAXNP = 6;
 constexpr int MAXNQ = 7;
 constexpr int MAXNG = 3;
 constexpr int TILE_ALIGN = 256;  // scenario element ranges start on multiples of this
+constexpr int TILE = 32;         // elements per warp tile
 
 enum : uint32_t { FLAG_DRY = 1u };
 enum : int { ERR_NONFINITE = 1, ERR_NEGDEPTH = 2 };
@@ -54,24 +55,30 @@ struct RefTab {
   T phi0;                          // constant mode value 1/sqrt(2)
 };
 
+// per-scenario forcing constants in the arithmetic type of a path
+template <typename T>
+struct ForcingT {
+  T t0, dt;                        // stage time = t0 + (step + c) dt
+  T storm[8];                      // x0, y0, speed cos(heading), speed sin(heading), rpeak, rm, re, t0
+  T tide[MAXSEG][3];               // amplitude, 2 pi / period, phase
+  T grid[6];                       // x0, y0, 1/dx, 1/dy, t0, 1/dt_rec
+  T ps[4];                         // pressure set-up x0, y0, sigma, peak
+};
+
 // per-scenario parameters (device array; an ensemble holds several)
 struct ScenDev {
   double t0, dt;
-  float dt_hi, dt_lo;
   float bdt_hi[3], bdt_lo[3];      // beta_s * dt of each Shu-Osher stage, float-float
   double bdt[3];                   // same in double
   double bw[3];                    // weight of stage s in the final combination (ledger)
   int32_t elem_begin, elem_end;
-  int32_t tile_begin, tile_end;
   int32_t rain_kind;               // 0 none, 1 constant per element, 2 storm, 3 grid
   int32_t gnx, gny, gnt;
-  double storm[8];                 // x0 y0 heading speed rpeak rm re t0
-  double gx0, gy0, gdx, gdy, gt0, gdt;
-  const float* grid;               // [gnt][gny][gnx] mm/h
   int32_t nseg;
   int32_t press;
-  double tamp[MAXSEG], tper[MAXSEG], tpha[MAXSEG];
-  double ps[4];                    // pressure set-up x0 y0 sigma peak
+  const float* grid;               // [gnt][gny][gnx] mm/h
+  ForcingT<float> f;
+  ForcingT<double> d;
 };
 
 // device control block

@@ -121,6 +121,40 @@ __device__ __forceinline__ double cos_r(double x) { return cos(x); }
 __device__ __forceinline__ float pow43_r(float h) { return h * cbrtf(h); }
 __device__ __forceinline__ double pow43_r(double h) { return h * cbrt(h); }
 
+// FP32 path: hardware approximations (MUFU, a few ulp, deterministic); FP64 path: exact
+__device__ __forceinline__ float frcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double frcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float fsqrt_pos(float x) { return x * rsqrtf(x); }  // x > 0
+__device__ __forceinline__ double fsqrt_pos(double x) { return sqrt(x); }
+__device__ __forceinline__ float fsqrt0(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+__device__ __forceinline__ double fsqrt0(double x) { return sqrt(x); }
+// H^{-4/3}
+__device__ __forceinline__ float fpowm43(float h) { return exp2f(-1.3333333f * __log2f(h)); }
+__device__ __forceinline__ double fpowm43(double h) { return 1.0 / (h * cbrt(h)); }
+__device__ __forceinline__ float fexp(float x) { return __expf(x); }
+__device__ __forceinline__ double fexp(double x) { return exp(x); }
+__device__ __forceinline__ float fsin(float x) { return __sinf(x); }
+__device__ __forceinline__ double fsin(double x) { return sin(x); }
+
+// tidal elevation: FP32 reduces the phase to [-1/2, 1/2] turns before the hardware sine
+__device__ __forceinline__ float tide_at(const ForcingT<float>& F, int k, float t) {
+  float u = fmaf(t, F.tide[k][1], F.tide[k][2]);
+  u -= rintf(u);
+  return F.tide[k][0] * __sinf(6.2831853f * u);
+}
+__device__ __forceinline__ double tide_at(const ForcingT<double>& F, int k, double t) {
+  return F.tide[k][0] * sin(F.tide[k][1] * t + F.tide[k][2]);
+}
+
+template <class T>
+__device__ __forceinline__ const ForcingT<T>& forcing(const ScenDev& S);
+template <>
+__device__ __forceinline__ const ForcingT<float>& forcing<float>(const ScenDev& S) { return S.f; }
+template <>
+__device__ __forceinline__ const ForcingT<double>& forcing<double>(const ScenDev& S) { return S.d; }
+
 // -------------------------------------------------------------------- precision policy ---
 struct Mixed {
   using T = float;
@@ -355,7 +389,7 @@ template <int FLUX, class T>
 __device__ __forceinline__ void edge_flux(const Trace<T>& L, const Trace<T>& R, T dcRL, T nx, T ny, T g, T H0, T& fz,
                                           T& fx, T& fy) {
   T HsL = max_r(L.H, H0), HsR = max_r(R.H, H0);
-  T iL = rcp_r(HsL), iR = rcp_r(HsR);
+  T iL = frcp(HsL), iR = frcp(HsR);
   T uL = L.qx * iL, vL = L.qy * iL, uR = R.qx * iR, vR = R.qy * iR;
   T unL = uL * nx + vL * ny, unR = uR * nx + vR * ny;
   T mL = L.qx * nx + L.qy * ny, mR = R.qx * nx + R.qy * ny;
@@ -365,18 +399,18 @@ __device__ __forceinline__ void edge_flux(const Trace<T>& L, const Trace<T>& R, 
   T cy = T(0.5) * (L.qy * unL + R.qy * unR);
   T cz = T(0.5) * (mL + mR);
   if (FLUX == 1) {  // local Lax-Friedrichs
-    T lam = max_r(abs_r(unL) + sqrt_r(g * HsL), abs_r(unR) + sqrt_r(g * HsR));
+    T lam = max_r(abs_r(unL) + fsqrt_pos(g * HsL), abs_r(unR) + fsqrt_pos(g * HsR));
     fz = cz - T(0.5) * lam * dz;
     fx = cx - T(0.5) * lam * dqx;
     fy = cy - T(0.5) * lam * dqy;
     return;
   }
   // Roe: averages (arithmetic depth, sqrt-depth-weighted velocity), eigen-decomposition
-  T sL = sqrt_r(HsL), sR = sqrt_r(HsR);
-  T is = rcp_r(sL + sR);
+  T sL = fsqrt_pos(HsL), sR = fsqrt_pos(HsR);
+  T is = frcp(sL + sR);
   T ut = (sL * uL + sR * uR) * is, vt = (sL * vL + sR * vR) * is;
-  T c = sqrt_r(g * T(0.5) * (HsL + HsR));
-  T ic = rcp_r(c);
+  T c = fsqrt_pos(g * T(0.5) * (HsL + HsR));
+  T ic = frcp(c);
   T utn = ut * nx + vt * ny, utt = vt * nx - ut * ny;
   T dqn = dqx * nx + dqy * ny, dqt = dqy * nx - dqx * ny;
   T w = (dqn - utn * dz) * ic;
@@ -478,37 +512,53 @@ __device__ bool positivity_fp64(double zbar, double& xbar, double& ybar, double*
   return nd > 0;
 }
 
-// positive-depth operator on a freshly combined element; sets E.Hb and the dry flag
+// positive-depth operator on a freshly combined element; sets E.Hb and the dry flag.
+// FP32 path: vertex depths are first bounded in FP32; an element clearly above H0 at every
+// vertex is case 1 (unchanged, wet), one whose mean depth is clearly below H0 with a vertex
+// clearly below H0 is case 2 (flat depth, dry, no momentum: the zeta slopes become minus the
+// bathymetry slopes).  Only elements near the threshold take the FP64 operator.
 template <int P, class Pol>
 __device__ __forceinline__ void apply_positivity(Elem<P, Pol>& E, const Geo<Pol>& G, long long e,
                                                  const StageArgs<Pol>& a, int* err) {
   using T = typename Pol::T;
   constexpr int NS = np_of(P) - 1;
   const RefTab<T>& tab = ctab<T, P>();
-  T H0 = a.H0;
-  bool need64 = true;
-  typename Pol::Acc Hbar = acc_add(E.zb, G.hbm);
-  T Hb = acc_r(Hbar);
+  const T H0 = a.H0;
+  const typename Pol::Acc Hbar = acc_add(E.zb, G.hbm);
+  const T Hb = acc_r(Hbar);
+  bool need64 = true, dry = false;
   if (sizeof(T) == 4) {
-    // FP32 filter: if every vertex depth is clearly above H0 the operator is the identity
     T hmin = T(3.0e38), bound = abs_r(Hb);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      T s = Hb, b = 0;
+      T v = Hb, b = 0;
 #pragma unroll
       for (int m = 0; m < NS; ++m) {
-        s = fma(E.zs[m], tab.vphi[i][m + 1], s);
+        v = fma(E.zs[m], tab.vphi[i][m + 1], v);
         b += abs_r(E.zs[m] * tab.vphi[i][m + 1]);
       }
-      s = fma(E.hb1, tab.vphi[i][1], s);
-      s = fma(E.hb2, tab.vphi[i][2], s);
+      v = fma(E.hb1, tab.vphi[i][1], v);
+      v = fma(E.hb2, tab.vphi[i][2], v);
       b += abs_r(E.hb1 * tab.vphi[i][1]) + abs_r(E.hb2 * tab.vphi[i][2]);
-      hmin = fminf(hmin, s);
+      hmin = fminf(hmin, v);
       bound = fmaxf(bound, b);
     }
-    need64 = !(hmin - T(4.0e-6) * (abs_r(Hb) + bound) > H0);
+    const T tol = T(4.0e-6) * (abs_r(Hb) + bound);
+    if (hmin - tol > H0) {
+      need64 = false;  // case 1
+    } else if (Hb < H0 * T(0.99999) && hmin + tol < H0 && Hb >= T(0)) {
+      need64 = false;  // case 2
+      dry = true;
+      E.zs[0] = -E.hb1;
+      E.zs[1] = -E.hb2;
+#pragma unroll
+      for (int m = 2; m < NS; ++m) E.zs[m] = T(0);
+#pragma unroll
+      for (int m = 0; m < NS; ++m) E.xs[m] = E.ys[m] = T(0);
+      E.xb = acc_make<typename Pol::Acc>(0.f, 0.f, 0.0);
+      E.yb = acc_make<typename Pol::Acc>(0.f, 0.f, 0.0);
+    }
   }
-  bool dry = false;
   if (need64) {
     double zs[NS], xs[NS], ys[NS];
 #pragma unroll
@@ -561,6 +611,26 @@ __device__ __forceinline__ void warp_reduce2(ff& a, ff& b) {
 }
 
 // ------------------------------------------------------------------------ stage kernel ----
+// Work split: 32-element tiles, warp w of the launch takes tiles w, w + W, w + 2W, ... (W warps
+// in the grid).  No block-wide barrier inside the loop; rain and boundary volumes accumulate per
+// lane and are reduced per warp when the warp moves to another scenario and at the end, into
+// ledger slot (scenario, warp): deterministic for a fixed launch shape.
+template <int P, class Pol>
+__device__ __forceinline__ void flush_ledger(const StageArgs<Pol>& a, int sc, long long gw, typename Pol::Acc& r,
+                                             typename Pol::Acc& b) {
+  using Acc = typename Pol::Acc;
+  warp_reduce2(r, b);
+  if ((threadIdx.x & 31) == 0) {
+    const ScenDev& S = a.scen[sc];
+    const double wdt = S.bw[a.stage] * S.dt;
+    double* L = a.ledger + 2 * ((long long)sc * a.wslots + gw);
+    L[0] += wdt * acc_d(r);
+    L[1] += wdt * acc_d(b);
+  }
+  r = acc_make<Acc>(0.f, 0.f, 0.0);
+  b = acc_make<Acc>(0.f, 0.f, 0.0);
+}
+
 template <int P, int FLUX, class Pol>
 __global__ void __launch_bounds__(256) stage_kernel(const StageArgs<Pol> a) {
   using T = typename Pol::T;
@@ -570,381 +640,311 @@ __global__ void __launch_bounds__(256) stage_kernel(const StageArgs<Pol> a) {
   constexpr int NQ = (P == 0) ? 1 : 7;
   const RefTab<T>& tab = ctab<T, P>();
 
-  __shared__ int s_tile;
-  __shared__ T s_zbc[MAXSEG];
-  __shared__ T s_storm[2];
-  __shared__ double s_t;
-  __shared__ Acc s_red[2][8];
   __shared__ T s_ephi[3][NG][NP];  // edge basis values, read at neighbour-dependent indices
-
   const int tid = threadIdx.x;
   for (int i = tid; i < 3 * NG * NP; i += blockDim.x) {
     const int j = i / (NG * NP), k = (i / NP) % NG, m = i % NP;
     s_ephi[j][k][m] = tab.ephi[j][k][m];
   }
-  for (int iter = 0;; ++iter) {
-    int tile;
-    if (a.persistent) {
-      if (tid == 0) s_tile = (int)atomicAdd(&a.ctl->tile_counter, 1u);
-      __syncthreads();
-      tile = s_tile;
-      __syncthreads();
-    } else {
-      if (iter > 0) break;
-      tile = blockIdx.x;
+  __syncthreads();
+
+  const int lane = tid & 31;
+  const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + (tid >> 5);
+  const long long W = (long long)gridDim.x * (blockDim.x >> 5);
+  const T stepc = (T)a.ctl->step + (sizeof(T) == 4 ? (T)a.cst_f : (T)a.cst);
+  const T g = a.g, H0 = a.H0;
+  Acc rain_acc = acc_make<Acc>(0.f, 0.f, 0.0), bdry_acc = acc_make<Acc>(0.f, 0.f, 0.0);
+  int cur = -1;
+
+  for (long long tile = gw; tile < a.ntiles; tile += W) {
+    const int sc = a.tile_scen[tile];
+    if (sc != cur) {
+      if (cur >= 0 && !a.tune) flush_ledger<P, Pol>(a, cur, gw, rain_acc, bdry_acc);
+      cur = sc;
     }
-    if (tile >= a.ntiles) break;
-    const ScenDev& S = a.scen[a.tile_scen[tile]];
-    // per-tile uniform quantities: stage time, storm centre, tidal elevations
-    if (tid == 0) {
-      const double t = S.t0 + ((double)a.ctl->step + a.cst) * S.dt;
-      s_t = t;
-      if (S.rain_kind == 2) {
-        const double tt = t - S.storm[7];
-        s_storm[0] = (T)(S.storm[0] + S.storm[3] * tt * cos(S.storm[2]));
-        s_storm[1] = (T)(S.storm[1] + S.storm[3] * tt * sin(S.storm[2]));
-      }
-      for (int k = 0; k < S.nseg && k < MAXSEG; ++k)
-        s_zbc[k] = (T)(S.tamp[k] * sin(6.283185307179586 * t / S.tper[k] + S.tpha[k]));
-    }
-    __syncthreads();
+    const ScenDev& S = a.scen[sc];
+    const ForcingT<T>& F = forcing<T>(S);
+    const long long e = tile * TILE + lane;
+    if (e >= S.elem_end) continue;
+    const T t = F.t0 + stepc * F.dt;
 
-    const long long e = (long long)tile * blockDim.x + tid;
-    Acc rain_vol = acc_make<Acc>(0.f, 0.f, 0.0), bdry_vol = acc_make<Acc>(0.f, 0.f, 0.0);
-    if (e < S.elem_end) {
-      const T g = a.g, H0 = a.H0;
-      const int4 nb = __ldg(a.nbr + e);
-      Geo<Pol> G;
-      load_geo(a.geo, e, nb, G);
-      Raw<RV> rme;
-      load_raw<RV>(a.in, e, rme);
-      Elem<P, Pol> E;
-      unpack<P>(rme, E);
-      const bool dry_me = (E.flags & FLAG_DRY) != 0;
-      const T detJ = T(0.5) * acc_r(G.A);
-      const T idetJ = T(2) * acc_r(G.invA);
-      // inverse Jacobian from the edge vectors: t0 = x1 - x0 = 2 (xr, yr), t2 = x0 - x2 = -2 (xs, ys)
-      // and ln_j = (t_j.y, -t_j.x)
-      const T xr = T(-0.5) * G.lny[0], yr = T(0.5) * G.lnx[0];
-      const T xs = T(0.5) * G.lny[2], ys = T(-0.5) * G.lnx[2];
-      const T rx = ys * idetJ, ry = -xs * idetJ, sx = -yr * idetJ, sy = xr * idetJ;
+    const int4 nb = __ldg(a.nbr + e);
+    Geo<Pol> G;
+    load_geo(a.geo, e, nb, G);
+    Raw<RV> rme;
+    load_raw<RV>(a.in, e, rme);
+    Elem<P, Pol> E;
+    unpack<P>(rme, E);
+    const bool dry_me = (E.flags & FLAG_DRY) != 0;
+    const T detJ = T(0.5) * acc_r(G.A);
+    const T idetJ = T(2) * acc_r(G.invA);
+    // inverse Jacobian from the edge vectors: t0 = x1 - x0 = 2 (xr, yr), t2 = x0 - x2 = -2 (xs, ys)
+    // and ln_j = (t_j.y, -t_j.x)
+    const T xr = T(-0.5) * G.lny[0], yr = T(0.5) * G.lnx[0];
+    const T xs = T(0.5) * G.lny[2], ys = T(-0.5) * G.lnx[2];
+    const T rx = ys * idetJ, ry = -xs * idetJ, sx = -yr * idetJ, sy = xr * idetJ;
 
-      // right-hand side accumulators: integrals of the weak form against each basis function
-      T Rz[NP], Rx[NP], Ry[NP];
+    T Rz[NP], Rx[NP], Ry[NP];  // weak-form integrals against each basis function
 #pragma unroll
-      for (int m = 0; m < NP; ++m) Rz[m] = Rx[m] = Ry[m] = 0;
-      Acc massout = acc_make<Acc>(0.f, 0.f, 0.0);  // edge mass outflow (volume per second)
+    for (int m = 0; m < NP; ++m) Rz[m] = Rx[m] = Ry[m] = 0;
+    Acc massout = acc_make<Acc>(0.f, 0.f, 0.0);  // edge mass outflow (volume per second)
 
-      // ---- 1. edge integrals
+    // ---- 1. edge integrals <Fhat.n, v>
+#pragma unroll 1
+    for (int j = 0; j < 3; ++j) {
+      const int code = (j == 0) ? nb.x : (j == 1 ? nb.y : nb.z);
+      const T lnx = (j == 0) ? G.lnx[0] : (j == 1 ? G.lnx[1] : G.lnx[2]);
+      const T lny = (j == 0) ? G.lny[0] : (j == 1 ? G.lny[1] : G.lny[2]);
+      const T len = fsqrt_pos(lnx * lnx + lny * lny);
+      const T il = frcp(len);
+      const T nx = lnx * il, ny = lny * il;
+      Trace<T> tm[NG], to[NG];  // my trace and the other side's, at my edge points
 #pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        const int code = (j == 0) ? nb.x : (j == 1 ? nb.y : nb.z);
-        const T lnx = G.lnx[j], lny = G.lny[j];
-        const T len = sqrt_r(lnx * lnx + lny * lny);
-        const T il = rcp_r(len);
-        const T nx = lnx * il, ny = lny * il;
-        T Fz[NG], Fx[NG], Fy[NG];  // flux along my outward normal at my edge points
-        Trace<T> tm[NG];
+      for (int k = 0; k < NG; ++k) tm[k] = trace_at<P, Pol>(E, s_ephi[j][k]);
+      bool me_L = true, wall = (code == -1), dry_o = false;
+      T dcRL = 0, dc_nm = 0;
+      if (code >= 0) {
+        const long long ne_ = code >> 2;
+        const int jn = code & 3;
+        Raw<RV> rnb;
+        load_raw<RV>(a.in, ne_, rnb);
+        Elem<P, Pol> N;
+        unpack<P>(rnb, N);
+        me_L = e < ne_;
+        dc_nm = acc_diff(N.zb, E.zb);                   // c_nb - c_me
+        dcRL = me_L ? dc_nm : acc_diff(E.zb, N.zb);     // c_R - c_L
+        dry_o = (N.flags & FLAG_DRY) != 0;
 #pragma unroll
-        for (int k = 0; k < NG; ++k) tm[k] = trace_at<P, Pol>(E, tab.ephi[j][k]);
-        if (code >= 0) {
-          const long long ne_ = code >> 2;
-          const int jn = code & 3;
-          Raw<RV> rnb;
-          load_raw<RV>(a.in, ne_, rnb);
-          Elem<P, Pol> N;
-          unpack<P>(rnb, N);
-          const bool me_L = e < ne_;
-          const T sgn = me_L ? T(1) : T(-1);
-          const T dc_nm = acc_diff(N.zb, E.zb);                 // c_nb - c_me
-          const T dcRL = me_L ? dc_nm : acc_diff(E.zb, N.zb);   // c_R - c_L
-          const T cnx = sgn * nx, cny = sgn * ny;               // L's outward normal
-          T fzc[NG], fxc[NG], fyc[NG];                          // canonical fluxes at my points
-          Trace<T> tn[NG];
-#pragma unroll
-          for (int k = 0; k < NG; ++k) {
-            tn[k] = trace_at<P, Pol>(N, s_ephi[jn][NG - 1 - k]);  // same physical point
-            const Trace<T> tL = me_L ? tm[k] : tn[k];
-            const Trace<T> tR = me_L ? tn[k] : tm[k];
-            edge_flux<FLUX, T>(tL, tR, dcRL, cnx, cny, g, H0, fzc[k], fxc[k], fyc[k]);
-          }
-          // edge mass flux integral in L's point order (identical bits on both sides)
-          T ecanon = 0;
-#pragma unroll
-          for (int kc = 0; kc < NG; ++kc) {
-            const T f = me_L ? fzc[kc] : fzc[NG - 1 - kc];
-            ecanon = fma(tab.gw[kc], f, ecanon);
-          }
-          ecanon = ecanon * (T(0.5) * len);
-          const bool dry_nb = (N.flags & FLAG_DRY) != 0;
-          const bool dry_L = me_L ? dry_me : dry_nb;
-          const bool dry_R = me_L ? dry_nb : dry_me;
-          const bool closed = (dry_L && ecanon > T(0)) || (dry_R && ecanon < T(0));
-          if (!closed) {
-            massout = acc_addr(massout, sgn * ecanon);
-#pragma unroll
-            for (int k = 0; k < NG; ++k) {
-              const T dn = tn[k].d + dc_nm;  // neighbour elevation relative to my mean
-              const T p = T(0.5) * (pdev(tm[k].d, tm[k].H, g) + pdev(dn, tn[k].H, g));
-              Fz[k] = sgn * fzc[k];
-              Fx[k] = sgn * fxc[k] + p * nx;
-              Fy[k] = sgn * fyc[k] + p * ny;
-            }
-          } else {
-#pragma unroll
-            for (int k = 0; k < NG; ++k) {  // closed edge: wall built from my own trace
-              const Trace<T> t = tm[k];
-              const T qn = t.qx * nx + t.qy * ny;
-              Trace<T> gh = t;
-              gh.qx = t.qx - T(2) * qn * nx;
-              gh.qy = t.qy - T(2) * qn * ny;
-              T fz, fx, fy;
-              edge_flux<FLUX, T>(t, gh, T(0), nx, ny, g, H0, fz, fx, fy);
-              const T p = pdev(t.d, t.H, g);
-              Fz[k] = 0;
-              Fx[k] = fx + p * nx;
-              Fy[k] = fy + p * ny;
-            }
-          }
-        } else {
-          // boundary: land (-1) mirrors the normal discharge and carries no mass; ocean
-          // (-2 - seg) takes the tidal elevation with the interior discharge
-          const bool land = (code == -1);
-          const int seg = -2 - code;
-          const T zbc = land ? T(0) : s_zbc[seg < MAXSEG ? seg : 0];
-          const T dgh = land ? T(0) : acc_r(acc_addr(acc_neg(E.zb), zbc));  // ghost zeta - c
-          T ebd = 0;
-#pragma unroll
-          for (int k = 0; k < NG; ++k) {
-            const Trace<T> t = tm[k];
-            Trace<T> gh = t;
-            if (land) {
-              const T qn = t.qx * nx + t.qy * ny;
-              gh.qx = t.qx - T(2) * qn * nx;
-              gh.qy = t.qy - T(2) * qn * ny;
-            } else {
-              gh.H = t.H + (dgh - t.d);
-              gh.d = dgh;
-            }
-            T fz, fx, fy;
-            edge_flux<FLUX, T>(t, gh, T(0), nx, ny, g, H0, fz, fx, fy);
-            const T p = T(0.5) * (pdev(t.d, t.H, g) + pdev(gh.d, gh.H, g));
-            Fz[k] = land ? T(0) : fz;
-            Fx[k] = fx + p * nx;
-            Fy[k] = fy + p * ny;
-            ebd = fma(tab.gw[k], Fz[k], ebd);
-          }
-          ebd = ebd * (T(0.5) * len);
-          if (!land && dry_me && ebd > T(0)) {  // closed: a dry element loses no water
-            ebd = 0;
-#pragma unroll
-            for (int k = 0; k < NG; ++k) {
-              const Trace<T> t = tm[k];
-              const T qn = t.qx * nx + t.qy * ny;
-              Trace<T> gh = t;
-              gh.qx = t.qx - T(2) * qn * nx;
-              gh.qy = t.qy - T(2) * qn * ny;
-              T fz, fx, fy;
-              edge_flux<FLUX, T>(t, gh, T(0), nx, ny, g, H0, fz, fx, fy);
-              const T p = pdev(t.d, t.H, g);
-              Fz[k] = 0;
-              Fx[k] = fx + p * nx;
-              Fy[k] = fy + p * ny;
-            }
-          }
-          massout = acc_addr(massout, ebd);
-          bdry_vol = acc_addr(bdry_vol, -ebd);
-        }
-        // lift: R_m -= sum_k w_k (len/2) F_k phi_m(edge j, point k)
+        for (int k = 0; k < NG; ++k) to[k] = trace_at<P, Pol>(N, s_ephi[jn][NG - 1 - k]);  // same point
+      } else if (code < -1) {  // ocean: tidal elevation, interior discharge
+        const int seg = min(-2 - code, MAXSEG - 1);
+        const T zbc = tide_at(F, seg, t);
+        const T dgh = acc_r(acc_addr(acc_neg(E.zb), zbc));  // ghost zeta - my mean
 #pragma unroll
         for (int k = 0; k < NG; ++k) {
-          const T wk = tab.gw[k] * (T(0.5) * len);
+          to[k] = tm[k];
+          to[k].H = tm[k].H + (dgh - tm[k].d);
+          to[k].d = dgh;
+        }
+      }
+      T Fz[NG], Fx[NG], Fy[NG];  // flux along my outward normal at my points
+      T emine = 0;              // mass flux integral along my outward normal
+      if (!wall) {
+        const T sgn = me_L ? T(1) : T(-1);
+        T fzc[NG], fxc[NG], fyc[NG];
 #pragma unroll
-          for (int m = 0; m < NP; ++m) {
-            const T ph = wk * tab.ephi[j][k][m];
-            if (m > 0) Rz[m] = fma(-ph, Fz[k], Rz[m]);
-            Rx[m] = fma(-ph, Fx[k], Rx[m]);
-            Ry[m] = fma(-ph, Fy[k], Ry[m]);
+        for (int k = 0; k < NG; ++k) {
+          const Trace<T> tL = me_L ? tm[k] : to[k];
+          const Trace<T> tR = me_L ? to[k] : tm[k];
+          edge_flux<FLUX, T>(tL, tR, dcRL, sgn * nx, sgn * ny, g, H0, fzc[k], fxc[k], fyc[k]);
+        }
+        T ecanon = 0;  // in L's point order: identical bits on both sides of the edge
+#pragma unroll
+        for (int kc = 0; kc < NG; ++kc) ecanon = fma(tab.gw[kc], me_L ? fzc[kc] : fzc[NG - 1 - kc], ecanon);
+        ecanon = ecanon * (T(0.5) * len);
+        const bool dry_L = me_L ? dry_me : dry_o, dry_R = me_L ? dry_o : dry_me;
+        // wet/dry closure: no water leaves a dry element (interior: either side; ocean: mine)
+        wall = (code >= 0) ? ((dry_L && ecanon > T(0)) || (dry_R && ecanon < T(0))) : (dry_me && ecanon > T(0));
+        if (!wall) {
+          emine = sgn * ecanon;
+#pragma unroll
+          for (int k = 0; k < NG; ++k) {
+            const T p = T(0.5) * (pdev(tm[k].d, tm[k].H, g) + pdev(to[k].d + dc_nm, to[k].H, g));
+            Fz[k] = sgn * fzc[k];
+            Fx[k] = sgn * fxc[k] + p * nx;
+            Fy[k] = sgn * fyc[k] + p * ny;
           }
         }
       }
-
-      // ---- 2. forcing: element rain = mean of the three nodal rates (Eq. rain)
-      T Re = 0;
-      if (S.rain_kind == 1) {
-        Re = a.rain_e[e];
-      } else if (S.rain_kind >= 2) {
-        const int4 nd = __ldg(a.nodes + e);
-        T acc = 0;
+      if (wall) {  // land edge or closed edge: reflective wall built from my own trace, no mass
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          const int n = (i == 0) ? nd.x : (i == 1 ? nd.y : nd.z);
-          const T px = a.node_xy[2 * (long long)n], py = a.node_xy[2 * (long long)n + 1];
-          if (S.rain_kind == 2) {
-            const T dx = px - s_storm[0], dy = py - s_storm[1];
-            const T r = sqrt_r(dx * dx + dy * dy);
-            const T rp = (T)S.storm[4], rm = (T)S.storm[5], re = (T)S.storm[6];
-            acc += (r < rm) ? rp * (T(0.5) + T(0.5) * r / rm) : rp * exp_r(-(r - rm) / re);
-          } else {
-            T gx = (T)((px - S.gx0) / S.gdx), gy = (T)((py - S.gy0) / S.gdy);
-            T gt = (T)((s_t - S.gt0) / S.gdt);
-            gx = fmin(fmax(gx, T(0)), T(S.gnx - 1));
-            gy = fmin(fmax(gy, T(0)), T(S.gny - 1));
-            gt = fmin(fmax(gt, T(0)), T(S.gnt - 1));
-            const int ix = min(max((int)floor(gx), 0), max(S.gnx - 2, 0));
-            const int iy = min(max((int)floor(gy), 0), max(S.gny - 2, 0));
-            const int it = min(max((int)floor(gt), 0), max(S.gnt - 2, 0));
-            const T fx = gx - T(ix), fy = gy - T(iy), ft = gt - T(it);
-            const int ix1 = S.gnx > 1 ? ix + 1 : ix, iy1 = S.gny > 1 ? iy + 1 : iy;
-            T val[2];
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-              const int kk = S.gnt > 1 ? it + q : 0;
-              const float* Gr = S.grid + (size_t)kk * S.gnx * S.gny;
-              const T v00 = Gr[(size_t)iy * S.gnx + ix], v10 = Gr[(size_t)iy * S.gnx + ix1];
-              const T v01 = Gr[(size_t)iy1 * S.gnx + ix], v11 = Gr[(size_t)iy1 * S.gnx + ix1];
-              val[q] = (T(1) - fy) * ((T(1) - fx) * v00 + fx * v10) + fy * ((T(1) - fx) * v01 + fx * v11);
-            }
-            acc += ((T(1) - ft) * val[0] + ft * val[1]) / T(3.6e6);
-          }
+        for (int k = 0; k < NG; ++k) {
+          const T qn = tm[k].qx * nx + tm[k].qy * ny;
+          Trace<T> gh = tm[k];
+          gh.qx = tm[k].qx - T(2) * qn * nx;
+          gh.qy = tm[k].qy - T(2) * qn * ny;
+          T fz, fx, fy;
+          edge_flux<FLUX, T>(tm[k], gh, T(0), nx, ny, g, H0, fz, fx, fy);
+          const T p = pdev(tm[k].d, tm[k].H, g);
+          Fz[k] = 0;
+          Fx[k] = fx + p * nx;
+          Fy[k] = fy + p * ny;
         }
-        Re = acc / T(3);
       }
-
-      // ---- 3. area integrals
-      // the linear modes have constant gradients: grad(hb) = hb1 grad(phi_1) + hb2 grad(phi_2)
-      const T g1x = tab.qdr[0][1] * rx + tab.qds[0][1] * sx, g1y = tab.qdr[0][1] * ry + tab.qds[0][1] * sy;
-      const T g2x = tab.qdr[0][2] * rx + tab.qds[0][2] * sx, g2y = tab.qdr[0][2] * ry + tab.qds[0][2] * sy;
-      const T hbx = E.hb1 * g1x + E.hb2 * g2x, hby = E.hb1 * g1y + E.hb2 * g2y;
-      const T cfm = (a.friction == 0) ? g * G.man * G.man : a.cf;
-      T vx[3] = {0, 0, 0}, vy[3] = {0, 0, 0};
-      if (S.press) {
-        const int4 nd = __ldg(a.nodes + e);
-        vx[0] = a.node_xy[2 * (long long)nd.x]; vy[0] = a.node_xy[2 * (long long)nd.x + 1];
-        vx[1] = a.node_xy[2 * (long long)nd.y]; vy[1] = a.node_xy[2 * (long long)nd.y + 1];
-        vx[2] = a.node_xy[2 * (long long)nd.z]; vy[2] = a.node_xy[2 * (long long)nd.z + 1];
-      }
+      massout = acc_addr(massout, emine);
+      if (code < -1) bdry_acc = acc_addr(bdry_acc, -emine);
+      // lift: R_m -= sum_k w_k (len/2) F_k phi_m(edge j, point k)
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) {
-        const Trace<T> t = trace_at<P, Pol>(E, tab.qphi[q]);
-        const T Hs = max_r(t.H, H0);
-        const T iH = rcp_r(Hs);
-        const T u = t.qx * iH, v = t.qy * iH;
-        const T pp = pdev(t.d, t.H, g);
-        T tau = 0;
-        if (a.friction == 0) tau = cfm * sqrt_r(u * u + v * v) / pow43_r(Hs);
-        else if (a.friction == 1) tau = cfm * sqrt_r(u * u + v * v) * iH;
-        T Fx = 0, Fy = 0;
-        if (S.press) {
-          const T px = tab.ql[q][0] * vx[0] + tab.ql[q][1] * vx[1] + tab.ql[q][2] * vx[2];
-          const T py = tab.ql[q][0] * vy[0] + tab.ql[q][1] * vy[1] + tab.ql[q][2] * vy[2];
-          const T dx = px - (T)S.ps[0], dy = py - (T)S.ps[1], s2 = (T)(S.ps[2] * S.ps[2]);
-          const T eta = (T)S.ps[3] * exp_r(-(dx * dx + dy * dy) / (T(2) * s2));
-          Fx = g * t.H * (-eta * dx / s2);
-          Fy = g * t.H * (-eta * dy / s2);
-        }
-        const T sx_ = g * t.d * hbx - tau * t.qx + Fx;
-        const T sy_ = g * t.d * hby - tau * t.qy + Fy;
-        const T fxx = t.qx * u + pp, fyx = t.qx * v;
-        const T fxy = t.qy * u, fyy = t.qy * v + pp;
-        const T wq = tab.qw[q] * detJ;
+      for (int k = 0; k < NG; ++k) {
+        const T wk = tab.gw[k] * (T(0.5) * len);
 #pragma unroll
         for (int m = 0; m < NP; ++m) {
-          const T dxm = tab.qdr[q][m] * rx + tab.qds[q][m] * sx;
-          const T dym = tab.qdr[q][m] * ry + tab.qds[q][m] * sy;
-          const T ph = tab.qphi[q][m];
-          if (m > 0) Rz[m] = fma(wq, dxm * t.qx + dym * t.qy, Rz[m]);
-          Rx[m] = fma(wq, dxm * fxx + dym * fyx + ph * sx_, Rx[m]);
-          Ry[m] = fma(wq, dxm * fxy + dym * fyy + ph * sy_, Ry[m]);
+          const T ph = wk * s_ephi[j][k][m];
+          if (m > 0) Rz[m] = fma(-ph, Fz[k], Rz[m]);
+          Rx[m] = fma(-ph, Fx[k], Rx[m]);
+          Ry[m] = fma(-ph, Fy[k], Ry[m]);
         }
-      }
-      if (dry_me) {  // the momentum equations are not advanced on dry elements
-#pragma unroll
-        for (int m = 0; m < NP; ++m) Rx[m] = Ry[m] = 0;
-      }
-
-      // ---- 4. Shu-Osher combination: out = a_n w^n + a_in w^in + beta dt M^{-1} R
-      const Acc an = acc_make<Acc>(a.a_n_hi, a.a_n_lo, a.a_n);
-      const Acc ain = acc_make<Acc>(a.a_in_hi, a.a_in_lo, a.a_in);
-      const Acc bdt = acc_make<Acc>(S.bdt_hi[a.stage], S.bdt_lo[a.stage], S.bdt[a.stage]);
-      // mean rates: d(zeta_bar)/dt = R_e - massout / A;  d(q_bar)/dt = phi_0 R_0 / detJ
-      const Acc zrate = acc_addr(acc_neg(acc_mul(massout, G.invA)), Re);
-      const T xrate = tab.phi0 * Rx[0] * idetJ, yrate = tab.phi0 * Ry[0] * idetJ;
-      Elem<P, Pol> O = E;
-      const bool has_n = (a.a_n != 0.0);
-      Elem<P, Pol> Wn = E;
-      if (has_n) {
-        Raw<RV> rn;
-        load_raw<RV>(a.wn, e, rn);
-        unpack<P>(rn, Wn);
-      }
-      {
-        Acc z = acc_mul(ain, E.zb), x = acc_mul(ain, E.xb), y = acc_mul(ain, E.yb);
-        if (has_n) {
-          z = acc_add(z, acc_mul(an, Wn.zb));
-          x = acc_add(x, acc_mul(an, Wn.xb));
-          y = acc_add(y, acc_mul(an, Wn.yb));
-        }
-        O.zb = acc_add(z, acc_mul(bdt, zrate));
-        O.xb = acc_addr(x, acc_r(bdt) * xrate);
-        O.yb = acc_addr(y, acc_r(bdt) * yrate);
-      }
-      const T an_r = (T)a.a_n, ain_r = (T)a.a_in, bdt_r = acc_r(bdt);
-#pragma unroll
-      for (int m = 0; m < NS; ++m) {
-        T z = ain_r * E.zs[m] + bdt_r * (Rz[m + 1] * idetJ);
-        T x = ain_r * E.xs[m] + bdt_r * (Rx[m + 1] * idetJ);
-        T y = ain_r * E.ys[m] + bdt_r * (Ry[m + 1] * idetJ);
-        if (has_n) {
-          z = fma(an_r, Wn.zs[m], z);
-          x = fma(an_r, Wn.xs[m], x);
-          y = fma(an_r, Wn.ys[m], y);
-        }
-        O.zs[m] = z;
-        O.xs[m] = x;
-        O.ys[m] = y;
-      }
-
-      // ---- 5. positive-depth operator, store
-      apply_positivity<P, Pol>(O, G, e, a, &a.ctl->err);
-      Raw<RV> ro;
-      pack<P>(O, ro);
-      store_raw<RV>(a.out, e, ro);
-
-      // ---- 6. ledger contribution of the element
-      rain_vol = acc_mulr(G.A, Re);
-    }
-    if (!a.tune) {
-      warp_reduce2(rain_vol, bdry_vol);
-      const int lane = tid & 31, wid = tid >> 5;
-      if (lane == 0) {
-        s_red[0][wid] = rain_vol;
-        s_red[1][wid] = bdry_vol;
-      }
-      __syncthreads();
-      if (tid == 0) {
-        Acc r = s_red[0][0], b = s_red[1][0];
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
-          r = acc_add(r, s_red[0][w]);
-          b = acc_add(b, s_red[1][w]);
-        }
-        const double wdt = S.bw[a.stage] * S.dt;
-        a.ledger[2 * tile] += wdt * acc_d(r);
-        a.ledger[2 * tile + 1] += wdt * acc_d(b);
       }
     }
-    __syncthreads();
+
+    // ---- 2. forcing: element rain = mean of the three nodal rates (Eq. rain)
+    T Re = 0;
+    if (S.rain_kind == 1) {
+      Re = a.rain_e[e];
+    } else if (S.rain_kind >= 2) {
+      const int4 nd = __ldg(a.nodes + e);
+      T acc = 0;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const long long n = (i == 0) ? nd.x : (i == 1 ? nd.y : nd.z);
+        const T px = a.node_xy[2 * n], py = a.node_xy[2 * n + 1];
+        if (S.rain_kind == 2) {
+          const T tt = t - F.storm[7];
+          const T dx = px - (F.storm[0] + F.storm[2] * tt), dy = py - (F.storm[1] + F.storm[3] * tt);
+          const T r = fsqrt0(dx * dx + dy * dy);
+          const T rp = F.storm[4], rm = F.storm[5], re = F.storm[6];
+          acc += (r < rm) ? rp * (T(0.5) + T(0.5) * fdiv(r, rm)) : rp * fexp(-fdiv(r - rm, re));
+        } else {
+          T gx = (px - F.grid[0]) * F.grid[2], gy = (py - F.grid[1]) * F.grid[3];
+          T gt = (t - F.grid[4]) * F.grid[5];
+          gx = fmin(fmax(gx, T(0)), T(S.gnx - 1));
+          gy = fmin(fmax(gy, T(0)), T(S.gny - 1));
+          gt = fmin(fmax(gt, T(0)), T(S.gnt - 1));
+          const int ix = min(max((int)floor(gx), 0), max(S.gnx - 2, 0));
+          const int iy = min(max((int)floor(gy), 0), max(S.gny - 2, 0));
+          const int it = min(max((int)floor(gt), 0), max(S.gnt - 2, 0));
+          const T fx = gx - T(ix), fy = gy - T(iy), ft = gt - T(it);
+          const int ix1 = S.gnx > 1 ? ix + 1 : ix, iy1 = S.gny > 1 ? iy + 1 : iy;
+          T val[2];
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const int kk = S.gnt > 1 ? it + q : 0;
+            const float* Gr = S.grid + (size_t)kk * S.gnx * S.gny;
+            const T v00 = Gr[(size_t)iy * S.gnx + ix], v10 = Gr[(size_t)iy * S.gnx + ix1];
+            const T v01 = Gr[(size_t)iy1 * S.gnx + ix], v11 = Gr[(size_t)iy1 * S.gnx + ix1];
+            val[q] = (T(1) - fy) * ((T(1) - fx) * v00 + fx * v10) + fy * ((T(1) - fx) * v01 + fx * v11);
+          }
+          acc += ((T(1) - ft) * val[0] + ft * val[1]) * T(1.0 / 3.6e6);
+        }
+      }
+      Re = acc * T(1.0 / 3.0);
+    }
+
+    // ---- 3. area integrals (grad v, F) + (s, v)
+    const T g1x = tab.qdr[0][1] * rx + tab.qds[0][1] * sx, g1y = tab.qdr[0][1] * ry + tab.qds[0][1] * sy;
+    const T g2x = tab.qdr[0][2] * rx + tab.qds[0][2] * sx, g2y = tab.qdr[0][2] * ry + tab.qds[0][2] * sy;
+    const T hbx = E.hb1 * g1x + E.hb2 * g2x, hby = E.hb1 * g1y + E.hb2 * g2y;  // constant grad(hb)
+    const T cfm = (a.friction == 0) ? g * G.man * G.man : a.cf;
+    T vx[3] = {0, 0, 0}, vy[3] = {0, 0, 0};
+    if (S.press) {
+      const int4 nd = __ldg(a.nodes + e);
+      vx[0] = a.node_xy[2 * (long long)nd.x]; vy[0] = a.node_xy[2 * (long long)nd.x + 1];
+      vx[1] = a.node_xy[2 * (long long)nd.y]; vy[1] = a.node_xy[2 * (long long)nd.y + 1];
+      vx[2] = a.node_xy[2 * (long long)nd.z]; vy[2] = a.node_xy[2 * (long long)nd.z + 1];
+    }
+#pragma unroll 1
+    for (int q = 0; q < NQ; ++q) {
+      const Trace<T> tq = trace_at<P, Pol>(E, tab.qphi[q]);
+      const T Hs = max_r(tq.H, H0);
+      const T iH = frcp(Hs);
+      const T u = tq.qx * iH, v = tq.qy * iH;
+      const T pp = pdev(tq.d, tq.H, g);
+      T tau = 0;
+      if (a.friction == 0) tau = cfm * fsqrt0(u * u + v * v) * fpowm43(Hs);
+      else if (a.friction == 1) tau = cfm * fsqrt0(u * u + v * v) * iH;
+      T Fxs = 0, Fys = 0;
+      if (S.press) {
+        const T px = tab.ql[q][0] * vx[0] + tab.ql[q][1] * vx[1] + tab.ql[q][2] * vx[2];
+        const T py = tab.ql[q][0] * vy[0] + tab.ql[q][1] * vy[1] + tab.ql[q][2] * vy[2];
+        const T dx = px - F.ps[0], dy = py - F.ps[1], is2 = frcp(F.ps[2] * F.ps[2]);
+        const T eta = F.ps[3] * fexp(-(dx * dx + dy * dy) * T(0.5) * is2);
+        Fxs = g * tq.H * (-eta * dx * is2);
+        Fys = g * tq.H * (-eta * dy * is2);
+      }
+      const T sx_ = g * tq.d * hbx - tau * tq.qx + Fxs;
+      const T sy_ = g * tq.d * hby - tau * tq.qy + Fys;
+      const T fxx = tq.qx * u + pp, fyx = tq.qx * v;
+      const T fxy = tq.qy * u, fyy = tq.qy * v + pp;
+      const T wq = tab.qw[q] * detJ;
+#pragma unroll
+      for (int m = 0; m < NP; ++m) {
+        const T dxm = tab.qdr[q][m] * rx + tab.qds[q][m] * sx;
+        const T dym = tab.qdr[q][m] * ry + tab.qds[q][m] * sy;
+        const T ph = tab.qphi[q][m];
+        if (m > 0) Rz[m] = fma(wq, dxm * tq.qx + dym * tq.qy, Rz[m]);
+        Rx[m] = fma(wq, dxm * fxx + dym * fyx + ph * sx_, Rx[m]);
+        Ry[m] = fma(wq, dxm * fxy + dym * fyy + ph * sy_, Ry[m]);
+      }
+    }
+    if (dry_me) {  // the momentum equations are not advanced on dry elements
+#pragma unroll
+      for (int m = 0; m < NP; ++m) Rx[m] = Ry[m] = 0;
+    }
+
+    // ---- 4. Shu-Osher combination: out = a_n w^n + a_in w^in + beta dt M^{-1} R
+    const Acc an = acc_make<Acc>(a.a_n_hi, a.a_n_lo, a.a_n);
+    const Acc ain = acc_make<Acc>(a.a_in_hi, a.a_in_lo, a.a_in);
+    const Acc bdt = acc_make<Acc>(S.bdt_hi[a.stage], S.bdt_lo[a.stage], S.bdt[a.stage]);
+    // mean rates: d(zeta_bar)/dt = R_e - massout / A;  d(q_bar)/dt = phi_0 R_0 / detJ
+    const Acc zrate = acc_addr(acc_neg(acc_mul(massout, G.invA)), Re);
+    const T xrate = tab.phi0 * Rx[0] * idetJ, yrate = tab.phi0 * Ry[0] * idetJ;
+    Elem<P, Pol> O = E;
+    Elem<P, Pol> Wn = E;
+    if (a.has_n) {
+      Raw<RV> rn;
+      load_raw<RV>(a.wn, e, rn);
+      unpack<P>(rn, Wn);
+    }
+    {
+      Acc z = acc_mul(ain, E.zb), x = acc_mul(ain, E.xb), y = acc_mul(ain, E.yb);
+      if (a.has_n) {
+        z = acc_add(z, acc_mul(an, Wn.zb));
+        x = acc_add(x, acc_mul(an, Wn.xb));
+        y = acc_add(y, acc_mul(an, Wn.yb));
+      }
+      O.zb = acc_add(z, acc_mul(bdt, zrate));
+      O.xb = acc_addr(x, acc_r(bdt) * xrate);
+      O.yb = acc_addr(y, acc_r(bdt) * yrate);
+    }
+    const T an_r = (sizeof(T) == 4) ? (T)a.a_n_hi : (T)a.a_n, ain_r = (sizeof(T) == 4) ? (T)a.a_in_hi : (T)a.a_in;
+    const T bdt_r = acc_r(bdt);
+#pragma unroll
+    for (int m = 0; m < NS; ++m) {
+      T z = ain_r * E.zs[m] + bdt_r * (Rz[m + 1] * idetJ);
+      T x = ain_r * E.xs[m] + bdt_r * (Rx[m + 1] * idetJ);
+      T y = ain_r * E.ys[m] + bdt_r * (Ry[m + 1] * idetJ);
+      if (a.has_n) {
+        z = fma(an_r, Wn.zs[m], z);
+        x = fma(an_r, Wn.xs[m], x);
+        y = fma(an_r, Wn.ys[m], y);
+      }
+      O.zs[m] = z;
+      O.xs[m] = x;
+      O.ys[m] = y;
+    }
+
+    // ---- 5. positive-depth operator, store
+    apply_positivity<P, Pol>(O, G, e, a, &a.ctl->err);
+    Raw<RV> ro;
+    pack<P>(O, ro);
+    store_raw<RV>(a.out, e, ro);
+
+    // ---- 6. ledger: rain volume rate of the element
+    rain_acc = acc_add(rain_acc, acc_mulr(G.A, Re));
   }
-  // launch epilogue: the last CTA to finish resets the work counter and, after the final stage
-  // of a step, advances the step counter read by the next step's CTAs
-  if (tid == 0) {
-    __threadfence();
-    const unsigned t = atomicAdd(&a.ctl->ticket, 1u);
-    if (t == gridDim.x - 1) {
-      a.ctl->ticket = 0;
-      a.ctl->tile_counter = 0;
-      if (a.last && !a.tune) a.ctl->step += 1ull;
+  if (cur >= 0 && !a.tune) flush_ledger<P, Pol>(a, cur, gw, rain_acc, bdry_acc);
+
+  // launch epilogue: the last CTA to finish advances the step counter after the final stage
+  if (a.last && !a.tune) {
+    __syncthreads();
+    if (tid == 0) {
       __threadfence();
+      const unsigned tk = atomicAdd(&a.ctl->ticket, 1u);
+      if (tk == gridDim.x - 1) {
+        a.ctl->ticket = 0;
+        a.ctl->step += 1ull;
+        __threadfence();
+      }
     }
   }
 }

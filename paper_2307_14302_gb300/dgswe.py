@@ -248,8 +248,8 @@ class Solver:
         _check(lib().dgswe_volume(self.h, C.byref(v)))
         return v.value
 
-    def set_launch(self, block, persistent):
-        _check(lib().dgswe_set_launch(self.h, block, persistent))
+    def set_launch(self, block, waves=1):
+        _check(lib().dgswe_set_launch(self.h, block, waves))
 
     def launch(self):
         b, p = C.c_int32(), C.c_int32()
@@ -305,19 +305,19 @@ class Ensemble:
         _check(lib().dgswe_ensemble_get_ledger(self.h, i, C.byref(led)))
         return led.as_dict()
 
-    def set_launch(self, block, persistent):
-        _check(lib().dgswe_set_launch(self.h, block, persistent))
+    def set_launch(self, block, waves=1):
+        _check(lib().dgswe_set_launch(self.h, block, waves))
 
     def launch_count(self) -> int:
         return int(lib().dgswe_launch_count(self.h))
 
 
 def from_workload(w, precision=MIXED, flux=FLUX_ROE, ssp_stages=None, dt=0.0, friction=MANNING, cf=0.0, device=0,
-                  stream=None, block=0, persistent=0) -> Solver:
+                  stream=None, block=0, waves=1) -> Solver:
     """A Solver set up with a workload's mesh, fields, forcing and nodal initial state."""
     s = Solver(p=w.p, flux=flux, ssp_stages=ssp_stages, precision=precision, H0=w.h0, cfl=w.cfl, dt=dt,
                friction=friction, cf=cf, device=device, stream=stream)
-    s.set_launch(block, persistent)
+    s.set_launch(block, waves)
     s.set_mesh(w.mesh)
     s.set_fields(w.hb, w.manning if friction == MANNING else None)
     if w.rain_nodal is not None:

@@ -29,13 +29,13 @@ def _built():
     D.lib()
 
 
-def _pair(w, steps, precision, flux=O.ROE, ssp=None, friction=O.MANNING, cf=0.0, block=0, persistent=0, dt=None):
+def _pair(w, steps, precision, flux=O.ROE, ssp=None, friction=O.MANNING, cf=0.0, block=0, waves=1, dt=None):
     ref = O.from_workload(w, flux=flux, ssp=ssp, friction=friction, cf=cf, dt=dt)
     dt = ref.cfl_dt(w.cfl) if dt is None else dt
     ref.set_dt(dt)
     ref.step(steps)
     dev = D.from_workload(w, precision=precision, flux=flux, ssp_stages=ssp, dt=dt, friction=friction, cf=cf,
-                          block=block, persistent=persistent)
+                          block=block, waves=waves)
     dev.step(steps)
     dev.sync()
     return ref, dev
@@ -207,11 +207,11 @@ def test_quadratic_friction_bathtub_short():
 def test_launch_shapes_give_identical_bits(prec):
     w = W.coastal_c2(n_tri=5000, seed=5, steps=30)
     outs = []
-    for block, pers in ((64, 0), (128, 1), (256, 0), (256, 1)):
-        dev = D.from_workload(w, precision=prec, block=block, persistent=pers)
+    for block, waves in ((64, 1), (128, 2), (256, 1), (256, 2)):
+        dev = D.from_workload(w, precision=prec, block=block, waves=waves)
         dev.step(30)
         dev.sync()
-        assert dev.launch() == (block, pers)
+        assert dev.launch() == (block, waves)
         outs.append(dev.state())
     for o in outs[1:]:
         assert np.array_equal(o, outs[0])
