@@ -261,7 +261,7 @@ def our_arm(args, ws, rank, local):
     launches = s.launch_count() - launches0
     s.sync()
     led = s.ledger()
-    block, waves = s.launch()
+    block, waves, split = s.launch()
     units, t_max = whole_job(w.dof * args.steps, t_mixed, ws, dev)
     value = units / t_max
     clocks = clk.summary()
@@ -320,7 +320,7 @@ def our_arm(args, ws, rank, local):
             "config": {"workload": w.name, "elements": E, "nodes": w.mesh.n_nodes, "p": 1, "dof": w.dof,
                        "ssp": "SSP(2,2)", "flux": "Roe", "precision": "FP32 bulk, float-float means, FP64 depth test",
                        "l2": "flushed (256 MiB write) between timed steps", "parallelism": f"replicas x{ws}",
-                       "launch": {"block": block, "waves": waves}, "dt_s": s_dt(led),
+                       "launch": {"block": block, "waves": waves, "split": split}, "dt_s": s_dt(led),
                        "mass_balance_rel_err": led["rel_err"]},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,

@@ -215,11 +215,14 @@ int dgswe_ensemble_step(dgswe_h ens, int64_t n_steps);
 int dgswe_ensemble_get_state(dgswe_h ens, int32_t member, double* zeta, double* qx, double* qy);
 int dgswe_ensemble_get_ledger(dgswe_h ens, int32_t member, dgswe_ledger* out);
 
-/* Launch shape of the stage kernel: block size (64, 128, 256, or 0 = autotune on the next step)
- * and waves (1 or 2): the grid holds waves x (CTAs resident per SM) x (SMs) CTAs, and its warps
- * take the 32-element tiles of all scenarios round-robin.  Results do not depend on the shape. */
-int dgswe_set_launch(dgswe_h, int32_t block, int32_t waves);
-int dgswe_get_launch(dgswe_h, int32_t* block, int32_t* waves);
+/* Launch shape of a stage: block size of the element kernel (64, 128, 256, or 0 = autotune on
+ * the next step), waves (1 or 2: the grid holds waves x CTAs resident per SM x SMs CTAs whose
+ * warps take the 32-element tiles round-robin), and split (1: a separate edge kernel computes
+ * every interior edge flux once and the element kernel gathers it; 0: one fused kernel in which
+ * both neighbours evaluate the edge).  Fused and split results agree to rounding; for a fixed
+ * split value results do not depend on block or waves. */
+int dgswe_set_launch(dgswe_h, int32_t block, int32_t waves, int32_t split);
+int dgswe_get_launch(dgswe_h, int32_t* block, int32_t* waves, int32_t* split);
 
 /* Number of kernel launches this context enqueued so far (all kinds). */
 int64_t dgswe_launch_count(dgswe_h);

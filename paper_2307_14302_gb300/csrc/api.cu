@@ -110,7 +110,8 @@ struct dgswe_ctx {
   long long E = 0, N = 0;          // padded element count, node count
   std::vector<long long> eoff, noff;
   DevBuf rec[3], nbr, geo, nodes, node_xy, xy64, hbn, rain_e, scen, tile_scen, ledger, ctl, eorig, grids, scratch,
-      gather_buf;
+      gather_buf, edges, slots;
+  long long nedges = 0;
   int ntiles = 0;                          // 32-element tiles
   int wslots = 0;                          // ledger slots per scenario
   int wcur = 0;                            // warps of the current launch shape
@@ -118,7 +119,7 @@ struct dgswe_ctx {
   std::vector<double> V0, VH0;
   std::vector<Stage> stages;
   // launch configuration
-  int block = 128, waves = 1;
+  int block = 128, waves = 1, split = 1;
   bool autotune = true;
   int grid = 0;
   cudaGraphExec_t g1 = nullptr, gK = nullptr;
@@ -128,7 +129,7 @@ struct dgswe_ctx {
   ~dgswe_ctx() {
     DeviceGuard dg_(device);
     DevBuf* bufs[] = {&rec[0], &rec[1], &rec[2], &nbr, &geo, &nodes, &node_xy, &xy64, &hbn, &rain_e, &scen,
-                      &tile_scen, &ledger, &ctl, &eorig, &grids, &scratch, &gather_buf};
+                      &tile_scen, &ledger, &ctl, &eorig, &grids, &scratch, &gather_buf, &edges, &slots};
     for (DevBuf* b : bufs) b->alloc(0);
     if (g1) cudaGraphExecDestroy(g1);
     if (gK) cudaGraphExecDestroy(gK);
@@ -332,6 +333,38 @@ static int build_layout(dgswe_h h) {
       (void)Gm;
     }
   }
+  // interior edges for the edge-split path, canonical orientation (L = lower element index)
+  const int ev = mx ? 1 : 2;
+  std::vector<uint32_t> edg;
+  for (size_t s = 0; s < ns; ++s) {
+    const HostMesh& M = h->sc[s].m;
+    const long long eo = h->eoff[s];
+    for (int e = 0; e < M.ne; ++e)
+      for (int j = 0; j < 3; ++j) {
+        const int32_t c = M.code[3 * (size_t)e + j];
+        if (c < 0 || (c >> 2) < e) continue;
+        const uint32_t wl = (uint32_t)(((e + eo) << 2) | j), wr = (uint32_t)((((c >> 2) + eo) << 2) | (c & 3));
+        const double lx = M.lnx[3 * (size_t)e + j], ly = M.lny[3 * (size_t)e + j];
+        const size_t at = edg.size();
+        edg.resize(at + 4 * ev, 0u);
+        edg[at] = wl;
+        edg[at + 1] = wr;
+        if (mx) {
+          const float fx = (float)lx, fy = (float)ly;
+          std::memcpy(&edg[at + 2], &fx, 4);
+          std::memcpy(&edg[at + 3], &fy, 4);
+        } else {
+          std::memcpy(&edg[at + 4], &lx, 8);
+          std::memcpy(&edg[at + 6], &ly, 8);
+        }
+      }
+  }
+  h->nedges = (long long)(edg.size() / (4 * ev));
+  const int sv = mx ? slot_vec_mixed(p) : slot_vec_fp64(p);
+  if (h->edges.alloc(std::max<size_t>(16, 4 * edg.size())) || h->slots.alloc(16 * (size_t)sv * 3 * E))
+    return fail(DGSWE_ENOMEM, "device allocation of the edge-split buffers failed");
+  if (!edg.empty()) CU(cudaMemcpy(h->edges.p, edg.data(), 4 * edg.size(), cudaMemcpyHostToDevice));
+  CU(cudaMemset(h->slots.p, 0, 16 * (size_t)sv * 3 * E));
   // upload
   const size_t rbytes = 16 * (size_t)h->rv * E;
   for (int b = 0; b < 3; ++b)
@@ -475,6 +508,10 @@ static StageArgs<Pol> make_args(dgswe_h h, int stage, int tune) {
   a.tile_scen = h->tile_scen.as<int32_t>();
   a.ledger = h->ledger.as<double>();
   a.ctl = h->ctl.as<Ctl>();
+  a.edges = h->edges.as<uint4>();
+  a.slots = h->slots.as<uint4>();
+  a.nedges = h->nedges;
+  a.split = h->split;
   a.ntiles = h->ntiles;
   a.wslots = h->wslots;
   a.stage = stage;
@@ -494,9 +531,23 @@ static StageArgs<Pol> make_args(dgswe_h h, int stage, int tune) {
   return a;
 }
 
+static int edge_grid(dgswe_h h) {
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+  const long long need = (h->nedges + 255) / 256;
+  return (int)std::max<long long>(1, std::min<long long>(need, 16LL * sms));
+}
+
+// one Runge-Kutta stage: (edge kernel, when split) then the element kernel
 static int launch_stage_once(dgswe_h h, int stage, int tune, cudaStream_t s) {
   const int grid = h->grid;
-  cudaError_t e;
+  cudaError_t e = cudaSuccess;
+  if (h->split && h->nedges > 0) {
+    if (mixed(h)) e = launch_edges<Mixed>(h->prm.p, h->prm.flux, make_args<Mixed>(h, stage, tune), edge_grid(h), 256, s);
+    else e = launch_edges<Fp64>(h->prm.p, h->prm.flux, make_args<Fp64>(h, stage, tune), edge_grid(h), 256, s);
+    if (e != cudaSuccess) return fail(DGSWE_ECUDA, "edge launch: %s", cudaGetErrorString(e));
+    h->launches++;
+  }
   if (mixed(h)) e = launch_stage<Mixed>(h->prm.p, h->prm.flux, make_args<Mixed>(h, stage, tune), grid, h->block, s);
   else e = launch_stage<Fp64>(h->prm.p, h->prm.flux, make_args<Fp64>(h, stage, tune), grid, h->block, s);
   if (e != cudaSuccess) return fail(DGSWE_ECUDA, "stage launch: %s", cudaGetErrorString(e));
@@ -504,18 +555,21 @@ static int launch_stage_once(dgswe_h h, int stage, int tune, cudaStream_t s) {
   return 0;
 }
 
+static int launches_per_stage(dgswe_h h) { return (h->split && h->nedges > 0) ? 2 : 1; }
+
 static int occupancy(dgswe_h h, int block) {
-  return mixed(h) ? stage_blocks_per_sm<Mixed>(h->prm.p, h->prm.flux, block)
-                  : stage_blocks_per_sm<Fp64>(h->prm.p, h->prm.flux, block);
+  return mixed(h) ? stage_blocks_per_sm<Mixed>(h->prm.p, h->prm.flux, block, h->split)
+                  : stage_blocks_per_sm<Fp64>(h->prm.p, h->prm.flux, block, h->split);
 }
 
 // grid = SMs x resident CTAs per SM x waves; its warps take the 32-element tiles round-robin
-static int apply_launch(dgswe_h h, int block, int waves) {
+static int apply_launch(dgswe_h h, int block, int waves, int split) {
   int sms = 0;
   CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
   if (int rc = fold_ledger(h)) return rc;
   h->block = block;
   h->waves = waves;
+  h->split = split;
   const int want = sms * std::max(1, occupancy(h, block)) * waves;
   const int need = (h->ntiles + block / 32 - 1) / (block / 32);  // one tile per warp
   h->grid = std::max(1, std::min(want, need));
@@ -532,10 +586,13 @@ static int autotune(dgswe_h h) {
   float best = 1e30f;
   int bb = 128, bp = 0;
   const int blocks[3] = {64, 128, 256};
+  int bs = 1;
+  for (int sp = 0; sp <= 1; ++sp)
   for (int pi = 1; pi <= 2; ++pi)
     for (int bi = 0; bi < 3; ++bi) {
+      h->split = sp;
       if (occupancy(h, blocks[bi]) < 1) continue;
-      if (int rc = apply_launch(h, blocks[bi], pi)) return rc;
+      if (int rc = apply_launch(h, blocks[bi], pi, sp)) return rc;
       for (int w = 0; w < 2; ++w)
         if (int rc = launch_stage_once(h, 0, 1, h->stream)) return rc;
       CU(cudaEventRecord(e0, h->stream));
@@ -545,12 +602,12 @@ static int autotune(dgswe_h h) {
       CU(cudaEventSynchronize(e1));
       float ms = 0.f;
       CU(cudaEventElapsedTime(&ms, e0, e1));
-      if (ms < best) { best = ms; bb = blocks[bi]; bp = pi; }
+      if (ms < best) { best = ms; bb = blocks[bi]; bp = pi; bs = sp; }
     }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   h->autotune = false;
-  return apply_launch(h, bb, bp);
+  return apply_launch(h, bb, bp, bs);
 }
 
 static int build_graphs(dgswe_h h) {
@@ -564,7 +621,7 @@ static int build_graphs(dgswe_h h) {
     cudaError_t ce = cudaStreamEndCapture(h->cap, &g);
     if (rc) return rc;
     if (ce != cudaSuccess) return fail(DGSWE_ECUDA, "graph capture: %s", cudaGetErrorString(ce));
-    h->launches -= nsteps * (long long)h->stages.size();  // counted when the graph runs
+    h->launches -= nsteps * (long long)h->stages.size() * launches_per_stage(h);  // counted when the graph runs
     cudaGraphExec_t ex;
     ce = cudaGraphInstantiate(&ex, g, 0);
     cudaGraphDestroy(g);
@@ -635,7 +692,7 @@ static int prepare(dgswe_h h) {
     if (int rc = reduce_volume(h, s, h->V0[s], h->VH0[s])) return rc;
   }
   if (int rc = upload_dt(h)) return rc;
-  if (int rc = apply_launch(h, h->block, h->waves)) return rc;
+  if (int rc = apply_launch(h, h->block, h->waves, h->split)) return rc;
   CU(cudaStreamSynchronize(h->stream));
   h->ready = true;
   return 0;
@@ -864,7 +921,7 @@ int dgswe_step(dgswe_h h, int64_t n) {
     if (int rc = autotune(h)) return rc;
   if (!h->g1)
     if (int rc = build_graphs(h)) return rc;
-  const long long per = (long long)h->stages.size();
+  const long long per = (long long)h->stages.size() * launches_per_stage(h);
   for (int64_t i = 0; i < n / h->K; ++i) CU(cudaGraphLaunch(h->gK, h->stream));
   for (int64_t i = 0; i < n % h->K; ++i) CU(cudaGraphLaunch(h->g1, h->stream));
   h->launches += n * per;
@@ -1092,7 +1149,7 @@ int dgswe_ensemble_get_ledger(dgswe_h ens, int32_t i, dgswe_ledger* out) {
   return ledger_of(ens, (size_t)i, out);
 }
 
-int dgswe_set_launch(dgswe_h h, int32_t block, int32_t waves) {
+int dgswe_set_launch(dgswe_h h, int32_t block, int32_t waves, int32_t split) {
   if (int rc = check_handle(h)) return rc;
   if (block != 0 && block != 64 && block != 128 && block != 256) return fail(DGSWE_EINVAL, "block must be 0, 64, 128 or 256");
   if (block == 0) {
@@ -1100,21 +1157,24 @@ int dgswe_set_launch(dgswe_h h, int32_t block, int32_t waves) {
     return 0;
   }
   if (waves < 1 || waves > 2) return fail(DGSWE_EINVAL, "waves must be 1 or 2");
+  if (split != 0 && split != 1) return fail(DGSWE_EINVAL, "split must be 0 or 1");
   h->autotune = false;
   if (!h->ready) {
     h->block = block;
     h->waves = waves;
+    h->split = split;
     return 0;
   }
   DeviceGuard dg_(h->device);
   CU(cudaStreamSynchronize(h->stream));
-  return apply_launch(h, block, waves);
+  return apply_launch(h, block, waves, split);
 }
 
-int dgswe_get_launch(dgswe_h h, int32_t* block, int32_t* waves) {
+int dgswe_get_launch(dgswe_h h, int32_t* block, int32_t* waves, int32_t* split) {
   if (int rc = check_handle(h)) return rc;
   if (block) *block = h->block;
   if (waves) *waves = h->waves;
+  if (split) *split = h->split;
   return 0;
 }
 

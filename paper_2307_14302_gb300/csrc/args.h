@@ -38,6 +38,10 @@ struct StageArgs {
   const int32_t* tile_scen;  // scenario of each 32-element tile
   double* ledger;          // [scenario][wslots][2]: rain volume, boundary inflow volume per warp
   Ctl* ctl;
+  const uint4* edges;      // edge-split path: interior edge records
+  uint4* slots;            // edge-split path: per (element, local edge) lift slots
+  long long nedges;
+  int split;               // 1: interior edges come from the slots written by the edge kernel
   int ntiles;              // 32-element tiles, processed round-robin by the launch's warps
   int wslots;              // ledger slots per scenario (>= warps of the launch)
   int stage;               // Shu-Osher stage index
@@ -63,7 +67,10 @@ cudaError_t upload_tables(int p, const RefTab<float>& tf, const RefTab<double>& 
 template <class Pol>
 cudaError_t launch_stage(int p, int flux, const StageArgs<Pol>& a, int grid, int block, cudaStream_t s);
 template <class Pol>
-int stage_blocks_per_sm(int p, int flux, int block);
+int stage_blocks_per_sm(int p, int flux, int block, int split);
+// edge kernel of the split path: one thread per interior edge, writes both sides' slots
+template <class Pol>
+cudaError_t launch_edges(int p, int flux, const StageArgs<Pol>& a, int grid, int block, cudaStream_t s);
 // positive-depth operator on records [begin, end) in place (a.in == a.out)
 template <class Pol>
 cudaError_t launch_prepare(int p, const StageArgs<Pol>& a, long long begin, long long end, cudaStream_t s);

@@ -38,6 +38,14 @@ DG_HD constexpr int np_of(int p) { return (p + 1) * (p + 2) / 2; }
 DG_HD constexpr int rec_vec_mixed(int p) { return (3 * np_of(p) + 7 + 3) / 4 <= 4 ? 4 : 8; }
 DG_HD constexpr int rec_vec_fp64(int p) { return ((3 * np_of(p) + 4) + 1) / 2 <= 8 ? 8 : 12; }
 
+// edge-split path: per interior edge one record {eL<<2|jL, eR<<2|jR, scaled normal of L's edge};
+// per (element, local edge) one slot with the edge's lift on that side: zeta modes 1.., qx and
+// qy modes 0.., the mass flux integral (outward), and a closed-edge flag.  Sizes in 16-byte units.
+DG_HD constexpr int edge_vec(bool fp64) { return fp64 ? 2 : 1; }
+DG_HD constexpr int slot_vals(int p) { return (np_of(p) - 1) + 2 * np_of(p); }
+DG_HD constexpr int slot_vec_mixed(int p) { return (slot_vals(p) + 2 + 3) / 4; }
+DG_HD constexpr int slot_vec_fp64(int p) { return (slot_vals(p) + 2 + 1) / 2; }
+
 // reference-element tables (basis, quadrature), held in constant memory per degree
 template <typename T>
 struct RefTab {

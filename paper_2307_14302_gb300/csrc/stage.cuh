@@ -610,6 +610,194 @@ __device__ __forceinline__ void warp_reduce2(ff& a, ff& b) {
   }
 }
 
+// ------------------------------------------------------------------ edge-split path ----
+template <class Pol>
+struct SlotT;
+template <>
+struct SlotT<Mixed> {
+  template <int P>
+  static constexpr int SV = slot_vec_mixed(P);
+};
+template <>
+struct SlotT<Fp64> {
+  template <int P>
+  static constexpr int SV = slot_vec_fp64(P);
+};
+
+// lift values of one side: zeta modes 1..NS, qx modes 0..NS, qy modes 0..NS, then mass, flag
+template <int P, class T>
+struct Lift {
+  static constexpr int NP = np_of(P), NV = slot_vals(P);
+  T v[NV];
+  T mass;
+  uint32_t flag;
+};
+
+template <int P>
+__device__ __forceinline__ void store_slot(uint4* __restrict__ slots, long long idx, const Lift<P, float>& L) {
+  constexpr int SV = slot_vec_mixed(P), NV = slot_vals(P);
+  float f[4 * SV];
+#pragma unroll
+  for (int i = 0; i < 4 * SV; ++i) f[i] = 0.f;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) f[i] = L.v[i];
+  f[NV] = L.mass;
+  f[NV + 1] = __uint_as_float(L.flag);
+  uint4* p = slots + idx * SV;
+#pragma unroll
+  for (int i = 0; i < SV; ++i)
+    p[i] = make_uint4(__float_as_uint(f[4 * i]), __float_as_uint(f[4 * i + 1]), __float_as_uint(f[4 * i + 2]),
+                      __float_as_uint(f[4 * i + 3]));
+}
+template <int P>
+__device__ __forceinline__ void load_slot(const uint4* __restrict__ slots, long long idx, Lift<P, float>& L) {
+  constexpr int SV = slot_vec_mixed(P), NV = slot_vals(P);
+  float f[4 * SV];
+  const uint4* p = slots + idx * SV;
+#pragma unroll
+  for (int i = 0; i < SV; ++i) {
+    const uint4 u = __ldg(p + i);
+    f[4 * i] = __uint_as_float(u.x);
+    f[4 * i + 1] = __uint_as_float(u.y);
+    f[4 * i + 2] = __uint_as_float(u.z);
+    f[4 * i + 3] = __uint_as_float(u.w);
+  }
+#pragma unroll
+  for (int i = 0; i < NV; ++i) L.v[i] = f[i];
+  L.mass = f[NV];
+  L.flag = __float_as_uint(f[NV + 1]);
+}
+template <int P>
+__device__ __forceinline__ void store_slot(uint4* __restrict__ slots, long long idx, const Lift<P, double>& L) {
+  constexpr int SV = slot_vec_fp64(P), NV = slot_vals(P);
+  double f[2 * SV];
+#pragma unroll
+  for (int i = 0; i < 2 * SV; ++i) f[i] = 0.0;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) f[i] = L.v[i];
+  f[NV] = L.mass;
+  f[NV + 1] = __hiloint2double(0, (int)L.flag);
+  uint4* p = slots + idx * SV;
+#pragma unroll
+  for (int i = 0; i < SV; ++i) {
+    uint4 u;
+    d2u(f[2 * i], u.x, u.y);
+    d2u(f[2 * i + 1], u.z, u.w);
+    p[i] = u;
+  }
+}
+template <int P>
+__device__ __forceinline__ void load_slot(const uint4* __restrict__ slots, long long idx, Lift<P, double>& L) {
+  constexpr int SV = slot_vec_fp64(P), NV = slot_vals(P);
+  double f[2 * SV];
+  const uint4* p = slots + idx * SV;
+#pragma unroll
+  for (int i = 0; i < SV; ++i) {
+    const uint4 u = __ldg(p + i);
+    f[2 * i] = u2d(u.x, u.y);
+    f[2 * i + 1] = u2d(u.z, u.w);
+  }
+#pragma unroll
+  for (int i = 0; i < NV; ++i) L.v[i] = f[i];
+  L.mass = f[NV];
+  L.flag = (uint32_t)__double2loint(f[NV + 1]);
+}
+
+__device__ __forceinline__ void load_edge(const uint4* e, long long i, int& eL, int& jL, int& eR, int& jR, float& lnx,
+                                          float& lny) {
+  const uint4 u = __ldg(e + i);
+  eL = (int)u.x >> 2; jL = (int)u.x & 3; eR = (int)u.y >> 2; jR = (int)u.y & 3;
+  lnx = __uint_as_float(u.z);
+  lny = __uint_as_float(u.w);
+}
+__device__ __forceinline__ void load_edge(const uint4* e, long long i, int& eL, int& jL, int& eR, int& jR,
+                                          double& lnx, double& lny) {
+  const uint4 u = __ldg(e + 2 * i), v = __ldg(e + 2 * i + 1);
+  eL = (int)u.x >> 2; jL = (int)u.x & 3; eR = (int)u.y >> 2; jR = (int)u.y & 3;
+  lnx = u2d(v.x, v.y);
+  lny = u2d(v.z, v.w);
+}
+
+// Edge kernel: one thread per interior edge, in the canonical orientation (L = lower element
+// index, normal outward from L).  Computes the numerical flux once, the wet/dry closure, the
+// pressure relative to each side's own mean elevation, and writes both sides' lift into their
+// slots (mass flux +E to L, -E to R: bitwise opposite).  A closed edge only raises the flag;
+// each side then builds its own wall flux in the element kernel.
+template <int P, int FLUX, class Pol>
+__global__ void __launch_bounds__(256) edge_kernel(const StageArgs<Pol> a) {
+  using T = typename Pol::T;
+  constexpr int NP = np_of(P), NG = P + 1, RV = Pol::template RV<P>;
+  const RefTab<T>& tab = ctab<T, P>();
+  __shared__ T s_ephi[3][NG][NP];
+  for (int i = threadIdx.x; i < 3 * NG * NP; i += blockDim.x) {
+    const int j = i / (NG * NP), k = (i / NP) % NG, m = i % NP;
+    s_ephi[j][k][m] = tab.ephi[j][k][m];
+  }
+  __syncthreads();
+  const T g = a.g, H0 = a.H0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.nedges;
+       i += (long long)gridDim.x * blockDim.x) {
+    int eL, jL, eR, jR;
+    T lnx, lny;
+    load_edge(a.edges, i, eL, jL, eR, jR, lnx, lny);
+    Raw<RV> rl, rr;
+    load_raw<RV>(a.in, eL, rl);
+    load_raw<RV>(a.in, eR, rr);
+    Elem<P, Pol> L, R;
+    unpack<P>(rl, L);
+    unpack<P>(rr, R);
+    const T len = fsqrt_pos(lnx * lnx + lny * lny);
+    const T il = frcp(len);
+    const T nx = lnx * il, ny = lny * il;
+    const T dcRL = acc_diff(R.zb, L.zb);
+    Trace<T> tl[NG], tr[NG];
+    T fz[NG], fx[NG], fy[NG];
+    T ecanon = 0;
+#pragma unroll
+    for (int k = 0; k < NG; ++k) {
+      tl[k] = trace_at<P, Pol>(L, s_ephi[jL][k]);
+      tr[k] = trace_at<P, Pol>(R, s_ephi[jR][NG - 1 - k]);
+      edge_flux<FLUX, T>(tl[k], tr[k], dcRL, nx, ny, g, H0, fz[k], fx[k], fy[k]);
+      ecanon = fma(tab.gw[k], fz[k], ecanon);
+    }
+    ecanon = ecanon * (T(0.5) * len);
+    const bool dryL = (L.flags & FLAG_DRY) != 0, dryR = (R.flags & FLAG_DRY) != 0;
+    const bool closed = (dryL && ecanon > T(0)) || (dryR && ecanon < T(0));
+    Lift<P, T> ol, orr;
+#pragma unroll
+    for (int v = 0; v < Lift<P, T>::NV; ++v) ol.v[v] = orr.v[v] = T(0);
+    ol.flag = orr.flag = closed ? 1u : 0u;
+    ol.mass = closed ? T(0) : ecanon;
+    orr.mass = closed ? T(0) : -ecanon;
+    if (!closed) {
+      constexpr int NS = NP - 1;
+#pragma unroll
+      for (int k = 0; k < NG; ++k) {
+        const T pl = T(0.5) * (pdev(tl[k].d, tl[k].H, g) + pdev(tr[k].d + dcRL, tr[k].H, g));
+        const T pr = T(0.5) * (pdev(tr[k].d, tr[k].H, g) + pdev(tl[k].d - dcRL, tl[k].H, g));
+        const T wk = tab.gw[k] * (T(0.5) * len);
+        // L: flux along n_L;  R: flux along n_R = -n_L
+        const T lz = fz[k], lx = fx[k] + pl * nx, ly = fy[k] + pl * ny;
+        const T rz = -fz[k], rx = -(fx[k] + pr * nx), ry = -(fy[k] + pr * ny);
+#pragma unroll
+        for (int m = 0; m < NP; ++m) {
+          const T phl = wk * s_ephi[jL][k][m], phr = wk * s_ephi[jR][NG - 1 - k][m];
+          if (m > 0) {
+            ol.v[m - 1] = fma(-phl, lz, ol.v[m - 1]);
+            orr.v[m - 1] = fma(-phr, rz, orr.v[m - 1]);
+          }
+          ol.v[NS + m] = fma(-phl, lx, ol.v[NS + m]);
+          ol.v[NS + NP + m] = fma(-phl, ly, ol.v[NS + NP + m]);
+          orr.v[NS + m] = fma(-phr, rx, orr.v[NS + m]);
+          orr.v[NS + NP + m] = fma(-phr, ry, orr.v[NS + NP + m]);
+        }
+      }
+    }
+    store_slot<P>(a.slots, 3LL * eL + jL, ol);
+    store_slot<P>(a.slots, 3LL * eR + jR, orr);
+  }
+}
+
 // ------------------------------------------------------------------------ stage kernel ----
 // Work split: 32-element tiles, warp w of the launch takes tiles w, w + W, w + 2W, ... (W warps
 // in the grid).  No block-wide barrier inside the loop; rain and boundary volumes accumulate per
@@ -631,7 +819,7 @@ __device__ __forceinline__ void flush_ledger(const StageArgs<Pol>& a, int sc, lo
   b = acc_make<Acc>(0.f, 0.f, 0.0);
 }
 
-template <int P, int FLUX, class Pol>
+template <int P, int FLUX, class Pol, bool SPLIT>
 __global__ void __launch_bounds__(256) stage_kernel(const StageArgs<Pol> a) {
   using T = typename Pol::T;
   using Acc = typename Pol::Acc;
@@ -695,15 +883,33 @@ __global__ void __launch_bounds__(256) stage_kernel(const StageArgs<Pol> a) {
       const int code = (j == 0) ? nb.x : (j == 1 ? nb.y : nb.z);
       const T lnx = (j == 0) ? G.lnx[0] : (j == 1 ? G.lnx[1] : G.lnx[2]);
       const T lny = (j == 0) ? G.lny[0] : (j == 1 ? G.lny[1] : G.lny[2]);
+      bool wall = (code == -1);
+      if (SPLIT && code >= 0) {  // interior edge: lift and mass flux from the edge kernel
+        Lift<P, T> lf;
+        load_slot<P>(a.slots, 3 * e + j, lf);
+        if (!lf.flag) {
+          constexpr int NSS = NP - 1;
+#pragma unroll
+          for (int m = 1; m < NP; ++m) Rz[m] += lf.v[m - 1];
+#pragma unroll
+          for (int m = 0; m < NP; ++m) {
+            Rx[m] += lf.v[NSS + m];
+            Ry[m] += lf.v[NSS + NP + m];
+          }
+          massout = acc_addr(massout, lf.mass);
+          continue;
+        }
+        wall = true;  // closed by the wet/dry rule: my own wall flux below
+      }
       const T len = fsqrt_pos(lnx * lnx + lny * lny);
       const T il = frcp(len);
       const T nx = lnx * il, ny = lny * il;
       Trace<T> tm[NG], to[NG];  // my trace and the other side's, at my edge points
 #pragma unroll
       for (int k = 0; k < NG; ++k) tm[k] = trace_at<P, Pol>(E, s_ephi[j][k]);
-      bool me_L = true, wall = (code == -1), dry_o = false;
+      bool me_L = true, dry_o = false;
       T dcRL = 0, dc_nm = 0;
-      if (code >= 0) {
+      if (!SPLIT && code >= 0) {
         const long long ne_ = code >> 2;
         const int jn = code & 3;
         Raw<RV> rnb;
@@ -1143,19 +1349,41 @@ static inline int grid_for(long long n, int block) {
   }                                                                                                          \
   template <>                                                                                                \
   cudaError_t launch_stage<POL>(int p, int flux, const StageArgs<POL>& a, int grid, int block, cudaStream_t s) { \
-    if (p == 1 && flux == 0) stage_kernel<1, 0, POL><<<grid, block, 0, s>>>(a);                               \
-    else if (p == 1) stage_kernel<1, 1, POL><<<grid, block, 0, s>>>(a);                                       \
-    else if (flux == 0) stage_kernel<2, 0, POL><<<grid, block, 0, s>>>(a);                                    \
-    else stage_kernel<2, 1, POL><<<grid, block, 0, s>>>(a);                                                  \
+    const int k = (p == 1 ? 0 : 4) + (flux ? 2 : 0) + (a.split ? 1 : 0);                                     \
+    switch (k) {                                                                                             \
+      case 0: stage_kernel<1, 0, POL, false><<<grid, block, 0, s>>>(a); break;                               \
+      case 1: stage_kernel<1, 0, POL, true><<<grid, block, 0, s>>>(a); break;                                \
+      case 2: stage_kernel<1, 1, POL, false><<<grid, block, 0, s>>>(a); break;                               \
+      case 3: stage_kernel<1, 1, POL, true><<<grid, block, 0, s>>>(a); break;                                \
+      case 4: stage_kernel<2, 0, POL, false><<<grid, block, 0, s>>>(a); break;                               \
+      case 5: stage_kernel<2, 0, POL, true><<<grid, block, 0, s>>>(a); break;                                \
+      case 6: stage_kernel<2, 1, POL, false><<<grid, block, 0, s>>>(a); break;                               \
+      default: stage_kernel<2, 1, POL, true><<<grid, block, 0, s>>>(a); break;                               \
+    }                                                                                                        \
     return cudaGetLastError();                                                                               \
   }                                                                                                          \
   template <>                                                                                                \
-  int stage_blocks_per_sm<POL>(int p, int flux, int block) {                                                 \
+  cudaError_t launch_edges<POL>(int p, int flux, const StageArgs<POL>& a, int grid, int block, cudaStream_t s) { \
+    if (p == 1 && flux == 0) edge_kernel<1, 0, POL><<<grid, block, 0, s>>>(a);                                \
+    else if (p == 1) edge_kernel<1, 1, POL><<<grid, block, 0, s>>>(a);                                        \
+    else if (flux == 0) edge_kernel<2, 0, POL><<<grid, block, 0, s>>>(a);                                     \
+    else edge_kernel<2, 1, POL><<<grid, block, 0, s>>>(a);                                                   \
+    return cudaGetLastError();                                                                               \
+  }                                                                                                          \
+  template <>                                                                                                \
+  int stage_blocks_per_sm<POL>(int p, int flux, int block, int split) {                                      \
     int n = 0;                                                                                               \
-    if (p == 1 && flux == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<1, 0, POL>, block, 0); \
-    else if (p == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<1, 1, POL>, block, 0);   \
-    else if (flux == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<2, 0, POL>, block, 0);\
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<2, 1, POL>, block, 0);               \
+    const int k = (p == 1 ? 0 : 4) + (flux ? 2 : 0) + (split ? 1 : 0);                                       \
+    switch (k) {                                                                                             \
+      case 0: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<1, 0, POL, false>, block, 0); break; \
+      case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<1, 0, POL, true>, block, 0); break; \
+      case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<1, 1, POL, false>, block, 0); break; \
+      case 3: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<1, 1, POL, true>, block, 0); break; \
+      case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<2, 0, POL, false>, block, 0); break; \
+      case 5: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<2, 0, POL, true>, block, 0); break; \
+      case 6: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<2, 1, POL, false>, block, 0); break; \
+      default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<2, 1, POL, true>, block, 0); break; \
+    }                                                                                                        \
     return n;                                                                                                \
   }                                                                                                          \
   template <>                                                                                                \

@@ -107,8 +107,8 @@ def lib():
         "dgswe_ensemble_step": ([_h, C.c_int64], C.c_int),
         "dgswe_ensemble_get_state": ([_h, C.c_int32, _d, _d, _d], C.c_int),
         "dgswe_ensemble_get_ledger": ([_h, C.c_int32, C.POINTER(Ledger)], C.c_int),
-        "dgswe_set_launch": ([_h, C.c_int32, C.c_int32], C.c_int),
-        "dgswe_get_launch": ([_h, _i, _i], C.c_int),
+        "dgswe_set_launch": ([_h, C.c_int32, C.c_int32, C.c_int32], C.c_int),
+        "dgswe_get_launch": ([_h, _i, _i, _i], C.c_int),
         "dgswe_launch_count": ([_h], C.c_int64),
         "dgswe_destroy": ([_h], None),
         "dgswe_last_error": ([], C.c_char_p),
@@ -248,13 +248,13 @@ class Solver:
         _check(lib().dgswe_volume(self.h, C.byref(v)))
         return v.value
 
-    def set_launch(self, block, waves=1):
-        _check(lib().dgswe_set_launch(self.h, block, waves))
+    def set_launch(self, block, waves=1, split=1):
+        _check(lib().dgswe_set_launch(self.h, block, waves, split))
 
     def launch(self):
-        b, p = C.c_int32(), C.c_int32()
-        _check(lib().dgswe_get_launch(self.h, C.byref(b), C.byref(p)))
-        return b.value, p.value
+        b, w, sp = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(lib().dgswe_get_launch(self.h, C.byref(b), C.byref(w), C.byref(sp)))
+        return b.value, w.value, sp.value
 
     def launch_count(self) -> int:
         return int(lib().dgswe_launch_count(self.h))
@@ -313,11 +313,11 @@ class Ensemble:
 
 
 def from_workload(w, precision=MIXED, flux=FLUX_ROE, ssp_stages=None, dt=0.0, friction=MANNING, cf=0.0, device=0,
-                  stream=None, block=0, waves=1) -> Solver:
+                  stream=None, block=0, waves=1, split=1) -> Solver:
     """A Solver set up with a workload's mesh, fields, forcing and nodal initial state."""
     s = Solver(p=w.p, flux=flux, ssp_stages=ssp_stages, precision=precision, H0=w.h0, cfl=w.cfl, dt=dt,
                friction=friction, cf=cf, device=device, stream=stream)
-    s.set_launch(block, waves)
+    s.set_launch(block, waves, split)
     s.set_mesh(w.mesh)
     s.set_fields(w.hb, w.manning if friction == MANNING else None)
     if w.rain_nodal is not None:

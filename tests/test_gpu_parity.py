@@ -205,16 +205,22 @@ def test_quadratic_friction_bathtub_short():
 # ----------------------------------------------------------- launch shapes, edge cases ----
 @pytest.mark.parametrize("prec", [D.FP64, D.MIXED])
 def test_launch_shapes_give_identical_bits(prec):
+    """Block size and waves do not change a single bit; fused and split agree to rounding."""
     w = W.coastal_c2(n_tri=5000, seed=5, steps=30)
-    outs = []
-    for block, waves in ((64, 1), (128, 2), (256, 1), (256, 2)):
-        dev = D.from_workload(w, precision=prec, block=block, waves=waves)
-        dev.step(30)
-        dev.sync()
-        assert dev.launch() == (block, waves)
-        outs.append(dev.state())
-    for o in outs[1:]:
-        assert np.array_equal(o, outs[0])
+    both = []
+    for split in (0, 1):
+        outs = []
+        for block, waves in ((64, 1), (128, 2), (256, 1), (256, 2)):
+            dev = D.from_workload(w, precision=prec, block=block, waves=waves, split=split)
+            dev.step(30)
+            dev.sync()
+            assert dev.launch() == (block, waves, split)
+            outs.append(dev.state())
+        for o in outs[1:]:
+            assert np.array_equal(o, outs[0])
+        both.append(outs[0])
+    tol = 1e-13 if prec == D.FP64 else 1e-5
+    assert np.abs(both[0] - both[1]).max() <= tol * max(1.0, np.abs(both[0]).max())
 
 
 def test_ragged_and_tiny_meshes():
