@@ -703,6 +703,40 @@ __device__ __forceinline__ void load_slot(const uint4* __restrict__ slots, long 
   L.flag = (uint32_t)__double2loint(f[NV + 1]);
 }
 
+// slot read from staged shared memory: vector i at base[i * stride]
+template <int P>
+__device__ __forceinline__ void load_slot(const uint4* base, long long, Lift<P, float>& L, int stride) {
+  constexpr int SV = slot_vec_mixed(P), NV = slot_vals(P);
+  float f[4 * SV];
+#pragma unroll
+  for (int i = 0; i < SV; ++i) {
+    const uint4 u = base[(size_t)i * stride];
+    f[4 * i] = __uint_as_float(u.x);
+    f[4 * i + 1] = __uint_as_float(u.y);
+    f[4 * i + 2] = __uint_as_float(u.z);
+    f[4 * i + 3] = __uint_as_float(u.w);
+  }
+#pragma unroll
+  for (int i = 0; i < NV; ++i) L.v[i] = f[i];
+  L.mass = f[NV];
+  L.flag = __float_as_uint(f[NV + 1]);
+}
+template <int P>
+__device__ __forceinline__ void load_slot(const uint4* base, long long, Lift<P, double>& L, int stride) {
+  constexpr int SV = slot_vec_fp64(P), NV = slot_vals(P);
+  double f[2 * SV];
+#pragma unroll
+  for (int i = 0; i < SV; ++i) {
+    const uint4 u = base[(size_t)i * stride];
+    f[2 * i] = u2d(u.x, u.y);
+    f[2 * i + 1] = u2d(u.z, u.w);
+  }
+#pragma unroll
+  for (int i = 0; i < NV; ++i) L.v[i] = f[i];
+  L.mass = f[NV];
+  L.flag = (uint32_t)__double2loint(f[NV + 1]);
+}
+
 __device__ __forceinline__ void load_edge(const uint4* e, long long i, int& eL, int& jL, int& eR, int& jR, float& lnx,
                                           float& lny) {
   const uint4 u = __ldg(e + i);
@@ -819,26 +853,52 @@ __device__ __forceinline__ void flush_ledger(const StageArgs<Pol>& a, int sc, lo
   b = acc_make<Acc>(0.f, 0.f, 0.0);
 }
 
+// asynchronous global -> shared copies of 16 bytes (the copying thread owns the data)
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// dynamic shared memory of the element kernel: per thread, the three neighbour records (fused)
+// or the three edge slots (split), then the step-initial record; interleaved by thread so that
+// the 16-byte reads of a warp hit distinct banks
+template <int P, class Pol, bool SPLIT>
+struct Staging {
+  static constexpr int RV = Pol::template RV<P>;
+  static constexpr int SV = SlotT<Pol>::template SV<P>;
+  static constexpr int PER_EDGE = SPLIT ? SV : RV;
+  static constexpr int VEC = 3 * PER_EDGE + RV;  // 16-byte vectors per thread
+};
+template <int P, class Pol, bool SPLIT>
+__host__ __device__ constexpr int staging_bytes(int block) {
+  return 16 * Staging<P, Pol, SPLIT>::VEC * block;
+}
+
 template <int P, int FLUX, class Pol, bool SPLIT>
 __global__ void __launch_bounds__(256) stage_kernel(const StageArgs<Pol> a) {
   using T = typename Pol::T;
   using Acc = typename Pol::Acc;
+  using St = Staging<P, Pol, SPLIT>;
   constexpr int NP = np_of(P), NS = NP - 1, NG = P + 1;
   constexpr int RV = Pol::template RV<P>;
   constexpr int NQ = (P == 0) ? 1 : 7;
   const RefTab<T>& tab = ctab<T, P>();
 
   __shared__ T s_ephi[3][NG][NP];  // edge basis values, read at neighbour-dependent indices
-  const int tid = threadIdx.x;
-  for (int i = tid; i < 3 * NG * NP; i += blockDim.x) {
+  extern __shared__ uint4 stg[];   // [St::VEC][blockDim]
+  const int tid = threadIdx.x, B = blockDim.x;
+  for (int i = tid; i < 3 * NG * NP; i += B) {
     const int j = i / (NG * NP), k = (i / NP) % NG, m = i % NP;
     s_ephi[j][k][m] = tab.ephi[j][k][m];
   }
   __syncthreads();
+  auto sv = [&](int v) -> uint4* { return stg + (size_t)v * B + tid; };
 
   const int lane = tid & 31;
-  const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + (tid >> 5);
-  const long long W = (long long)gridDim.x * (blockDim.x >> 5);
+  const long long gw = (long long)blockIdx.x * (B >> 5) + (tid >> 5);
+  const long long W = (long long)gridDim.x * (B >> 5);
   const T stepc = (T)a.ctl->step + (sizeof(T) == 4 ? (T)a.cst_f : (T)a.cst);
   const T g = a.g, H0 = a.H0;
   Acc rain_acc = acc_make<Acc>(0.f, 0.f, 0.0), bdry_acc = acc_make<Acc>(0.f, 0.f, 0.0);
@@ -857,12 +917,34 @@ __global__ void __launch_bounds__(256) stage_kernel(const StageArgs<Pol> a) {
     const T t = F.t0 + stepc * F.dt;
 
     const int4 nb = __ldg(a.nbr + e);
+    // stage what the edge loop and the combination need, asynchronously
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int code = (j == 0) ? nb.x : (j == 1 ? nb.y : nb.z);
+      if (SPLIT) {
+        const uint4* src = a.slots + (3 * e + j) * St::SV;
+#pragma unroll
+        for (int i = 0; i < St::SV; ++i) cp_async16(sv(j * St::PER_EDGE + i), src + i);
+      } else if (code >= 0) {
+        const uint4* src = a.in + (long long)(code >> 2) * RV;
+#pragma unroll
+        for (int i = 0; i < RV; ++i) cp_async16(sv(j * St::PER_EDGE + i), src + i);
+      }
+    }
+    if (a.has_n) {
+      const uint4* src = a.wn + e * RV;
+#pragma unroll
+      for (int i = 0; i < RV; ++i) cp_async16(sv(3 * St::PER_EDGE + i), src + i);
+    }
+    cp_async_commit();
+
     Geo<Pol> G;
     load_geo(a.geo, e, nb, G);
     Raw<RV> rme;
     load_raw<RV>(a.in, e, rme);
     Elem<P, Pol> E;
     unpack<P>(rme, E);
+    const int4 nd = (S.rain_kind >= 2 || S.press) ? __ldg(a.nodes + e) : make_int4(0, 0, 0, 0);
     const bool dry_me = (E.flags & FLAG_DRY) != 0;
     const T detJ = T(0.5) * acc_r(G.A);
     const T idetJ = T(2) * acc_r(G.invA);
@@ -875,9 +957,129 @@ __global__ void __launch_bounds__(256) stage_kernel(const StageArgs<Pol> a) {
     T Rz[NP], Rx[NP], Ry[NP];  // weak-form integrals against each basis function
 #pragma unroll
     for (int m = 0; m < NP; ++m) Rz[m] = Rx[m] = Ry[m] = 0;
-    Acc massout = acc_make<Acc>(0.f, 0.f, 0.0);  // edge mass outflow (volume per second)
 
-    // ---- 1. edge integrals <Fhat.n, v>
+    // ---- area integrals (grad v, F) + (s, v), while the staged copies are in flight
+    const T g1x = tab.qdr[0][1] * rx + tab.qds[0][1] * sx, g1y = tab.qdr[0][1] * ry + tab.qds[0][1] * sy;
+    const T g2x = tab.qdr[0][2] * rx + tab.qds[0][2] * sx, g2y = tab.qdr[0][2] * ry + tab.qds[0][2] * sy;
+    const T hbx = E.hb1 * g1x + E.hb2 * g2x, hby = E.hb1 * g1y + E.hb2 * g2y;  // constant grad(hb)
+    const T cfm = (a.friction == 0) ? g * G.man * G.man : a.cf;
+    T vx[3] = {0, 0, 0}, vy[3] = {0, 0, 0};
+    if (S.press) {
+      vx[0] = a.node_xy[2 * (long long)nd.x]; vy[0] = a.node_xy[2 * (long long)nd.x + 1];
+      vx[1] = a.node_xy[2 * (long long)nd.y]; vy[1] = a.node_xy[2 * (long long)nd.y + 1];
+      vx[2] = a.node_xy[2 * (long long)nd.z]; vy[2] = a.node_xy[2 * (long long)nd.z + 1];
+    }
+    // p = 1: the basis gradients are constant, so accumulate flux sums and source moments per
+    // point and apply the gradients once
+    T SF[6] = {0, 0, 0, 0, 0, 0};       // sum_q w_q (fx_z, fx_x, fx_y, fy_z, fy_x, fy_y)
+    T SS[NP][2];                        // sum_q w_q phi_m s_(x,y)
+#pragma unroll
+    for (int m = 0; m < NP; ++m) SS[m][0] = SS[m][1] = 0;
+#pragma unroll 1
+    for (int q = 0; q < NQ; ++q) {
+      const Trace<T> tq = trace_at<P, Pol>(E, tab.qphi[q]);
+      const T Hs = max_r(tq.H, H0);
+      const T iH = frcp(Hs);
+      const T u = tq.qx * iH, v = tq.qy * iH;
+      const T pp = pdev(tq.d, tq.H, g);
+      T tau = 0;
+      if (a.friction == 0) tau = cfm * fsqrt0(u * u + v * v) * fpowm43(Hs);
+      else if (a.friction == 1) tau = cfm * fsqrt0(u * u + v * v) * iH;
+      T Fxs = 0, Fys = 0;
+      if (S.press) {
+        const T px = tab.ql[q][0] * vx[0] + tab.ql[q][1] * vx[1] + tab.ql[q][2] * vx[2];
+        const T py = tab.ql[q][0] * vy[0] + tab.ql[q][1] * vy[1] + tab.ql[q][2] * vy[2];
+        const T dx = px - F.ps[0], dy = py - F.ps[1], is2 = frcp(F.ps[2] * F.ps[2]);
+        const T eta = F.ps[3] * fexp(-(dx * dx + dy * dy) * T(0.5) * is2);
+        Fxs = g * tq.H * (-eta * dx * is2);
+        Fys = g * tq.H * (-eta * dy * is2);
+      }
+      const T sx_ = g * tq.d * hbx - tau * tq.qx + Fxs;
+      const T sy_ = g * tq.d * hby - tau * tq.qy + Fys;
+      const T fxx = tq.qx * u + pp, fyx = tq.qx * v;
+      const T fxy = tq.qy * u, fyy = tq.qy * v + pp;
+      const T w = tab.qw[q];
+      if (P == 1) {
+        SF[0] = fma(w, tq.qx, SF[0]);
+        SF[1] = fma(w, fxx, SF[1]);
+        SF[2] = fma(w, fxy, SF[2]);
+        SF[3] = fma(w, tq.qy, SF[3]);
+        SF[4] = fma(w, fyx, SF[4]);
+        SF[5] = fma(w, fyy, SF[5]);
+#pragma unroll
+        for (int m = 0; m < NP; ++m) {
+          const T wp = w * tab.qphi[q][m];
+          SS[m][0] = fma(wp, sx_, SS[m][0]);
+          SS[m][1] = fma(wp, sy_, SS[m][1]);
+        }
+      } else {
+        const T wq = w * detJ;
+#pragma unroll
+        for (int m = 0; m < NP; ++m) {
+          const T dxm = tab.qdr[q][m] * rx + tab.qds[q][m] * sx;
+          const T dym = tab.qdr[q][m] * ry + tab.qds[q][m] * sy;
+          const T ph = tab.qphi[q][m];
+          if (m > 0) Rz[m] = fma(wq, dxm * tq.qx + dym * tq.qy, Rz[m]);
+          Rx[m] = fma(wq, dxm * fxx + dym * fyx + ph * sx_, Rx[m]);
+          Ry[m] = fma(wq, dxm * fxy + dym * fyy + ph * sy_, Ry[m]);
+        }
+      }
+    }
+    if (P == 1) {
+      const T gx[3] = {T(0), g1x, g2x}, gy[3] = {T(0), g1y, g2y};
+#pragma unroll
+      for (int m = 0; m < NP; ++m) {
+        if (m > 0) Rz[m] = detJ * (gx[m] * SF[0] + gy[m] * SF[3]);
+        Rx[m] = detJ * (gx[m] * SF[1] + gy[m] * SF[4] + SS[m][0]);
+        Ry[m] = detJ * (gx[m] * SF[2] + gy[m] * SF[5] + SS[m][1]);
+      }
+    }
+
+    // ---- forcing: element rain = mean of the three nodal rates (Eq. rain)
+    T Re = 0;
+    if (S.rain_kind == 1) {
+      Re = a.rain_e[e];
+    } else if (S.rain_kind >= 2) {
+      T acc = 0;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const long long n = (i == 0) ? nd.x : (i == 1 ? nd.y : nd.z);
+        const T px = a.node_xy[2 * n], py = a.node_xy[2 * n + 1];
+        if (S.rain_kind == 2) {
+          const T tt = t - F.storm[7];
+          const T dx = px - (F.storm[0] + F.storm[2] * tt), dy = py - (F.storm[1] + F.storm[3] * tt);
+          const T r = fsqrt0(dx * dx + dy * dy);
+          const T rp = F.storm[4], rm = F.storm[5], re = F.storm[6];
+          acc += (r < rm) ? rp * (T(0.5) + T(0.5) * fdiv(r, rm)) : rp * fexp(-fdiv(r - rm, re));
+        } else {
+          T gx = (px - F.grid[0]) * F.grid[2], gy = (py - F.grid[1]) * F.grid[3];
+          T gt = (t - F.grid[4]) * F.grid[5];
+          gx = fmin(fmax(gx, T(0)), T(S.gnx - 1));
+          gy = fmin(fmax(gy, T(0)), T(S.gny - 1));
+          gt = fmin(fmax(gt, T(0)), T(S.gnt - 1));
+          const int ix = min(max((int)floor(gx), 0), max(S.gnx - 2, 0));
+          const int iy = min(max((int)floor(gy), 0), max(S.gny - 2, 0));
+          const int it = min(max((int)floor(gt), 0), max(S.gnt - 2, 0));
+          const T fx = gx - T(ix), fy = gy - T(iy), ft = gt - T(it);
+          const int ix1 = S.gnx > 1 ? ix + 1 : ix, iy1 = S.gny > 1 ? iy + 1 : iy;
+          T val[2];
+#pragma unroll
+          for (int qq = 0; qq < 2; ++qq) {
+            const int kk = S.gnt > 1 ? it + qq : 0;
+            const float* Gr = S.grid + (size_t)kk * S.gnx * S.gny;
+            const T v00 = Gr[(size_t)iy * S.gnx + ix], v10 = Gr[(size_t)iy * S.gnx + ix1];
+            const T v01 = Gr[(size_t)iy1 * S.gnx + ix], v11 = Gr[(size_t)iy1 * S.gnx + ix1];
+            val[qq] = (T(1) - fy) * ((T(1) - fx) * v00 + fx * v10) + fy * ((T(1) - fx) * v01 + fx * v11);
+          }
+          acc += ((T(1) - ft) * val[0] + ft * val[1]) * T(1.0 / 3.6e6);
+        }
+      }
+      Re = acc * T(1.0 / 3.0);
+    }
+
+    // ---- edge integrals <Fhat.n, v>, from the staged neighbour records or edge slots
+    cp_async_wait_all();
+    Acc massout = acc_make<Acc>(0.f, 0.f, 0.0);  // edge mass outflow (volume per second)
 #pragma unroll 1
     for (int j = 0; j < 3; ++j) {
       const int code = (j == 0) ? nb.x : (j == 1 ? nb.y : nb.z);
@@ -886,15 +1088,14 @@ __global__ void __launch_bounds__(256) stage_kernel(const StageArgs<Pol> a) {
       bool wall = (code == -1);
       if (SPLIT && code >= 0) {  // interior edge: lift and mass flux from the edge kernel
         Lift<P, T> lf;
-        load_slot<P>(a.slots, 3 * e + j, lf);
+        load_slot<P>(sv(j * St::PER_EDGE), 0, lf, B);
         if (!lf.flag) {
-          constexpr int NSS = NP - 1;
 #pragma unroll
           for (int m = 1; m < NP; ++m) Rz[m] += lf.v[m - 1];
 #pragma unroll
           for (int m = 0; m < NP; ++m) {
-            Rx[m] += lf.v[NSS + m];
-            Ry[m] += lf.v[NSS + NP + m];
+            Rx[m] += lf.v[NS + m];
+            Ry[m] += lf.v[NS + NP + m];
           }
           massout = acc_addr(massout, lf.mass);
           continue;
@@ -913,7 +1114,8 @@ __global__ void __launch_bounds__(256) stage_kernel(const StageArgs<Pol> a) {
         const long long ne_ = code >> 2;
         const int jn = code & 3;
         Raw<RV> rnb;
-        load_raw<RV>(a.in, ne_, rnb);
+#pragma unroll
+        for (int i = 0; i < RV; ++i) rnb.v[i] = *sv(j * St::PER_EDGE + i);
         Elem<P, Pol> N;
         unpack<P>(rnb, N);
         me_L = e < ne_;
@@ -992,102 +1194,12 @@ __global__ void __launch_bounds__(256) stage_kernel(const StageArgs<Pol> a) {
         }
       }
     }
-
-    // ---- 2. forcing: element rain = mean of the three nodal rates (Eq. rain)
-    T Re = 0;
-    if (S.rain_kind == 1) {
-      Re = a.rain_e[e];
-    } else if (S.rain_kind >= 2) {
-      const int4 nd = __ldg(a.nodes + e);
-      T acc = 0;
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const long long n = (i == 0) ? nd.x : (i == 1 ? nd.y : nd.z);
-        const T px = a.node_xy[2 * n], py = a.node_xy[2 * n + 1];
-        if (S.rain_kind == 2) {
-          const T tt = t - F.storm[7];
-          const T dx = px - (F.storm[0] + F.storm[2] * tt), dy = py - (F.storm[1] + F.storm[3] * tt);
-          const T r = fsqrt0(dx * dx + dy * dy);
-          const T rp = F.storm[4], rm = F.storm[5], re = F.storm[6];
-          acc += (r < rm) ? rp * (T(0.5) + T(0.5) * fdiv(r, rm)) : rp * fexp(-fdiv(r - rm, re));
-        } else {
-          T gx = (px - F.grid[0]) * F.grid[2], gy = (py - F.grid[1]) * F.grid[3];
-          T gt = (t - F.grid[4]) * F.grid[5];
-          gx = fmin(fmax(gx, T(0)), T(S.gnx - 1));
-          gy = fmin(fmax(gy, T(0)), T(S.gny - 1));
-          gt = fmin(fmax(gt, T(0)), T(S.gnt - 1));
-          const int ix = min(max((int)floor(gx), 0), max(S.gnx - 2, 0));
-          const int iy = min(max((int)floor(gy), 0), max(S.gny - 2, 0));
-          const int it = min(max((int)floor(gt), 0), max(S.gnt - 2, 0));
-          const T fx = gx - T(ix), fy = gy - T(iy), ft = gt - T(it);
-          const int ix1 = S.gnx > 1 ? ix + 1 : ix, iy1 = S.gny > 1 ? iy + 1 : iy;
-          T val[2];
-#pragma unroll
-          for (int q = 0; q < 2; ++q) {
-            const int kk = S.gnt > 1 ? it + q : 0;
-            const float* Gr = S.grid + (size_t)kk * S.gnx * S.gny;
-            const T v00 = Gr[(size_t)iy * S.gnx + ix], v10 = Gr[(size_t)iy * S.gnx + ix1];
-            const T v01 = Gr[(size_t)iy1 * S.gnx + ix], v11 = Gr[(size_t)iy1 * S.gnx + ix1];
-            val[q] = (T(1) - fy) * ((T(1) - fx) * v00 + fx * v10) + fy * ((T(1) - fx) * v01 + fx * v11);
-          }
-          acc += ((T(1) - ft) * val[0] + ft * val[1]) * T(1.0 / 3.6e6);
-        }
-      }
-      Re = acc * T(1.0 / 3.0);
-    }
-
-    // ---- 3. area integrals (grad v, F) + (s, v)
-    const T g1x = tab.qdr[0][1] * rx + tab.qds[0][1] * sx, g1y = tab.qdr[0][1] * ry + tab.qds[0][1] * sy;
-    const T g2x = tab.qdr[0][2] * rx + tab.qds[0][2] * sx, g2y = tab.qdr[0][2] * ry + tab.qds[0][2] * sy;
-    const T hbx = E.hb1 * g1x + E.hb2 * g2x, hby = E.hb1 * g1y + E.hb2 * g2y;  // constant grad(hb)
-    const T cfm = (a.friction == 0) ? g * G.man * G.man : a.cf;
-    T vx[3] = {0, 0, 0}, vy[3] = {0, 0, 0};
-    if (S.press) {
-      const int4 nd = __ldg(a.nodes + e);
-      vx[0] = a.node_xy[2 * (long long)nd.x]; vy[0] = a.node_xy[2 * (long long)nd.x + 1];
-      vx[1] = a.node_xy[2 * (long long)nd.y]; vy[1] = a.node_xy[2 * (long long)nd.y + 1];
-      vx[2] = a.node_xy[2 * (long long)nd.z]; vy[2] = a.node_xy[2 * (long long)nd.z + 1];
-    }
-#pragma unroll 1
-    for (int q = 0; q < NQ; ++q) {
-      const Trace<T> tq = trace_at<P, Pol>(E, tab.qphi[q]);
-      const T Hs = max_r(tq.H, H0);
-      const T iH = frcp(Hs);
-      const T u = tq.qx * iH, v = tq.qy * iH;
-      const T pp = pdev(tq.d, tq.H, g);
-      T tau = 0;
-      if (a.friction == 0) tau = cfm * fsqrt0(u * u + v * v) * fpowm43(Hs);
-      else if (a.friction == 1) tau = cfm * fsqrt0(u * u + v * v) * iH;
-      T Fxs = 0, Fys = 0;
-      if (S.press) {
-        const T px = tab.ql[q][0] * vx[0] + tab.ql[q][1] * vx[1] + tab.ql[q][2] * vx[2];
-        const T py = tab.ql[q][0] * vy[0] + tab.ql[q][1] * vy[1] + tab.ql[q][2] * vy[2];
-        const T dx = px - F.ps[0], dy = py - F.ps[1], is2 = frcp(F.ps[2] * F.ps[2]);
-        const T eta = F.ps[3] * fexp(-(dx * dx + dy * dy) * T(0.5) * is2);
-        Fxs = g * tq.H * (-eta * dx * is2);
-        Fys = g * tq.H * (-eta * dy * is2);
-      }
-      const T sx_ = g * tq.d * hbx - tau * tq.qx + Fxs;
-      const T sy_ = g * tq.d * hby - tau * tq.qy + Fys;
-      const T fxx = tq.qx * u + pp, fyx = tq.qx * v;
-      const T fxy = tq.qy * u, fyy = tq.qy * v + pp;
-      const T wq = tab.qw[q] * detJ;
-#pragma unroll
-      for (int m = 0; m < NP; ++m) {
-        const T dxm = tab.qdr[q][m] * rx + tab.qds[q][m] * sx;
-        const T dym = tab.qdr[q][m] * ry + tab.qds[q][m] * sy;
-        const T ph = tab.qphi[q][m];
-        if (m > 0) Rz[m] = fma(wq, dxm * tq.qx + dym * tq.qy, Rz[m]);
-        Rx[m] = fma(wq, dxm * fxx + dym * fyx + ph * sx_, Rx[m]);
-        Ry[m] = fma(wq, dxm * fxy + dym * fyy + ph * sy_, Ry[m]);
-      }
-    }
     if (dry_me) {  // the momentum equations are not advanced on dry elements
 #pragma unroll
       for (int m = 0; m < NP; ++m) Rx[m] = Ry[m] = 0;
     }
 
-    // ---- 4. Shu-Osher combination: out = a_n w^n + a_in w^in + beta dt M^{-1} R
+    // ---- Shu-Osher combination: out = a_n w^n + a_in w^in + beta dt M^{-1} R
     const Acc an = acc_make<Acc>(a.a_n_hi, a.a_n_lo, a.a_n);
     const Acc ain = acc_make<Acc>(a.a_in_hi, a.a_in_lo, a.a_in);
     const Acc bdt = acc_make<Acc>(S.bdt_hi[a.stage], S.bdt_lo[a.stage], S.bdt[a.stage]);
@@ -1098,7 +1210,8 @@ __global__ void __launch_bounds__(256) stage_kernel(const StageArgs<Pol> a) {
     Elem<P, Pol> Wn = E;
     if (a.has_n) {
       Raw<RV> rn;
-      load_raw<RV>(a.wn, e, rn);
+#pragma unroll
+      for (int i = 0; i < RV; ++i) rn.v[i] = *sv(3 * St::PER_EDGE + i);
       unpack<P>(rn, Wn);
     }
     {
@@ -1129,13 +1242,13 @@ __global__ void __launch_bounds__(256) stage_kernel(const StageArgs<Pol> a) {
       O.ys[m] = y;
     }
 
-    // ---- 5. positive-depth operator, store
+    // ---- positive-depth operator, store
     apply_positivity<P, Pol>(O, G, e, a, &a.ctl->err);
     Raw<RV> ro;
     pack<P>(O, ro);
     store_raw<RV>(a.out, e, ro);
 
-    // ---- 6. ledger: rain volume rate of the element
+    // ---- ledger: rain volume rate of the element
     rain_acc = acc_add(rain_acc, acc_mulr(G.A, Re));
   }
   if (cur >= 0 && !a.tune) flush_ledger<P, Pol>(a, cur, gw, rain_acc, bdry_acc);
@@ -1345,20 +1458,31 @@ static inline int grid_for(long long n, int block) {
   cudaError_t upload_tables<POL>(int p, const RefTab<float>& tf, const RefTab<double>& td) {                 \
     cudaError_t e = cudaMemcpyToSymbol(c_tab_f, &tf, sizeof(RefTab<float>), p * sizeof(RefTab<float>));     \
     if (e != cudaSuccess) return e;                                                                          \
+    const int m1 = staging_bytes<1, POL, false>(256), m1s = staging_bytes<1, POL, true>(256);                \
+    const int m2 = staging_bytes<2, POL, false>(256), m2s = staging_bytes<2, POL, true>(256);                \
+    const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;                                 \
+    cudaFuncSetAttribute(stage_kernel<1, 0, POL, false>, A, m1);                                             \
+    cudaFuncSetAttribute(stage_kernel<1, 1, POL, false>, A, m1);                                             \
+    cudaFuncSetAttribute(stage_kernel<1, 0, POL, true>, A, m1s);                                             \
+    cudaFuncSetAttribute(stage_kernel<1, 1, POL, true>, A, m1s);                                             \
+    cudaFuncSetAttribute(stage_kernel<2, 0, POL, false>, A, m2);                                             \
+    cudaFuncSetAttribute(stage_kernel<2, 1, POL, false>, A, m2);                                             \
+    cudaFuncSetAttribute(stage_kernel<2, 0, POL, true>, A, m2s);                                             \
+    cudaFuncSetAttribute(stage_kernel<2, 1, POL, true>, A, m2s);                                             \
     return cudaMemcpyToSymbol(c_tab_d, &td, sizeof(RefTab<double>), p * sizeof(RefTab<double>));            \
   }                                                                                                          \
   template <>                                                                                                \
   cudaError_t launch_stage<POL>(int p, int flux, const StageArgs<POL>& a, int grid, int block, cudaStream_t s) { \
     const int k = (p == 1 ? 0 : 4) + (flux ? 2 : 0) + (a.split ? 1 : 0);                                     \
     switch (k) {                                                                                             \
-      case 0: stage_kernel<1, 0, POL, false><<<grid, block, 0, s>>>(a); break;                               \
-      case 1: stage_kernel<1, 0, POL, true><<<grid, block, 0, s>>>(a); break;                                \
-      case 2: stage_kernel<1, 1, POL, false><<<grid, block, 0, s>>>(a); break;                               \
-      case 3: stage_kernel<1, 1, POL, true><<<grid, block, 0, s>>>(a); break;                                \
-      case 4: stage_kernel<2, 0, POL, false><<<grid, block, 0, s>>>(a); break;                               \
-      case 5: stage_kernel<2, 0, POL, true><<<grid, block, 0, s>>>(a); break;                                \
-      case 6: stage_kernel<2, 1, POL, false><<<grid, block, 0, s>>>(a); break;                               \
-      default: stage_kernel<2, 1, POL, true><<<grid, block, 0, s>>>(a); break;                               \
+      case 0: stage_kernel<1, 0, POL, false><<<grid, block, staging_bytes<1, POL, false>(block), s>>>(a); break; \
+      case 1: stage_kernel<1, 0, POL, true><<<grid, block, staging_bytes<1, POL, true>(block), s>>>(a); break; \
+      case 2: stage_kernel<1, 1, POL, false><<<grid, block, staging_bytes<1, POL, false>(block), s>>>(a); break; \
+      case 3: stage_kernel<1, 1, POL, true><<<grid, block, staging_bytes<1, POL, true>(block), s>>>(a); break; \
+      case 4: stage_kernel<2, 0, POL, false><<<grid, block, staging_bytes<2, POL, false>(block), s>>>(a); break; \
+      case 5: stage_kernel<2, 0, POL, true><<<grid, block, staging_bytes<2, POL, true>(block), s>>>(a); break; \
+      case 6: stage_kernel<2, 1, POL, false><<<grid, block, staging_bytes<2, POL, false>(block), s>>>(a); break; \
+      default: stage_kernel<2, 1, POL, true><<<grid, block, staging_bytes<2, POL, true>(block), s>>>(a); break; \
     }                                                                                                        \
     return cudaGetLastError();                                                                               \
   }                                                                                                          \
@@ -1375,14 +1499,14 @@ static inline int grid_for(long long n, int block) {
     int n = 0;                                                                                               \
     const int k = (p == 1 ? 0 : 4) + (flux ? 2 : 0) + (split ? 1 : 0);                                       \
     switch (k) {                                                                                             \
-      case 0: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<1, 0, POL, false>, block, 0); break; \
-      case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<1, 0, POL, true>, block, 0); break; \
-      case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<1, 1, POL, false>, block, 0); break; \
-      case 3: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<1, 1, POL, true>, block, 0); break; \
-      case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<2, 0, POL, false>, block, 0); break; \
-      case 5: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<2, 0, POL, true>, block, 0); break; \
-      case 6: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<2, 1, POL, false>, block, 0); break; \
-      default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<2, 1, POL, true>, block, 0); break; \
+      case 0: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<1, 0, POL, false>, block, staging_bytes<1, POL, false>(block)); break; \
+      case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<1, 0, POL, true>, block, staging_bytes<1, POL, true>(block)); break; \
+      case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<1, 1, POL, false>, block, staging_bytes<1, POL, false>(block)); break; \
+      case 3: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<1, 1, POL, true>, block, staging_bytes<1, POL, true>(block)); break; \
+      case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<2, 0, POL, false>, block, staging_bytes<2, POL, false>(block)); break; \
+      case 5: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<2, 0, POL, true>, block, staging_bytes<2, POL, true>(block)); break; \
+      case 6: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<2, 1, POL, false>, block, staging_bytes<2, POL, false>(block)); break; \
+      default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<2, 1, POL, true>, block, staging_bytes<2, POL, true>(block)); break; \
     }                                                                                                        \
     return n;                                                                                                \
   }                                                                                                          \
