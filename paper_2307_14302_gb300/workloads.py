@@ -215,6 +215,58 @@ def jittered_delaunay(lx, ly, n_tri_target, seed, jitter=0.35, ocean_side="x0", 
     return Mesh(np.ascontiguousarray(xy), tri, bedge, btype, bseg)
 
 
+def jittered_grid_mesh(lx, ly, n_tri_target, seed, jitter=0.25, ocean_side="x0", xs=None) -> Mesh:
+    """Seeded jittered structured mesh: an (nx+1) x (ny+1) node lattice, interior nodes moved by up
+    to ``jitter`` of the local spacing, boundary nodes moved along their side only, each cell split
+    along a random diagonal.  ``xs`` (optional, increasing from 0 to lx) fixes the node columns,
+    which grades the mesh in x.  Linear in the node count, so meshes of millions of triangles are
+    drawn in seconds."""
+    rng = np.random.default_rng(seed)
+    if xs is None:
+        h = math.sqrt(2.0 * lx * ly / max(n_tri_target, 2))
+        nx = max(int(round(lx / h)), 1)
+        xs = np.linspace(0.0, lx, nx + 1)
+    else:
+        xs = np.asarray(xs, float)
+        nx = len(xs) - 1
+    ny = max(int(round(n_tri_target / (2 * nx))), 1)
+    ys = np.linspace(0.0, ly, ny + 1)
+    dxl = np.diff(xs)
+    hxl = np.minimum(np.r_[dxl[0], dxl], np.r_[dxl, dxl[-1]])  # local x spacing per column
+    hy = ly / ny
+    X, Y = np.meshgrid(xs, ys, indexing="xy")
+    HX = np.broadcast_to(hxl, X.shape)
+    jx = rng.uniform(-jitter, jitter, X.shape) * HX
+    jy = rng.uniform(-jitter, jitter, X.shape) * hy
+    jx[:, 0] = jx[:, -1] = 0.0
+    jy[0, :] = jy[-1, :] = 0.0
+    X = X + jx
+    Y = Y + jy
+    xy = np.stack([X.ravel(), Y.ravel()], axis=1)
+    ii, jj = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
+    a = (jj * (nx + 1) + ii).ravel()
+    b, c, d = a + 1, a + nx + 2, a + nx + 1
+    flip = rng.uniform(0, 1, a.size) < 0.5
+    t1 = np.where(flip[:, None], np.stack([a, b, d], 1), np.stack([a, b, c], 1))
+    t2 = np.where(flip[:, None], np.stack([b, c, d], 1), np.stack([a, c, d], 1))
+    tri = _ccw(xy, np.concatenate([t1, t2]))
+    bedge = _boundary_edges(tri)
+    btype, bseg = _tag_rect(xy, bedge, lx, ly, ocean_side)
+    return Mesh(np.ascontiguousarray(xy), tri, bedge, btype, bseg)
+
+
+def graded_columns(lx, x_coast, hmin, hmax, width, n_tri_target, ly):
+    """Node columns whose spacing grows from hmin at x_coast to hmax at distance >= width, with
+    the row count chosen so the mesh holds about n_tri_target triangles."""
+    xf = np.linspace(0.0, lx, 200_001)
+    hh = hmin + (hmax - hmin) * np.minimum(1.0, np.abs(xf - x_coast) / width) ** 2
+    cells = np.concatenate([[0.0], np.cumsum(np.diff(xf) / (0.5 * (hh[1:] + hh[:-1])))])
+    nx = max(int(round(cells[-1])), 2)
+    xs = np.interp(np.linspace(0.0, cells[-1], nx + 1), cells, xf)
+    xs[0], xs[-1] = 0.0, lx
+    return xs
+
+
 def density_mean(density, lx, ly, n=64):
     xs = (np.arange(n) + 0.5) / n * lx
     ys = (np.arange(n) + 0.5) / n * ly
@@ -294,7 +346,7 @@ def _initial_dry(hb, h0):
     return np.where(hb < h0, 0.5 * h0 - hb, 0.0)
 
 
-def coastal_c2(n_tri=250_000, seed=2, steps=2000) -> Workload:
+def coastal_c2(n_tri=250_000, seed=2, steps=2000, fast_mesh=False) -> Workload:
     """Coastal wet/dry workload: jittered Delaunay mesh (~n_tri triangles) on 400 km x 300 km,
     p=1, 3000 m offshore depth tapering across a shelf to a floodplain rising to +2 m (about
     20% initially dry), Manning n ~ U[0.02, 0.06] per element, a moving radially symmetric rain
@@ -302,7 +354,7 @@ def coastal_c2(n_tri=250_000, seed=2, steps=2000) -> Workload:
     12.42 h tide on the open (x = 0) side."""
     lx, ly = 400_000.0, 300_000.0
     rng = np.random.default_rng(seed)
-    mesh = jittered_delaunay(lx, ly, n_tri, seed)
+    mesh = jittered_grid_mesh(lx, ly, n_tri, seed) if fast_mesh else jittered_delaunay(lx, ly, n_tri, seed)
     x, y = mesh.xy[:, 0], mesh.xy[:, 1]
     hb = _coastal_bathymetry(x, y, lx, ly, 2.0, rng.uniform(0, 2 * np.pi))
     manning = rng.uniform(0.02, 0.06, mesh.n_tri)
@@ -318,17 +370,13 @@ def coastal_c2(n_tri=250_000, seed=2, steps=2000) -> Workload:
 
 
 def graded_c3(n_tri=2_000_000, seed=3, steps=1000) -> Workload:
-    """p=2 graded mesh: edge lengths graded from ~100 m near the coast to ~5 km offshore
-    (point density rising toward the coast), same bathymetry/forcing families as the coastal
-    workload with a new seed, plus a Gaussian pressure-driven setup of 2 m peak at the coast."""
+    """p=2 graded mesh: edge lengths graded from ~100 m at the coastline (x = 0.78 lx) to 5 km
+    100 km away (node columns), same bathymetry/forcing families as the coastal workload with a new
+    seed, plus a Gaussian pressure-driven set-up of 2 m peak at the coast; SSP(3,3)."""
     lx, ly = 400_000.0, 300_000.0
     rng = np.random.default_rng(seed)
-
-    def density(px, py):
-        d = np.abs(px - 0.78 * lx) / lx  # distance to the coastline, normalised
-        return np.clip((0.02 / (0.02 + d)) ** 2, 4e-4, 1.0)
-
-    mesh = jittered_delaunay(lx, ly, n_tri, seed, density=density)
+    xs = graded_columns(lx, 0.78 * lx, 100.0, 5000.0, 100_000.0, n_tri, ly)
+    mesh = jittered_grid_mesh(lx, ly, n_tri, seed, xs=xs)
     x, y = mesh.xy[:, 0], mesh.xy[:, 1]
     hb = _coastal_bathymetry(x, y, lx, ly, 2.0, rng.uniform(0, 2 * np.pi))
     manning = rng.uniform(0.02, 0.06, mesh.n_tri)
@@ -343,14 +391,15 @@ def graded_c3(n_tri=2_000_000, seed=3, steps=1000) -> Workload:
     )
 
 
-def ensemble_c4(n_scen=64, lo=20_000, hi=400_000, seed=4, steps=500) -> list[Workload]:
+def ensemble_c4(n_scen=64, lo=20_000, hi=400_000, seed=4, steps=500, fast_mesh=True) -> list[Workload]:
     """Ensemble of coastal scenarios on seeded meshes with log-uniform sizes in [lo, hi]; each
-    has its own rain peak (10..80 mm/h), track heading, Manning field and tidal phase."""
+    has its own rain peak (10..80 mm/h), track heading, Manning field and tidal phase.  Meshes are
+    jittered grids (``fast_mesh``) or jittered-point Delaunay triangulations."""
     rng = np.random.default_rng(seed)
     sizes = np.exp(rng.uniform(np.log(lo), np.log(hi), n_scen)).astype(int)
     out = []
     for s, n in enumerate(sizes):
-        w = coastal_c2(int(n), seed=1000 * seed + s, steps=steps)
+        w = coastal_c2(int(n), seed=1000 * seed + s, steps=steps, fast_mesh=fast_mesh)
         w.storm.rpeak = rng.uniform(10.0, 80.0) * MMH
         w.storm.heading = rng.uniform(0.0, 2 * np.pi)
         w.tide.phase = np.array([rng.uniform(0, 2 * np.pi)])
@@ -366,7 +415,7 @@ def hurricane_c5(n_tri=8_000_000, seed=5, hours=24.0) -> Workload:
     0.3 once the solver has fixed dt (``steps`` is filled in by the caller)."""
     lx, ly = 1_500_000.0, 1_000_000.0
     rng = np.random.default_rng(seed)
-    mesh = jittered_delaunay(lx, ly, n_tri, seed)
+    mesh = jittered_grid_mesh(lx, ly, n_tri, seed)
     x, y = mesh.xy[:, 0], mesh.xy[:, 1]
     s = x / lx + 0.02 * np.sin(2 * np.pi * 2 * y / ly + rng.uniform(0, 2 * np.pi))
     hb = np.where(s < 0.4, 3000.0 - 2800.0 * 0.5 * (1 - np.cos(np.pi * np.clip(s / 0.4, 0, 1))),
