@@ -1,18 +1,22 @@
 #!/usr/bin/env python
 """Throughput of the DG rainfall shallow-water stepper on GB300.
 
-Workload: the coastal wet/dry configuration (seeded jittered Delaunay mesh of ~250k triangles on
-400 km x 300 km, p = 1, SSP(2,2), Roe flux, Manning friction, moving parametric rain, tide on the
-open boundary).  A step is one SSP-RK step of the whole mesh: every stage runs the fused kernel
-(edge fluxes, area integrals, sources, stage combination, positive-depth operator, ledger).
+Default workload: the coastal wet/dry configuration (seeded jittered Delaunay mesh of ~250k
+triangles on 400 km x 300 km, p = 1, SSP(2,2), Roe flux, Manning friction, moving parametric rain,
+tide on the open boundary).  A step is one SSP-RK step of the whole mesh: every stage runs the
+stage kernel (edge fluxes, area integrals, sources, stage combination, positive-depth operator,
+ledger).  ``--workload graded`` (2M triangles, p = 2, SSP(3,3), pressure set-up) and
+``--workload hurricane`` (8M triangles, hourly gridded rain) measure the same way.
 
-    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--workload W]
 
 Metric: DOF-updates per second (3 (p+1)(p+2)/2 DOF per triangle, one update per step), FP32-mixed
 path; the FP64 path is timed on the same workload and reported beside it.  L2 is flushed (a
-256 MiB write) between timed steps, outside the events that time them.  With N > 1 (torchrun) each
-rank runs an independent replica (the mesh is not sharded): value = all ranks' DOF-updates / the
-slowest rank's time.  Prints one JSON line on rank 0.
+256 MiB write) between timed steps, outside the events that time them.  On the coastal workload the
+line also carries the batched ensemble (64 scenarios of 20k-400k triangles): scenario-steps/s,
+against the same scenarios run one by one on the FP64 path.  With N > 1 (torchrun) each rank runs
+an independent replica (the mesh is not sharded; ensemble scenarios are dealt to ranks): value =
+all ranks' DOF-updates / the slowest rank's time.  Prints one JSON line on rank 0.
 """
 from __future__ import annotations
 
@@ -36,14 +40,20 @@ REASONS = ["sw_power_cap", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slo
 def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=0, help="0: the workload's default (2000, 1000, 2000)")
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--n-tri", type=int, default=250_000)
+    ap.add_argument("--workload", choices=["coastal", "graded", "hurricane"], default="coastal",
+                    help="coastal 250k p=1 (default); graded 2M p=2; hurricane 8M p=1")
+    ap.add_argument("--n-tri", type=int, default=0, help="0: the workload's own size")
+    ap.add_argument("--subsample-steps", type=int, default=1000, help="graded: steps of the 20k oracle comparison")
     ap.add_argument("--fp64-steps", type=int, default=0, help="0: max(10, steps // 100)")
     ap.add_argument("--e2e-steps", type=int, default=0, help="0: min(steps, 40)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ens-scenarios", type=int, default=64, help="ensemble size (0: no ensemble measurement)")
+    ap.add_argument("--ens-steps", type=int, default=500)
+    ap.add_argument("--ens-fp64-steps", type=int, default=10, help="FP64 steps timed per scenario")
     return ap.parse_args(argv)
 
 
@@ -139,10 +149,11 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------ roofline ----
-def stage_bytes_per_element(precision: str, p: int, rain_from_nodes: bool, nodes_per_elem: float):
+def stage_bytes_per_element(precision: str, p: int, rain_from_nodes: bool, nodes_per_elem: float,
+                            pressure: bool = False):
     """Algorithmic DRAM bytes one stage launch moves per element: own record in and out, static
-    geometry and connectivity, the step-initial record on stages > 0, rain node data.  Neighbour
-    records are L2 hits (Hilbert-ordered mesh) and are not counted."""
+    geometry and connectivity, the step-initial record on stages > 0, node data (rain, pressure
+    set-up).  Neighbour records are L2 hits (Hilbert-ordered mesh) and are not counted."""
     np_ = (p + 1) * (p + 2) // 2
     if precision == "mixed":
         rec = 16 * (4 if 3 * np_ + 7 <= 16 else 8)
@@ -152,7 +163,7 @@ def stage_bytes_per_element(precision: str, p: int, rain_from_nodes: bool, nodes
         rec = 16 * (8 if 3 * np_ + 4 <= 16 else 12)
         static = 16 + 80
         xy = 16
-    rain = (16 + xy * nodes_per_elem) if rain_from_nodes else 0.0
+    rain = (16 + xy * nodes_per_elem) if (rain_from_nodes or pressure) else 0.0
     first = rec + static + rain + rec
     later = first + rec
     return first, later
@@ -185,18 +196,27 @@ def time_oracle(w, budget_s: float, steps: int | None = None):
 
 def reference_arm(args, ws, rank):
     """--impl reference: the oracle timed on the host cores, K steps after W, each step one SSP
-    step of a same-family coastal mesh sized so the whole run stays within a few minutes."""
+    step of a mesh of the same workload family sized so the whole run stays within a few
+    minutes."""
     if rank != 0:
         return
     from paper_2307_14302_gb300 import workloads as W
 
+    def family(n):
+        if args.workload == "coastal":
+            return W.coastal_c2(n_tri=n, seed=2)
+        if args.workload == "graded":
+            return W.graded_c3(n_tri=n)
+        return W.hurricane_c5(n_tri=n)
+
+    full = args.n_tri or {"coastal": 250_000, "graded": 2_000_000, "hurricane": 8_000_000}[args.workload]
     # element-step rate of the oracle, from a small calibration mesh
-    cal = W.coastal_c2(n_tri=4000, seed=2)
+    cal = family(4000)
     rate, _, _ = time_oracle(cal, 0.5)
     elem_rate = rate / (cal.dof / cal.mesh.n_tri)
     budget = 150.0
-    n_tri = int(max(2000, min(args.n_tri, budget * elem_rate / max(1, args.steps + args.warmup))))
-    w = W.coastal_c2(n_tri=n_tri, seed=2)
+    n_tri = int(max(2000, min(full, budget * elem_rate / max(1, args.steps + args.warmup))))
+    w = family(n_tri)
     import oracle as O
 
     o = O.from_workload(w)
@@ -205,14 +225,15 @@ def reference_arm(args, ws, rank):
     o.step(args.steps)
     dt = time.perf_counter() - t0
     value = w.dof * args.steps / dt
-    sample = (f"{args.steps} SSP(2,2) steps of the coastal family at {w.mesh.n_tri} triangles "
-              f"(the {args.n_tri}-triangle workload scaled to fit the run budget)")
+    ssp = "SSP(2,2)" if w.p == 1 else "SSP(3,3)"
+    sample = (f"{args.steps} {ssp} steps of the {args.workload} family at {w.mesh.n_tri} triangles "
+              f"(the {full}-triangle workload scaled to fit the run budget)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"coastal-{args.n_tri // 1000}k-p1", "elements_timed": w.mesh.n_tri, "p": 1,
-                   "ssp": "SSP(2,2)", "flux": "Roe", "impl": "FP64 CPU oracle, single thread"},
+        "config": {"workload": f"{args.workload}-{full // 1000}k-p{w.p}", "elements_timed": w.mesh.n_tri, "p": w.p,
+                   "ssp": ssp, "flux": "Roe", "impl": "FP64 CPU oracle, single thread"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -220,12 +241,30 @@ def reference_arm(args, ws, rank):
 
 
 # -------------------------------------------------------------------------------- ours ----
+WORKLOADS = {
+    # name: (generator, default timed steps, ncu summary of its stage kernel)
+    "coastal": ("coastal_c2", 2000, "stage_kernel_mixed_p1_coastal.md"),
+    "graded": ("graded_c3", 1000, "stage_kernel_mixed_p2_graded.md"),
+    "hurricane": ("hurricane_c5", 2000, "stage_kernel_mixed_p1_hurricane.md"),
+}
+
+
+def make_workload(args):
+    from paper_2307_14302_gb300 import workloads as W
+
+    gen = getattr(W, WORKLOADS[args.workload][0])
+    if args.workload == "coastal":
+        return gen(n_tri=args.n_tri, seed=2, steps=args.steps)
+    if args.workload == "graded":
+        return gen(n_tri=args.n_tri or 2_000_000, steps=args.steps)
+    return gen(n_tri=args.n_tri or 8_000_000)
+
+
 def our_arm(args, ws, rank, local):
     import numpy as np
     import torch
 
     from paper_2307_14302_gb300 import dgswe as D
-    from paper_2307_14302_gb300 import workloads as W
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -233,8 +272,11 @@ def our_arm(args, ws, rank, local):
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
     assert stream.cuda_stream != 0
-    w = W.coastal_c2(n_tri=args.n_tri, seed=2, steps=args.steps)
+    w = make_workload(args)
     E = w.mesh.n_tri
+    p = w.p
+    np_ = (p + 1) * (p + 2) // 2
+    stages = 2 if p == 1 else 3
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     torch.cuda.synchronize(dev)
 
@@ -268,18 +310,17 @@ def our_arm(args, ws, rank, local):
 
     # roofline of the stage kernel: algorithmic bytes per launch / average launch duration
     nodes_per_elem = w.mesh.n_nodes / E
-    b0, b1 = stage_bytes_per_element("mixed", 1, True, nodes_per_elem)
-    bytes_per_launch = E * (b0 + b1) / 2
-    stages = 2
+    rain_nodes = w.storm is not None or w.rain_grid is not None
+    b0, b1 = stage_bytes_per_element("mixed", p, rain_nodes, nodes_per_elem, w.pressure is not None)
+    bytes_per_launch = E * (b0 + (stages - 1) * b1) / stages
     launch_s = t_mixed / (args.steps * stages)
     peak, peak_kind = load_peaks()
     achieved = bytes_per_launch / launch_s / 1e9
-    traffic = profiled_traffic(E)
+    traffic = profiled_traffic(WORKLOADS[args.workload][2], E)
 
     # ---- end to end through the public API: state in from pinned host memory, one step,
     # state back to pinned host memory, every step
-    k_e2e = args.e2e_steps or min(args.steps, 40)
-    np_ = 3
+    k_e2e = args.e2e_steps or min(args.steps, 40 if E < 1_000_000 else 10)
     zi, xi, yi = (torch.empty((np_, E), dtype=torch.float64).pin_memory().numpy() for _ in range(3))
     zo, xo, yo = (torch.empty((np_, E), dtype=torch.float64).pin_memory().numpy() for _ in range(3))
     s.state_arrays(zi, xi, yi)
@@ -294,6 +335,7 @@ def our_arm(args, ws, rank, local):
     e2e = {"value": units_e / t_e, "unit": UNIT, "h2d_bytes_per_step": int(zi.nbytes * 3),
            "d2h_bytes_per_step": int(zo.nbytes * 3), "steps": k_e2e}
     s.close()
+    del zi, xi, yi, zo, xo, yo
 
     # ---- FP64 path on the same workload
     k64 = args.fp64_steps or max(10, args.steps // 100)
@@ -306,25 +348,33 @@ def our_arm(args, ws, rank, local):
             "mixed_speedup": value / (units64 / t64m)}
     s64.close()
 
+    ensemble = None
+    if args.workload == "coastal" and args.ens_scenarios > 0:
+        ensemble = ensemble_measure(args, ws, rank, dev, stream, flush)
+    subsample = None
+    if args.workload == "graded" and rank == 0 and args.subsample_steps > 0:
+        subsample = graded_subsample_error(args, stream)
+
+    ssp = "SSP(2,2)" if stages == 2 else "SSP(3,3)"
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         v, n, secs = time_oracle(w, args.cpu_seconds)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{n} SSP(2,2) steps of the same {E}-triangle workload, FP64, one thread ({secs:.1f} s)"}
+               "sample": f"{n} {ssp} steps of the same {E}-triangle workload, FP64, one thread ({secs:.1f} s)"}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": w.name, "elements": E, "nodes": w.mesh.n_nodes, "p": 1, "dof": w.dof,
-                       "ssp": "SSP(2,2)", "flux": "Roe", "precision": "FP32 bulk, float-float means, FP64 depth test",
+            "config": {"workload": w.name, "elements": E, "nodes": w.mesh.n_nodes, "p": p, "dof": w.dof,
+                       "ssp": ssp, "flux": "Roe", "precision": "FP32 bulk, float-float means, FP64 depth test",
                        "l2": "flushed (256 MiB write) between timed steps", "parallelism": f"replicas x{ws}",
                        "launch": {"block": block, "waves": waves, "split": split}, "dt_s": s_dt(led),
-                       "mass_balance_rel_err": led["rel_err"]},
+                       "simulated_s": led["t"], "mass_balance_rel_err": led["rel_err"]},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "peak_source": peak_kind, "kernel": "stage_kernel<1,Roe,Mixed>",
+                         "peak_source": peak_kind, "kernel": f"stage_kernel<{p},Roe,Mixed>",
                          "bytes_per_launch": bytes_per_launch, "avg_launch_us": 1e6 * launch_s},
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -332,20 +382,145 @@ def our_arm(args, ws, rank, local):
             "clocks": clocks,
             "fp64": fp64,
         }
+        if ensemble is not None:
+            line["ensemble"] = ensemble
+        if subsample is not None:
+            line["subsample_vs_oracle"] = subsample
         print(json.dumps(line), flush=True)
+
+
+def graded_subsample_error(args, stream):
+    """Mixed path against the FP64 oracle on the graded family's 20k-triangle subsample."""
+    import numpy as np
+
+    import oracle as O
+    from paper_2307_14302_gb300 import dgswe as D
+    from paper_2307_14302_gb300 import workloads as W
+
+    w = W.graded_c3(n_tri=20_000, steps=args.subsample_steps)
+    ref = O.from_workload(w)
+    dt = ref.cfl_dt(w.cfl)
+    ref.set_dt(dt)
+    dev = D.from_workload(w, precision=D.MIXED, dt=dt, stream=stream.cuda_stream)
+    dev.step(args.subsample_steps)
+    dev.sync()
+    ref.step(args.subsample_steps)
+    got, want = dev.state(), ref.state()
+    led = dev.ledger()
+    out = {"elements": w.mesh.n_tri, "steps": args.subsample_steps,
+           "max_abs_err_zeta_m": float(np.abs(got[:, 0] - want[:, 0]).max()),
+           "max_abs_err_q_m2s": float(np.abs(got[:, 1:] - want[:, 1:]).max()),
+           "mass_balance_rel_err": led["rel_err"]}
+    dev.close()
+    return out
+
+
+def deal_scenarios(sizes, ws):
+    """Owner rank of each scenario: largest first, each to the least-loaded rank (ties: lowest)."""
+    load = [0] * ws
+    owner = [0] * len(sizes)
+    for i in sorted(range(len(sizes)), key=lambda i: (-sizes[i], i)):
+        r = min(range(ws), key=lambda k: (load[k], k))
+        load[r] += sizes[i]
+        owner[i] = r
+    return owner
+
+
+def ensemble_measure(args, ws, rank, dev, stream, flush):
+    """Batched ensemble: scenarios of the coastal family on meshes of log-uniform size in
+    [20k, 400k] triangles, each with its own rain peak, track heading, Manning field and tidal
+    phase, advanced together (one launch per stage over all scenarios, steps replayed from CUDA
+    graphs).  Beside it: the same scenarios run one after another, FP32-mixed and plain FP64.
+    Scenarios are dealt to ranks largest-first (each rank's own ensemble); the totals are the
+    whole job's."""
+    import numpy as np
+    import torch
+
+    from paper_2307_14302_gb300 import dgswe as D
+    from paper_2307_14302_gb300 import workloads as W
+
+    t_gen = time.perf_counter()
+    all_w = W.ensemble_c4(n_scen=args.ens_scenarios, steps=args.ens_steps)
+    t_gen = time.perf_counter() - t_gen
+    owner = deal_scenarios([x.mesh.n_tri for x in all_w], ws)
+    mine = [x for x, r in zip(all_w, owner) if r == rank]
+    k = args.ens_steps
+
+    def timed(fn):
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / 1e3
+
+    # members (mixed, fixed launch shape: no per-member autotuning); each also timed solo
+    members, solo = [], 0.0
+    k_solo = 20
+    for w in mine:
+        m = D.from_workload(w, precision=D.MIXED, stream=stream.cuda_stream, block=64, waves=1, split=0)
+        m.step(3)
+        flush.zero_()
+        solo += timed(lambda: m.step(k_solo)) * k / k_solo
+        members.append(m)
+    ens = D.Ensemble(members, device=dev.index, stream=stream.cuda_stream)
+    for m in members:
+        m.close()
+    ens.step(3)
+    ens.sync()
+    barrier(ws)
+    flush.zero_()
+    t_ens = timed(lambda: ens.step(k))
+    barrier(ws)
+    ens.sync()
+    rel = max(abs(ens.ledger(i)["rel_err"]) for i in range(len(mine)))
+    block, waves, split = ens.launch()
+    ens.close()
+
+    # the same scenarios as sequential plain FP64 GPU runs (k64 steps timed each, scaled to k)
+    seq64 = 0.0
+    for w in mine:
+        s64 = D.from_workload(w, precision=D.FP64, stream=stream.cuda_stream, block=128, waves=1, split=1)
+        s64.step(2)
+        flush.zero_()
+        seq64 += timed(lambda: s64.step(args.ens_fp64_steps)) * k / args.ens_fp64_steps
+        s64.close()
+
+    dof = sum(w.dof for w in mine)
+    n_tri = sum(w.mesh.n_tri for w in mine)
+    units, t_max = whole_job(len(mine) * k, t_ens, ws, dev)
+    dof_units, _ = whole_job(dof * k, t_ens, ws, dev)
+    _, t_solo = whole_job(0.0, solo, ws, dev)
+    _, t_seq64 = whole_job(0.0, seq64, ws, dev)
+    n_all = len(all_w)
+    return {
+        "metric": "ensemble scenario-steps/s", "value": units / t_max, "unit": "scenario-steps/s",
+        "dof_updates_per_s": dof_units / t_max, "steps": k, "scenarios": n_all,
+        "elements_total": int(sum(w.mesh.n_tri for w in all_w)), "elements_rank0": n_tri,
+        "ms_per_step": 1e3 * t_max / k,
+        "sequential_mixed": {"value": n_all * k / t_solo, "unit": "scenario-steps/s",
+                             "note": f"each scenario alone, {k_solo} steps timed, scaled to {k}"},
+        "sequential_fp64": {"value": n_all * k / t_seq64, "unit": "scenario-steps/s",
+                            "note": f"each scenario alone on the FP64 path, {args.ens_fp64_steps} steps timed, scaled to {k}"},
+        "speedup_vs_sequential_fp64": t_seq64 / t_max,
+        "launch": {"block": block, "waves": waves, "split": split},
+        "mass_balance_rel_err_max": rel, "mesh_generation_s": t_gen,
+        "l2": "inputs larger than L2 (ensemble state and geometry > 1 GB)",
+    }
 
 
 def s_dt(led):
     return led["t"] / max(1, led["steps"])
 
 
-def profiled_traffic(n_elem):
-    """DRAM bytes per stage launch from the committed ncu summary (dram__bytes_read.sum +
+def profiled_traffic(summary, n_elem):
+    """DRAM bytes per stage launch from a committed ncu summary (dram__bytes_read.sum +
     dram__bytes_write.sum of one capture, scaled to n_elem), or None when the summary is missing
     or was taken on a different kernel source."""
     import re
 
-    path = os.path.join(ROOT, "profiles", "stage_kernel_mixed_p1_coastal.md")
+    path = os.path.join(ROOT, "profiles", summary)
     if not os.path.exists(path):
         return None
     txt = open(path).read()
@@ -367,6 +542,10 @@ def kernel_hash():
 
 def main(argv=None):
     args = parse_args(argv)
+    if args.steps <= 0:
+        args.steps = WORKLOADS[args.workload][1]
+    if args.workload == "coastal" and args.n_tri <= 0 and args.impl == "ours":
+        args.n_tri = 250_000
     ws, rank, local = dist_init()
     if args.impl == "reference":
         reference_arm(args, ws, rank)

@@ -305,8 +305,13 @@ class Ensemble:
         _check(lib().dgswe_ensemble_get_ledger(self.h, i, C.byref(led)))
         return led.as_dict()
 
-    def set_launch(self, block, waves=1):
-        _check(lib().dgswe_set_launch(self.h, block, waves))
+    def set_launch(self, block, waves=1, split=1):
+        _check(lib().dgswe_set_launch(self.h, block, waves, split))
+
+    def launch(self):
+        b, w, s = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(lib().dgswe_get_launch(self.h, C.byref(b), C.byref(w), C.byref(s)))
+        return b.value, w.value, s.value
 
     def launch_count(self) -> int:
         return int(lib().dgswe_launch_count(self.h))

@@ -255,16 +255,72 @@ def jittered_grid_mesh(lx, ly, n_tri_target, seed, jitter=0.25, ocean_side="x0",
     return Mesh(np.ascontiguousarray(xy), tri, bedge, btype, bseg)
 
 
-def graded_columns(lx, x_coast, hmin, hmax, width, n_tri_target, ly):
-    """Node columns whose spacing grows from hmin at x_coast to hmax at distance >= width, with
-    the row count chosen so the mesh holds about n_tri_target triangles."""
-    xf = np.linspace(0.0, lx, 200_001)
-    hh = hmin + (hmax - hmin) * np.minimum(1.0, np.abs(xf - x_coast) / width) ** 2
+def _graded_h(x, x_coast, hmin, hmax, width):
+    return hmin + (hmax - hmin) * np.minimum(1.0, np.abs(x - x_coast) / width) ** 2
+
+
+def _graded_columns(lx, ly, x_coast, hmin, hmax, width):
+    """Column abscissae with spacing h(x) and the cell count of each column (ly / h)."""
+    xf = np.linspace(0.0, lx, 400_001)
+    hh = _graded_h(xf, x_coast, hmin, hmax, width)
     cells = np.concatenate([[0.0], np.cumsum(np.diff(xf) / (0.5 * (hh[1:] + hh[:-1])))])
     nx = max(int(round(cells[-1])), 2)
     xs = np.interp(np.linspace(0.0, cells[-1], nx + 1), cells, xf)
     xs[0], xs[-1] = 0.0, lx
-    return xs
+    ny = np.maximum(1, np.round(ly / _graded_h(xs, x_coast, hmin, hmax, width))).astype(np.int64)
+    return xs, ny
+
+
+def graded_strip_mesh(lx, ly, x_coast, hmin, hmax, n_tri_target, seed, jitter=0.2, ocean_side="x0") -> Mesh:
+    """Seeded mesh graded in x: node columns spaced by h(x) = hmin + (hmax - hmin) min(1,
+    |x - x_coast| / width)^2, each column holding ly / h(x) nodes, neighbouring columns joined by
+    merging their nodes in y order (a strip triangulation).  Element sizes are roughly isotropic
+    and follow h.  ``width`` is chosen by bisection so the mesh has about n_tri_target
+    triangles; interior nodes are jittered by up to ``jitter`` of the local spacing."""
+    rng = np.random.default_rng(seed)
+    lo, hi = math.log(1e2), math.log(1e8)
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        _, ny = _graded_columns(lx, ly, x_coast, hmin, hmax, math.exp(mid))
+        if int(np.sum(ny[:-1] + ny[1:])) < n_tri_target:
+            lo = mid
+        else:
+            hi = mid
+    xs, ny = _graded_columns(lx, ly, x_coast, hmin, hmax, math.exp(hi))
+    ncol = len(xs)
+    gap = np.diff(xs)
+    xgap = np.minimum(np.r_[gap[0], gap], np.r_[gap, gap[-1]])
+    start = np.concatenate([[0], np.cumsum(ny + 1)])
+    xy = np.empty((int(start[-1]), 2))
+    for i in range(ncol):
+        n = int(ny[i])
+        y = np.linspace(0.0, ly, n + 1)
+        y[1:-1] += rng.uniform(-jitter, jitter, n - 1) * (ly / n)
+        x = np.full(n + 1, xs[i])
+        if 0 < i < ncol - 1:
+            x += rng.uniform(-jitter, jitter, n + 1) * xgap[i]
+        xy[start[i]:start[i + 1], 0] = x
+        xy[start[i]:start[i + 1], 1] = y
+    tris = []
+    for i in range(ncol - 1):
+        a0, na = int(start[i]), int(ny[i]) + 1
+        b0, nb = int(start[i + 1]), int(ny[i + 1]) + 1
+        ya, yb = xy[a0 + 1:a0 + na, 1], xy[b0 + 1:b0 + nb, 1]
+        # advance events in y order: moving up column A (kind 0) or column B (kind 1)
+        key = np.concatenate([ya, yb])
+        kind = np.concatenate([np.zeros(na - 1, np.int64), np.ones(nb - 1, np.int64)])
+        o = np.lexsort((kind, key))
+        kind = kind[o]
+        ia = np.cumsum(kind == 0) - (kind == 0)  # A index before the event
+        ib = np.cumsum(kind == 1) - (kind == 1)
+        t = np.where((kind == 0)[:, None],
+                     np.stack([a0 + ia, a0 + ia + 1, b0 + ib], 1),
+                     np.stack([a0 + ia, b0 + ib + 1, b0 + ib], 1))
+        tris.append(t)
+    tri = _ccw(xy, np.concatenate(tris).astype(np.int64))
+    bedge = _boundary_edges(tri)
+    btype, bseg = _tag_rect(xy, bedge, lx, ly, ocean_side)
+    return Mesh(np.ascontiguousarray(xy), tri, bedge, btype, bseg)
 
 
 def density_mean(density, lx, ly, n=64):
@@ -370,13 +426,14 @@ def coastal_c2(n_tri=250_000, seed=2, steps=2000, fast_mesh=False) -> Workload:
 
 
 def graded_c3(n_tri=2_000_000, seed=3, steps=1000) -> Workload:
-    """p=2 graded mesh: edge lengths graded from ~100 m at the coastline (x = 0.78 lx) to 5 km
-    100 km away (node columns), same bathymetry/forcing families as the coastal workload with a new
-    seed, plus a Gaussian pressure-driven set-up of 2 m peak at the coast; SSP(3,3)."""
+    """p=2 graded mesh: element sizes graded from 100 m at the coastline (x = 0.78 lx) to 5 km
+    offshore and inland (a strip mesh; smaller n_tri scale both sizes by sqrt(2M / n_tri), the
+    same generator at coarser sizing), same bathymetry/forcing families as the coastal workload
+    with a new seed, plus a Gaussian pressure-driven set-up of 2 m peak at the coast; SSP(3,3)."""
     lx, ly = 400_000.0, 300_000.0
     rng = np.random.default_rng(seed)
-    xs = graded_columns(lx, 0.78 * lx, 100.0, 5000.0, 100_000.0, n_tri, ly)
-    mesh = jittered_grid_mesh(lx, ly, n_tri, seed, xs=xs)
+    f = max(1.0, math.sqrt(2_000_000 / n_tri))
+    mesh = graded_strip_mesh(lx, ly, 0.78 * lx, 100.0 * f, 5000.0 * f, n_tri, seed)
     x, y = mesh.xy[:, 0], mesh.xy[:, 1]
     hb = _coastal_bathymetry(x, y, lx, ly, 2.0, rng.uniform(0, 2 * np.pi))
     manning = rng.uniform(0.02, 0.06, mesh.n_tri)

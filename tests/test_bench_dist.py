@@ -57,3 +57,16 @@ def test_reference_arm_other_ranks_exit_without_work(tmp_path):
     import bench
 
     assert bench.reference_arm(bench.parse_args(["--impl", "reference"]), 2, 1) is None
+
+
+def test_ensemble_scenarios_are_dealt_to_every_rank_once():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    sizes = [400, 20, 300, 250, 90, 90, 60, 10]
+    for ws in (1, 2, 3):
+        owner = bench.deal_scenarios(sizes, ws)
+        assert sorted(set(owner)) == list(range(ws))
+        loads = [sum(s for s, o in zip(sizes, owner) if o == r) for r in range(ws)]
+        assert max(loads) - min(loads) <= max(sizes)
+    assert bench.deal_scenarios(sizes, 1) == [0] * len(sizes)

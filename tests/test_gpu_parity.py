@@ -176,6 +176,61 @@ def test_coastal_full_size_short_run(prec):
     assert dev.ledger()["rel_err"] < 1e-12
 
 
+# ------------------------------------------------------------- graded p=2 (C3) ------
+@pytest.mark.parametrize("prec", [D.FP64, D.MIXED])
+def test_graded_p2_subsample_matches_oracle(prec):
+    """The graded p=2 family on its 20k-triangle subsample (same generator, coarser sizing),
+    SSP(3,3), pressure set-up, moving rain, tide: 100 steps, every element compared."""
+    w = W.graded_c3(n_tri=20_000, steps=100)
+    ref, dev = _pair(w, 100, prec)
+    got, want = dev.state(), ref.state()
+    if prec == D.FP64:
+        assert _fp64_err(got, want) <= FP64_TOL
+    else:
+        ez, eq = _mixed_err(got, want)
+        assert ez <= MIXED_TOL and eq <= MIXED_TOL, (ez, eq)
+    assert dev.ledger()["rel_err"] < 1e-12
+    assert 0 < dev.dry().sum() < w.mesh.n_tri
+
+
+@pytest.mark.slow
+def test_graded_full_size_two_steps():
+    """The 2M-triangle graded p=2 workload in the benchmark's launch configuration, mixed path,
+    two SSP(3,3) steps against the oracle on every element."""
+    w = W.graded_c3()
+    ref, dev = _pair(w, 2, D.MIXED)
+    ez, eq = _mixed_err(dev.state(), ref.state())
+    assert ez <= MIXED_TOL and eq <= MIXED_TOL, (ez, eq)
+    assert dev.ledger()["rel_err"] < 1e-12
+
+
+# ---------------------------------------------------------- hurricane basin (C5) ------
+@pytest.mark.parametrize("prec", [D.FP64, D.MIXED])
+def test_hurricane_family_small_matches_oracle(prec):
+    """The hurricane family (hourly gridded rain on the 0.1 degree grid, 30% dry land, tide) on
+    a 20k-triangle mesh of the same basin: 100 steps, every element compared."""
+    w = W.hurricane_c5(n_tri=20_000)
+    ref, dev = _pair(w, 100, prec)
+    got, want = dev.state(), ref.state()
+    if prec == D.FP64:
+        assert _fp64_err(got, want) <= FP64_TOL
+    else:
+        ez, eq = _mixed_err(got, want)
+        assert ez <= MIXED_TOL and eq <= MIXED_TOL, (ez, eq)
+    assert dev.ledger()["rel_err"] < 1e-12
+
+
+@pytest.mark.slow
+def test_hurricane_full_size_two_steps():
+    """The 8M-triangle hurricane workload, mixed path, benchmark launch configuration: two
+    steps against the oracle on every element."""
+    w = W.hurricane_c5()
+    ref, dev = _pair(w, 2, D.MIXED)
+    ez, eq = _mixed_err(dev.state(), ref.state())
+    assert ez <= MIXED_TOL and eq <= MIXED_TOL, (ez, eq)
+    assert dev.ledger()["rel_err"] < 1e-12
+
+
 # -------------------------------------------------------------------- forcing paths ------
 @pytest.mark.parametrize("prec", [D.FP64, D.MIXED])
 def test_gridded_rain_and_pressure_setup(prec):
@@ -263,17 +318,21 @@ def test_negative_mean_depth_is_reported_not_trapped():
 
 # --------------------------------------------------------------------------- ensemble ----
 @pytest.mark.parametrize("prec", [D.FP64, D.MIXED])
-def test_ensemble_members_match_solo_runs(prec):
+@pytest.mark.parametrize("split", [0, 1])
+def test_ensemble_members_match_solo_runs(prec, split):
+    """Batching does not change a bit: each member of an ensemble, run with the same kernels
+    (launch shape fixed on both sides), ends bit-identical to its solo run."""
     ws = W.ensemble_c4(n_scen=3, lo=1500, hi=6000, seed=8, steps=40)
     solos, members = [], []
     for w in ws:
-        s = D.from_workload(w, precision=prec)
+        s = D.from_workload(w, precision=prec, block=128, split=split)
         members.append(s)
-        solo = D.from_workload(w, precision=prec)
+        solo = D.from_workload(w, precision=prec, block=128, split=split)
         solo.step(40)
         solo.sync()
         solos.append((solo.state(), solo.ledger()))
     ens = D.Ensemble(members)
+    ens.set_launch(128, 1, split)
     ens.step(40)
     ens.sync()
     for i, (st, led) in enumerate(solos):
