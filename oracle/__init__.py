@@ -76,6 +76,8 @@ def lib():
                                   C.c_double, _d]
         L.orc_positivity_vertex.restype = C.c_int
         L.orc_positivity_vertex.argtypes = [C.c_double, _d, _d, _d, _d, _d, _d, _u8]
+        L.orc_positivity_modal.restype = C.c_int
+        L.orc_positivity_modal.argtypes = [C.c_int, C.c_double, _d, _d]
         L.orc_ssp_amplification.restype = C.c_double
         L.orc_ssp_amplification.argtypes = [C.c_int, C.c_double]
         _lib = L
@@ -251,6 +253,15 @@ def positivity_vertex(H, qx, qy, h0=0.01):
     c = lib().orc_positivity_vertex(h0, _p(_f64(H)), _p(Ho), _p(_f64(qx)), _p(_f64(qy)), _p(qxo), _p(qyo),
                                     _p(dry, _u8))
     return c, Ho, qxo, qyo, dry
+
+
+def positivity_modal(p, w, hbv, h0=0.01):
+    """M Pi_h on one element: w [3][Np] modal (zeta, qx, qy) -> (new modes, dry)."""
+    out = np.ascontiguousarray(np.array(w, dtype=np.float64).reshape(3, -1))
+    rc = lib().orc_positivity_modal(p, h0, _p(_f64(hbv)), _p(out))
+    if rc < 0:
+        raise ValueError("p must be 0, 1 or 2")
+    return out, bool(rc)
 
 
 def ssp_amplification(stages, z):

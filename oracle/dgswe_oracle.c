@@ -36,7 +36,10 @@
  *     when its updated depth is below H0 and all three are dry in case 2;  M Pi^f zeroes dry
  *     vertex momentum and spreads it evenly over the wet ones (all dry: momentum lost);
  *     the element mean is never touched, the linear part is rebuilt from vertex values;
- *     p=2 elements with a vertex below H0 are first truncated to their p=1 modes;
+ *     at p=2 the operator acts on the linear part (modes 0..2) and the quadratic modes are
+ *     scaled by theta = clamp((Hmin - H0) / H0, 0, 1), Hmin the smallest vertex depth of the
+ *     linear part: untouched when Hmin >= 2 H0, removed when Hmin <= H0, blended between, so
+ *     the result depends continuously on the state (no knife-edge switch at H0);
  *   - an element is dry when any vertex is dry; a dry element keeps receiving rain and edge
  *     inflow but its momentum right-hand side is zero; an edge whose total mass flux would
  *     leave a dry element is closed (each side sees a wall built from its own state);
@@ -760,60 +763,80 @@ int orc_positivity_vertex(double H0, const double* H, double* Ho, const double* 
   return cas;
 }
 
-/* rebuild modes 1..2 of variable v from three vertex values (the linear interpolant projected on
- * the orthonormal basis with the exact area rule); mode 0 is left as it is */
-static void set_linear_part(const orc_t* o, double* we, const double f[3]) {
+/* rebuild modes 1..2 of one variable from three vertex values (the linear interpolant projected
+ * on the orthonormal basis with the exact area rule); mode 0 is left as it is */
+static void set_linear_part(int p, double* we, const double f[3]) {
   double l[NQMAX][3], qw[NQMAX];
-  int nq = area_rule_bary(o->p < 1 ? 1 : o->p, l, qw);
-  for (int m = 1; m < 3 && m < o->np; ++m) {
+  int nq = area_rule_bary(p < 1 ? 1 : p, l, qw);
+  for (int m = 1; m < 3 && m < (p + 1) * (p + 2) / 2; ++m) {
     double s = 0.0;
     for (int q = 0; q < nq; ++q) {
       double r, ss, phi[NPMAX];
       bary_to_rs(l[q], &r, &ss);
-      orc_basis(o->p, r, ss, phi, NULL, NULL);
+      orc_basis(p, r, ss, phi, NULL, NULL);
       s += qw[q] * (l[q][0] * f[0] + l[q][1] * f[1] + l[q][2] * f[2]) * phi[m];
     }
     we[m] = s;
   }
 }
 
-static void positivity(orc_t* o, double* W) {
-  const int np = o->np;
-  for (int e = 0; e < o->ne; ++e) {
-    double* we = W + (size_t)e * 3 * np;
-    const int32_t* vt = o->tri + 3 * e;
-    double qx[3], qy[3], H[3];
-    for (int pass = 0; pass < 2; ++pass) {
-      for (int i = 0; i < 3; ++i) {
-        double s0 = 0, s1 = 0, s2 = 0;
-        for (int m = 0; m < np; ++m) {
-          s0 += we[m] * o->phv[i][m]; s1 += we[np + m] * o->phv[i][m]; s2 += we[2 * np + m] * o->phv[i][m];
-        }
-        qx[i] = s1; qy[i] = s2; H[i] = s0 + o->hb[vt[i]];
-      }
-      if (pass == 0 && o->p >= 2 && (H[0] < o->H0 || H[1] < o->H0 || H[2] < o->H0)) {
-        for (int v = 0; v < 3; ++v)
-          for (int m = 3; m < np; ++m) we[v * np + m] = 0.0; /* truncate to p = 1 */
-        continue;
-      }
-      break;
+/* M Pi_h on one element's modes we[3][np] (zeta, qx, qy) with nodal bathymetry hbv at its
+ * vertices and phv the basis at the vertices; returns 1 if the element is dry */
+static int element_positivity(int p, const double phv[3][NPMAX], double H0, const double hbv[3], double* we) {
+  const int np = (p + 1) * (p + 2) / 2;
+  const int nl = np < 3 ? np : 3; /* modes of the linear part */
+  double qx[3], qy[3], H[3];
+  for (int i = 0; i < 3; ++i) {
+    double s0 = 0, s1 = 0, s2 = 0;
+    for (int m = 0; m < nl; ++m) {
+      s0 += we[m] * phv[i][m]; s1 += we[np + m] * phv[i][m]; s2 += we[2 * np + m] * phv[i][m];
     }
-    double Ho[3], qxo[3], qyo[3];
-    uint8_t dv[3];
-    int cas = orc_positivity_vertex(o->H0, H, Ho, qx, qy, qxo, qyo, dv);
-    if (cas != 1 && np > 1) {
-      double zo[3] = {Ho[0] - o->hb[vt[0]], Ho[1] - o->hb[vt[1]], Ho[2] - o->hb[vt[2]]};
-      set_linear_part(o, we, zo);
-    }
-    int nd = dv[0] + dv[1] + dv[2];
-    if (nd == 3) {
-      for (int m = 0; m < np; ++m) we[np + m] = we[2 * np + m] = 0.0;
-    } else if (nd > 0 && np > 1) {
-      set_linear_part(o, we + np, qxo);
-      set_linear_part(o, we + 2 * np, qyo);
-    }
-    o->dry[e] = nd > 0;
+    qx[i] = s1; qy[i] = s2; H[i] = s0 + hbv[i];
   }
+  if (p >= 2) { /* quadratic modes blended out as the linear part's shallowest vertex nears H0 */
+    double hmin = H[0] < H[1] ? H[0] : H[1];
+    hmin = hmin < H[2] ? hmin : H[2];
+    double th = (hmin - H0) / H0;
+    th = th < 0.0 ? 0.0 : th;
+    if (th < 1.0)
+      for (int v = 0; v < 3; ++v)
+        for (int m = 3; m < np; ++m) we[v * np + m] *= th;
+  }
+  double Ho[3], qxo[3], qyo[3];
+  uint8_t dv[3];
+  int cas = orc_positivity_vertex(H0, H, Ho, qx, qy, qxo, qyo, dv);
+  if (cas != 1 && np > 1) {
+    double zo[3] = {Ho[0] - hbv[0], Ho[1] - hbv[1], Ho[2] - hbv[2]};
+    set_linear_part(p, we, zo);
+  }
+  int nd = dv[0] + dv[1] + dv[2];
+  if (nd == 3) {
+    for (int m = 0; m < np; ++m) we[np + m] = we[2 * np + m] = 0.0;
+  } else if (nd > 0 && np > 1) {
+    set_linear_part(p, we + np, qxo);
+    set_linear_part(p, we + 2 * np, qyo);
+  }
+  return nd > 0;
+}
+
+static void positivity(orc_t* o, double* W) {
+  for (int e = 0; e < o->ne; ++e) {
+    const int32_t* vt = o->tri + 3 * e;
+    const double hbv[3] = {o->hb[vt[0]], o->hb[vt[1]], o->hb[vt[2]]};
+    o->dry[e] = (uint8_t)element_positivity(o->p, (const double(*)[NPMAX])o->phv, o->H0, hbv, W + (size_t)e * 3 * o->np);
+  }
+}
+
+int orc_positivity_modal(int p, double H0, const double* hbv, double* w) {
+  if (p < 0 || p > 2) return -1;
+  double phv[3][NPMAX];
+  for (int i = 0; i < 3; ++i) {
+    double l[3] = {0, 0, 0}, r, s;
+    l[i] = 1.0;
+    bary_to_rs(l, &r, &s);
+    orc_basis(p, r, s, phv[i], NULL, NULL);
+  }
+  return element_positivity(p, (const double(*)[NPMAX])phv, H0, hbv, w);
 }
 
 /* ------------------------------------------------------------------- state and time --- */

@@ -57,6 +57,11 @@ void orc_numflux(int flux, double g, double H0, const double* wl, double hbl, co
                  double nx, double ny, double* f);
 int orc_positivity_vertex(double H0, const double* H, double* Hout, const double* qx, const double* qy, double* qxo,
                           double* qyo, uint8_t* dry);
+/* M Pi_h (Sec. 2.4) on one element: w[3][Np] modal zeta, qx, qy in/out, hbv nodal bathymetry
+ * at the three vertices; at p = 2 the quadratic modes are blended out continuously as the
+ * linear part's shallowest vertex depth falls from 2 H0 to H0.  Returns 1 if the element is
+ * dry, 0 if wet, -1 for p outside 0..2. */
+int orc_positivity_modal(int p, double H0, const double* hbv, double* w);
 double orc_ssp_amplification(int stages, double z);
 
 #ifdef __cplusplus

@@ -192,6 +192,91 @@ def test_positive_depth_operator_cases_and_invariants():
                 assert abs(qxo.sum() - qx.sum()) < 1e-13 and abs(qyo.sum() - qy.sum()) < 1e-13
 
 
+def _vertex_basis(p):
+    return np.array([O.basis(p, r, s)[0] for (r, s) in ((-1.0, -1.0), (1.0, -1.0), (-1.0, 1.0))])
+
+
+def _p2_element(rng, zeta_lin_vertices, quad_scale=0.02):
+    """p=2 modes whose linear part (modes 0..2) takes the given vertex values; random
+    quadratic modes and momentum."""
+    V = _vertex_basis(2)
+    w = np.zeros((3, 6))
+    w[0, :3] = np.linalg.solve(V[:, :3], zeta_lin_vertices)
+    w[0, 3:] = rng.uniform(-quad_scale, quad_scale, 3)
+    w[1:, :] = rng.normal(scale=0.01, size=(2, 6))
+    return w
+
+
+def test_p2_positivity_blends_quadratic_modes_continuously():
+    """At p=2 the operator acts on the linear part and scales the quadratic modes by
+    clamp((Hmin - H0)/H0, 0, 1), Hmin the linear part's smallest vertex depth."""
+    h0 = 0.01
+    V = _vertex_basis(2)
+    rng = np.random.default_rng(11)
+    hb = np.array([0.3, -0.2, 0.1])
+    for _ in range(200):
+        # well above the band: untouched, bit for bit
+        H = rng.uniform(2.0 * h0, 1.0, 3)
+        w = _p2_element(rng, H - hb)
+        out, dry = O.positivity_modal(2, w, hb, h0)
+        assert np.array_equal(out, w) and not dry
+        # inside the band: linear part untouched, quadratic modes scaled by theta
+        H = rng.uniform(1.0 * h0, 2.0 * h0, 3)
+        H[rng.integers(3)] = 1.5 * h0 if rng.uniform() < 0.5 else H.min()
+        theta = (H.min() - h0) / h0
+        w = _p2_element(rng, H - hb)
+        out, dry = O.positivity_modal(2, w, hb, h0)
+        assert np.allclose(out[:, :3], w[:, :3], rtol=0, atol=1e-15) and not dry
+        assert np.allclose(out[:, 3:], theta * w[:, 3:], rtol=0, atol=1e-13)  # theta from rounded vertex values
+        # below H0 at a vertex: quadratic modes removed, p=1 operator on the linear part
+        H = rng.uniform(-0.05, 0.2, 3)
+        H[rng.integers(3)] = rng.uniform(-0.05, h0 * 0.999)
+        w = _p2_element(rng, H - hb)
+        out, dry = O.positivity_modal(2, w, hb, h0)
+        assert not out[:, 3:].any()
+        assert abs(out[0, 0] - w[0, 0]) <= 1e-15                   # element mean kept
+        Hn = V[:, :3] @ out[0, :3] + hb
+        c, Ho, _, _, _ = O.positivity_vertex(H, V[:, :3] @ w[1, :3], V[:, :3] @ w[2, :3], h0)
+        assert np.allclose(Hn, Ho, rtol=0, atol=1e-14)
+        assert dry == (c == 2)
+
+
+def test_p2_positivity_has_no_jump_at_the_threshold():
+    """A state perturbed by 1e-9 m across the shallowest-vertex threshold H0 changes by
+    O(1e-7) of its quadratic modes, not by the modes themselves: rounding differences between
+    two arithmetic paths cannot flip the outcome."""
+    h0 = 0.01
+    rng = np.random.default_rng(12)
+    hb = np.array([1.0, 0.5, 0.2])
+    for _ in range(100):
+        H = rng.uniform(h0, 0.1, 3)
+        k = rng.integers(3)
+        H[k] = h0
+        outs = []
+        for eps in (-1e-9, 1e-9):
+            Hk = H.copy()
+            Hk[k] += eps
+            w = _p2_element(np.random.default_rng(5), Hk - hb)
+            outs.append(O.positivity_modal(2, w, hb, h0)[0])
+        assert np.abs(outs[0] - outs[1]).max() < 1e-8
+
+
+def test_p1_modal_operator_equals_vertex_operator():
+    h0 = 0.01
+    V = _vertex_basis(1)
+    rng = np.random.default_rng(13)
+    hb = np.array([0.05, -0.02, 0.0])
+    for _ in range(500):
+        H = rng.uniform(-0.05, 0.2, 3)
+        w = np.stack([np.linalg.solve(V, H - hb), np.linalg.solve(V, rng.normal(size=3)),
+                      np.linalg.solve(V, rng.normal(size=3))])
+        out, dry = O.positivity_modal(1, w, hb, h0)
+        c, Ho, qxo, qyo, dv = O.positivity_vertex(H, V @ w[1], V @ w[2], h0)
+        assert np.allclose(V @ out[0] + hb, Ho, atol=1e-14)
+        assert np.allclose(V @ out[1], qxo, atol=1e-13) and np.allclose(V @ out[2], qyo, atol=1e-13)
+        assert dry == bool(dv.any())
+
+
 # --------------------------------------------------------------------------- SSP-RK --
 def test_ssp_stability_polynomials_are_truncated_taylor_series():
     for z in np.linspace(-2.5, 0.5, 13):
