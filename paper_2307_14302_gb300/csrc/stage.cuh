@@ -435,27 +435,36 @@ __device__ __forceinline__ T pdev(T d, T H, T g) {
 
 // FP64 positive-depth operator on the linear part (Sec. 2.4).  zs/xs/ys are modes 1.. of
 // zeta/qx/qy (double, in place); zbar/xbar/ybar means; returns true if the element is dry.
+// At p = 2 the operator acts on the linear part and the quadratic modes are scaled by
+// clamp((Hmin - H0) / H0, 0, 1), Hmin the linear part's smallest vertex depth (continuous in
+// the state: untouched from 2 H0 up, removed at H0 and below).
 template <int P>
 __device__ bool positivity_fp64(double zbar, double& xbar, double& ybar, double* zs, double* xs, double* ys,
                                 const double hbv[3], double H0, const RefTab<double>& tb, bool& changed) {
   constexpr int NP = np_of(P), NS = NP - 1;
+  constexpr int NL = NS < 2 ? NS : 2;  // linear modes among zs
   double H[3];
   changed = false;
-  for (int pass = 0; pass < 2; ++pass) {
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      double z = zbar;
+  for (int i = 0; i < 3; ++i) {
+    double z = zbar;
 #pragma unroll
-      for (int m = 0; m < NS; ++m) z = fma(zs[m], tb.vphi[i][m + 1], z);
-      H[i] = z + hbv[i];
-    }
-    if (pass == 0 && P >= 2 && (H[0] < H0 || H[1] < H0 || H[2] < H0)) {
+    for (int m = 0; m < NL; ++m) z = fma(zs[m], tb.vphi[i][m + 1], z);
+    H[i] = z + hbv[i];
+  }
+  if (P >= 2) {
+    const double hmin = fmin(fmin(H[0], H[1]), H[2]);
+    double th = (hmin - H0) / H0;
+    th = th < 0.0 ? 0.0 : th;
+    if (th < 1.0) {
 #pragma unroll
-      for (int m = 2; m < NS; ++m) zs[m] = xs[m] = ys[m] = 0.0;  // truncate to p = 1
+      for (int m = 2; m < NS; ++m) {
+        zs[m] *= th;
+        xs[m] *= th;
+        ys[m] *= th;
+      }
       changed = true;
-      continue;
     }
-    break;
   }
   if (H[0] >= H0 && H[1] >= H0 && H[2] >= H0) return false;
   changed = true;
@@ -515,10 +524,12 @@ __device__ bool positivity_fp64(double zbar, double& xbar, double& ybar, double*
 }
 
 // positive-depth operator on a freshly combined element; sets E.Hb and the dry flag.
-// FP32 path: vertex depths are first bounded in FP32; an element clearly above H0 at every
-// vertex is case 1 (unchanged, wet), one whose mean depth is clearly below H0 with a vertex
-// clearly below H0 is case 2 (flat depth, dry, no momentum: the zeta slopes become minus the
-// bathymetry slopes).  Only elements near the threshold take the FP64 operator.
+// FP32 path: the linear part's vertex depths are first bounded in FP32; an element clearly
+// above H0 at every vertex is case 1 (unchanged, wet; at p = 2 its quadratic modes are scaled
+// by the continuous blend factor when the shallowest vertex is below 2 H0), one whose mean
+// depth is clearly below H0 with a vertex clearly below H0 is case 2 (flat depth, dry, no
+// momentum: the zeta slopes become minus the bathymetry slopes).  Only elements near the
+// threshold take the FP64 operator.
 template <int P, class Pol>
 __device__ __forceinline__ void apply_positivity(Elem<P, Pol>& E, const Geo<Pol>& G, long long e,
                                                  const StageArgs<Pol>& a, int* err) {
@@ -528,6 +539,7 @@ __device__ __forceinline__ void apply_positivity(Elem<P, Pol>& E, const Geo<Pol>
   const T H0 = a.H0;
   const typename Pol::Acc Hbar = acc_add(E.zb, G.hbm);
   const T Hb = acc_r(Hbar);
+  constexpr int NL = NS < 2 ? NS : 2;  // linear modes among zs
   bool need64 = true, dry = false;
   if (sizeof(T) == 4) {
     T hmin = T(3.0e38), bound = abs_r(Hb);
@@ -535,7 +547,7 @@ __device__ __forceinline__ void apply_positivity(Elem<P, Pol>& E, const Geo<Pol>
     for (int i = 0; i < 3; ++i) {
       T v = Hb, b = 0;
 #pragma unroll
-      for (int m = 0; m < NS; ++m) {
+      for (int m = 0; m < NL; ++m) {
         v = fma(E.zs[m], tab.vphi[i][m + 1], v);
         b += abs_r(E.zs[m] * tab.vphi[i][m + 1]);
       }
@@ -548,6 +560,15 @@ __device__ __forceinline__ void apply_positivity(Elem<P, Pol>& E, const Geo<Pol>
     const T tol = T(4.0e-6) * (abs_r(Hb) + bound);
     if (hmin - tol > H0) {
       need64 = false;  // case 1
+      if (P >= 2 && hmin < T(2) * H0) {  // quadratic modes blended out, continuous in hmin
+        const T th = (hmin - H0) * frcp(H0);
+#pragma unroll
+        for (int m = 2; m < NS; ++m) {
+          E.zs[m] *= th;
+          E.xs[m] *= th;
+          E.ys[m] *= th;
+        }
+      }
     } else if (Hb < H0 * T(0.99999) && hmin + tol < H0 && Hb >= T(0)) {
       need64 = false;  // case 2
       dry = true;

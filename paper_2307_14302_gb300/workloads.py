@@ -215,10 +215,10 @@ def jittered_delaunay(lx, ly, n_tri_target, seed, jitter=0.35, ocean_side="x0", 
     return Mesh(np.ascontiguousarray(xy), tri, bedge, btype, bseg)
 
 
-def jittered_grid_mesh(lx, ly, n_tri_target, seed, jitter=0.25, ocean_side="x0", xs=None) -> Mesh:
+def jittered_grid_mesh(lx, ly, n_tri_target, seed, jitter=0.2, ocean_side="x0", xs=None) -> Mesh:
     """Seeded jittered structured mesh: an (nx+1) x (ny+1) node lattice, interior nodes moved by up
     to ``jitter`` of the local spacing, boundary nodes moved along their side only, each cell split
-    along a random diagonal.  ``xs`` (optional, increasing from 0 to lx) fixes the node columns,
+    along its shorter diagonal.  ``xs`` (optional, increasing from 0 to lx) fixes the node columns,
     which grades the mesh in x.  Linear in the node count, so meshes of millions of triangles are
     drawn in seconds."""
     rng = np.random.default_rng(seed)
@@ -246,7 +246,11 @@ def jittered_grid_mesh(lx, ly, n_tri_target, seed, jitter=0.25, ocean_side="x0",
     ii, jj = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
     a = (jj * (nx + 1) + ii).ravel()
     b, c, d = a + 1, a + nx + 2, a + nx + 1
-    flip = rng.uniform(0, 1, a.size) < 0.5
+    # split each jittered cell along its shorter diagonal (the Delaunay choice for a convex
+    # quadrilateral with near-equal angles), which keeps slivers out of large meshes
+    dac = np.hypot(*(xy[a] - xy[c]).T)
+    dbd = np.hypot(*(xy[b] - xy[d]).T)
+    flip = dbd < dac
     t1 = np.where(flip[:, None], np.stack([a, b, d], 1), np.stack([a, b, c], 1))
     t2 = np.where(flip[:, None], np.stack([b, c, d], 1), np.stack([a, c, d], 1))
     tri = _ccw(xy, np.concatenate([t1, t2]))
