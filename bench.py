@@ -43,8 +43,9 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=0, help="0: the workload's default (2000, 1000, 2000)")
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["coastal", "graded", "hurricane"], default="coastal",
-                    help="coastal 250k p=1 (default); graded 2M p=2; hurricane 8M p=1")
+    ap.add_argument("--workload", choices=["coastal", "graded", "hurricane", "basin"], default="coastal",
+                    help="coastal 250k p=1 (default); graded 2M p=2; hurricane 8M p=1; basin 400 p=1 (launch-bound: "
+                         "CUDA graphs against direct launches)")
     ap.add_argument("--n-tri", type=int, default=0, help="0: the workload's own size")
     ap.add_argument("--subsample-steps", type=int, default=1000, help="graded: steps of the 20k oracle comparison")
     ap.add_argument("--fp64-steps", type=int, default=0, help="0: max(10, steps // 100)")
@@ -207,9 +208,12 @@ def reference_arm(args, ws, rank):
             return W.coastal_c2(n_tri=n, seed=2)
         if args.workload == "graded":
             return W.graded_c3(n_tri=n)
+        if args.workload == "basin":
+            return W.basin_c1()
         return W.hurricane_c5(n_tri=n)
 
-    full = args.n_tri or {"coastal": 250_000, "graded": 2_000_000, "hurricane": 8_000_000}[args.workload]
+    full = args.n_tri or {"coastal": 250_000, "graded": 2_000_000, "hurricane": 8_000_000,
+                          "basin": 400}[args.workload]
     # element-step rate of the oracle, from a small calibration mesh
     cal = family(4000)
     rate, _, _ = time_oracle(cal, 0.5)
@@ -243,6 +247,7 @@ def reference_arm(args, ws, rank):
 # -------------------------------------------------------------------------------- ours ----
 WORKLOADS = {
     # name: (generator, default timed steps, ncu summary of its stage kernel)
+    "basin": ("basin_c1", 2000, None),
     "coastal": ("coastal_c2", 2000, "stage_kernel_mixed_p1_coastal.md"),
     "graded": ("graded_c3", 1000, "stage_kernel_mixed_p2_graded.md"),
     "hurricane": ("hurricane_c5", 2000, "stage_kernel_mixed_p1_hurricane.md"),
@@ -257,7 +262,71 @@ def make_workload(args):
         return gen(n_tri=args.n_tri, seed=2, steps=args.steps)
     if args.workload == "graded":
         return gen(n_tri=args.n_tri or 2_000_000, steps=args.steps)
+    if args.workload == "basin":
+        return gen()
     return gen(n_tri=args.n_tri or 8_000_000)
+
+
+def basin_arm(args, ws, rank, local):
+    """The 400-triangle basin fits in L2 and is bound by launch latency: whole runs of K steps
+    timed with graph replay (the library default) and with every stage launched directly."""
+    import torch
+
+    from paper_2307_14302_gb300 import dgswe as D
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    w = make_workload(args)
+    out = {}
+    for mode in ("graphs", "direct"):
+        s = D.from_workload(w, precision=D.MIXED, stream=stream.cuda_stream)
+        s.set_graphs(mode == "graphs")
+        s.step(max(args.warmup, 3))
+        s.sync()
+        l0 = s.launch_count()
+        barrier(ws)
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            a.record(stream)
+            s.step(args.steps)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+        t = a.elapsed_time(b) / 1e3
+        barrier(ws)
+        units, tmax = whole_job(w.dof * args.steps, t, ws, dev)
+        out[mode] = {"value": units / tmax, "unit": UNIT, "ms_per_step": 1e3 * tmax / args.steps,
+                     "launches": s.launch_count() - l0, "clocks": clk.summary(), "launch": s.launch()}
+        led = s.ledger()
+        s.close()
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        v, n, secs = time_oracle(w, min(args.cpu_seconds, 5.0))
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{n} SSP(2,2) steps of the same 400-triangle basin, FP64, one thread ({secs:.1f} s)"}
+    if rank == 0:
+        g = out["graphs"]
+        block, waves, split = g["launch"]
+        line = {
+            "metric": METRIC, "value": g["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": g["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "elements": w.mesh.n_tri, "p": 1, "dof": w.dof, "ssp": "SSP(2,2)",
+                       "flux": "Roe", "l2": "whole problem L2-resident (launch-bound case, not flushed)",
+                       "parallelism": f"replicas x{ws}", "launch": {"block": block, "waves": waves, "split": split},
+                       "mass_balance_rel_err": led["rel_err"]},
+            "roofline": None,
+            "roofline_note": "launch-bound: 400 elements per launch, no HBM traffic to speak of",
+            "cpu_baseline": cpu,
+            "e2e": None,
+            "gpu_launches": g["launches"],
+            "clocks": g["clocks"],
+            "direct_launches": {k: out["direct"][k] for k in ("value", "unit", "ms_per_step", "launches")},
+            "graph_speedup": out["direct"]["ms_per_step"] / g["ms_per_step"],
+        }
+        print(json.dumps(line), flush=True)
 
 
 def our_arm(args, ws, rank, local):
@@ -316,7 +385,7 @@ def our_arm(args, ws, rank, local):
     launch_s = t_mixed / (args.steps * stages)
     peak, peak_kind = load_peaks()
     achieved = bytes_per_launch / launch_s / 1e9
-    traffic = profiled_traffic(WORKLOADS[args.workload][2], E)
+    traffic = profiled_traffic(WORKLOADS[args.workload][2], E) if WORKLOADS[args.workload][2] else None
 
     # ---- end to end through the public API: state in from pinned host memory, one step,
     # state back to pinned host memory, every step
@@ -549,6 +618,8 @@ def main(argv=None):
     ws, rank, local = dist_init()
     if args.impl == "reference":
         reference_arm(args, ws, rank)
+    elif args.workload == "basin":
+        basin_arm(args, ws, rank, local)
     else:
         our_arm(args, ws, rank, local)
     if ws > 1:

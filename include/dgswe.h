@@ -224,6 +224,12 @@ int dgswe_ensemble_get_ledger(dgswe_h ens, int32_t member, dgswe_ledger* out);
 int dgswe_set_launch(dgswe_h, int32_t block, int32_t waves, int32_t split);
 int dgswe_get_launch(dgswe_h, int32_t* block, int32_t* waves, int32_t* split);
 
+/* How dgswe_step enqueues its work: 1 (default) replays whole steps from CUDA graphs captured
+ * once (1-step and 8-step graphs); 0 launches every kernel of every stage directly on the
+ * stream.  Results are bit-identical; the direct form exists to measure what the graphs save
+ * on small, launch-bound meshes.  Returns DGSWE_EINVAL for other values. */
+int dgswe_set_graphs(dgswe_h, int32_t on);
+
 /* Number of kernel launches this context enqueued so far (all kinds). */
 int64_t dgswe_launch_count(dgswe_h);
 

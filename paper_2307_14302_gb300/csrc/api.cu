@@ -121,6 +121,7 @@ struct dgswe_ctx {
   // launch configuration
   int block = 128, waves = 1, split = 1;
   bool autotune = true;
+  bool graphs = true;  // replay steps from CUDA graphs (else direct launches)
   int grid = 0;
   cudaGraphExec_t g1 = nullptr, gK = nullptr;
   int K = 8;
@@ -921,12 +922,25 @@ int dgswe_step(dgswe_h h, int64_t n) {
   DeviceGuard dg_(h->device);
   if (h->autotune)
     if (int rc = autotune(h)) return rc;
+  if (!h->graphs) {  // every stage launched directly
+    for (int64_t i = 0; i < n; ++i)
+      for (size_t s = 0; s < h->stages.size(); ++s)
+        if (int rc = launch_stage_once(h, (int)s, 0, h->stream)) return rc;
+    return 0;
+  }
   if (!h->g1)
     if (int rc = build_graphs(h)) return rc;
   const long long per = (long long)h->stages.size() * launches_per_stage(h);
   for (int64_t i = 0; i < n / h->K; ++i) CU(cudaGraphLaunch(h->gK, h->stream));
   for (int64_t i = 0; i < n % h->K; ++i) CU(cudaGraphLaunch(h->g1, h->stream));
   h->launches += n * per;
+  return 0;
+}
+
+int dgswe_set_graphs(dgswe_h h, int32_t on) {
+  if (int rc = check_handle(h)) return rc;
+  if (on != 0 && on != 1) return fail(DGSWE_EINVAL, "graphs must be 0 or 1");
+  h->graphs = on != 0;
   return 0;
 }
 

@@ -902,6 +902,14 @@ __host__ __device__ constexpr int staging_bytes(int block) {
 #ifndef DG_STAGE_MIN_BLOCKS
 #define DG_STAGE_MIN_BLOCKS 1  // CTAs of 256 threads the element kernel must fit per SM (register budget)
 #endif
+#ifndef DG_AREA_UNROLL
+#define DG_AREA_UNROLL 1  // unroll factor of the area-quadrature loop
+#endif
+#ifndef DG_EDGE_UNROLL
+#define DG_EDGE_UNROLL 1  // unroll factor of the three-edge loop
+#endif
+constexpr int kAreaUnroll = DG_AREA_UNROLL;
+constexpr int kEdgeUnroll = DG_EDGE_UNROLL;
 
 template <int P, int FLUX, class Pol, bool SPLIT>
 __global__ void __launch_bounds__(256, DG_STAGE_MIN_BLOCKS) stage_kernel(const StageArgs<Pol> a) {
@@ -1009,8 +1017,10 @@ __global__ void __launch_bounds__(256, DG_STAGE_MIN_BLOCKS) stage_kernel(const S
     const T g2x = tab.qdr[0][2] * rx + tab.qds[0][2] * sx, g2y = tab.qdr[0][2] * ry + tab.qds[0][2] * sy;
     const T hbx = E.hb1 * g1x + E.hb2 * g2x, hby = E.hb1 * g1y + E.hb2 * g2y;  // constant grad(hb)
     const T cfm = (a.friction == 0) ? g * G.man * G.man : a.cf;
+    // vertex coordinates (rain at the nodes, pressure set-up), loaded before the area loop so
+    // their latency overlaps it
     T vx[3] = {0, 0, 0}, vy[3] = {0, 0, 0};
-    if (s_press) {
+    if (s_rain >= 2 || s_press) {
       vx[0] = a.node_xy[2 * (long long)nd.x]; vy[0] = a.node_xy[2 * (long long)nd.x + 1];
       vx[1] = a.node_xy[2 * (long long)nd.y]; vy[1] = a.node_xy[2 * (long long)nd.y + 1];
       vx[2] = a.node_xy[2 * (long long)nd.z]; vy[2] = a.node_xy[2 * (long long)nd.z + 1];
@@ -1021,7 +1031,7 @@ __global__ void __launch_bounds__(256, DG_STAGE_MIN_BLOCKS) stage_kernel(const S
     T SS[NP][2];                        // sum_q w_q phi_m s_(x,y)
 #pragma unroll
     for (int m = 0; m < NP; ++m) SS[m][0] = SS[m][1] = 0;
-#pragma unroll 1
+#pragma unroll kAreaUnroll
     for (int q = 0; q < NQ; ++q) {
       const Trace<T> tq = trace_at<P, Pol>(E, tab.qphi[q]);
       const T Hs = max_r(tq.H, H0);
@@ -1089,8 +1099,7 @@ __global__ void __launch_bounds__(256, DG_STAGE_MIN_BLOCKS) stage_kernel(const S
       T acc = 0;
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        const long long n = (i == 0) ? nd.x : (i == 1 ? nd.y : nd.z);
-        const T px = a.node_xy[2 * n], py = a.node_xy[2 * n + 1];
+        const T px = vx[i], py = vy[i];
         if (s_rain == 2) {
           const T dx = px - s_xc, dy = py - s_yc;
           const T r = fsqrt0(dx * dx + dy * dy);
@@ -1124,7 +1133,7 @@ __global__ void __launch_bounds__(256, DG_STAGE_MIN_BLOCKS) stage_kernel(const S
     // ---- edge integrals <Fhat.n, v>, from the staged neighbour records or edge slots
     cp_async_wait_all();
     Acc massout = acc_make<Acc>(0.f, 0.f, 0.0);  // edge mass outflow (volume per second)
-#pragma unroll 1
+#pragma unroll kEdgeUnroll
     for (int j = 0; j < 3; ++j) {
       const int code = (j == 0) ? nb.x : (j == 1 ? nb.y : nb.z);
       const T lnx = (j == 0) ? G.lnx[0] : (j == 1 ? G.lnx[1] : G.lnx[2]);

@@ -61,7 +61,7 @@ EXPORTS = [
     "dgswe_set_state", "dgswe_load_state", "dgswe_step", "dgswe_sync", "dgswe_get_dt", "dgswe_get_state", "dgswe_get_state_device",
     "dgswe_get_dry", "dgswe_get_ledger", "dgswe_volume", "dgswe_volume_sum_noalloc", "dgswe_ensemble_create", "dgswe_ensemble_step",
     "dgswe_ensemble_get_state", "dgswe_ensemble_get_ledger", "dgswe_set_launch", "dgswe_get_launch",
-    "dgswe_launch_count", "dgswe_destroy", "dgswe_last_error",
+    "dgswe_set_graphs", "dgswe_launch_count", "dgswe_destroy", "dgswe_last_error",
 ]
 
 _lib = None
@@ -110,6 +110,7 @@ def lib():
         "dgswe_set_launch": ([_h, C.c_int32, C.c_int32, C.c_int32], C.c_int),
         "dgswe_get_launch": ([_h, _i, _i, _i], C.c_int),
         "dgswe_launch_count": ([_h], C.c_int64),
+        "dgswe_set_graphs": ([_h, C.c_int32], C.c_int),
         "dgswe_destroy": ([_h], None),
         "dgswe_last_error": ([], C.c_char_p),
     }
@@ -259,6 +260,10 @@ class Solver:
     def launch_count(self) -> int:
         return int(lib().dgswe_launch_count(self.h))
 
+    def set_graphs(self, on: bool):
+        """Replay steps from CUDA graphs (default) or launch every stage directly."""
+        _check(lib().dgswe_set_graphs(self.h, 1 if on else 0))
+
 
 def volume_sum_noalloc(w0_ptr, area_ptr, n, out_ptr, stream=None):
     """dgswe_volume_sum_noalloc on caller-owned device pointers (allocates nothing)."""
@@ -315,6 +320,9 @@ class Ensemble:
 
     def launch_count(self) -> int:
         return int(lib().dgswe_launch_count(self.h))
+
+    def set_graphs(self, on: bool):
+        _check(lib().dgswe_set_graphs(self.h, 1 if on else 0))
 
 
 def from_workload(w, precision=MIXED, flux=FLUX_ROE, ssp_stages=None, dt=0.0, friction=MANNING, cf=0.0, device=0,
