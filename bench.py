@@ -52,6 +52,7 @@ def parse_args(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=0, help="0: min(steps, 40)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--launch", default="", help="block,waves,split of the stage kernels (default: autotuned)")
     ap.add_argument("--ens-scenarios", type=int, default=64, help="ensemble size (0: no ensemble measurement)")
     ap.add_argument("--ens-steps", type=int, default=500)
     ap.add_argument("--ens-fp64-steps", type=int, default=10, help="FP64 steps timed per scenario")
@@ -254,6 +255,14 @@ WORKLOADS = {
 }
 
 
+def fixed_launch(args):
+    """Solver keyword arguments for --launch block,waves,split (empty: autotune)."""
+    if not args.launch:
+        return {}
+    block, waves, split = (int(v) for v in args.launch.split(","))
+    return {"block": block, "waves": waves, "split": split}
+
+
 def make_workload(args):
     from paper_2307_14302_gb300 import workloads as W
 
@@ -360,7 +369,7 @@ def our_arm(args, ws, rank, local):
         return sum(a.elapsed_time(b) for a, b in evs) / 1e3
 
     # ---- FP32-mixed path (headline)
-    s = D.from_workload(w, precision=D.MIXED, stream=stream.cuda_stream)
+    s = D.from_workload(w, precision=D.MIXED, stream=stream.cuda_stream, **fixed_launch(args))
     s.step(max(args.warmup, 3))
     s.sync()
     launches0 = s.launch_count()

@@ -518,8 +518,6 @@ static StageArgs<Pol> make_args(dgswe_h h, int stage, int tune) {
   a.stage = stage;
   a.last = (stage == S - 1) ? 1 : 0;
   a.has_n = st.a_n != 0.0 ? 1 : 0;
-  auto pow2 = [](double c) { int ex; return c == 0.0 || std::frexp(c, &ex) == 0.5; };
-  a.pow2 = (pow2(st.a_n) && pow2(st.a_in)) ? 1 : 0;
   a.cst_f = (float)st.c;
   a.tune = tune;
   a.friction = h->prm.friction;

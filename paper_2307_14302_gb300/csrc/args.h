@@ -50,7 +50,6 @@ struct StageArgs {
   int classify_only;       // prepare pass: derive depth and dry flag, keep the state as given
   int friction;            // 0 Manning, 1 quadratic, 2 none
   int has_n;               // the stage combines with the step-initial state
-  int pow2;                // a_n and a_in are exact powers of two (or zero)
   float a_n_hi, a_n_lo, a_in_hi, a_in_lo;  // Shu-Osher coefficients as float-float
   double a_n, a_in;
   float cst_f;             // stage time as a fraction of dt

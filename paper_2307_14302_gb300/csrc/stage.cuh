@@ -25,6 +25,10 @@
 #include "args.h"
 #include "layout.h"
 
+#ifndef DG_ROE_FORM
+#define DG_ROE_FORM 0  // 1: FP32 Roe dissipation in the subcritical cancellation-free form
+#endif
+
 namespace dg {
 
 // ------------------------------------------------------------ float-float (FP32 pairs) ---
@@ -92,8 +96,6 @@ __device__ __forceinline__ void acc_set(ff& a, double v) {
   a.hi = (float)v;
   a.lo = (float)(v - (double)a.hi);
 }
-__device__ __forceinline__ double acc_scale2(double a, float, double c) { return a * c; }
-__device__ __forceinline__ ff acc_scale2(ff a, float c, double) { return {a.hi * c, a.lo * c}; }  // c = 2^k
 __device__ __forceinline__ double acc_neg(double a) { return -a; }
 __device__ __forceinline__ ff acc_neg(ff a) { return {-a.hi, -a.lo}; }
 template <class Acc>
@@ -140,14 +142,20 @@ __device__ __forceinline__ double fexp(double x) { return exp(x); }
 __device__ __forceinline__ float fsin(float x) { return __sinf(x); }
 __device__ __forceinline__ double fsin(double x) { return sin(x); }
 
-// tidal elevation: FP32 reduces the phase to [-1/2, 1/2] turns before the hardware sine
-__device__ __forceinline__ float tide_at(const ForcingT<float>& F, int k, float t) {
-  float u = fmaf(t, F.tide[k][1], F.tide[k][2]);
-  u -= rintf(u);
-  return F.tide[k][0] * __sinf(6.2831853f * u);
+// tidal elevation A sin(2 pi t / T + phi) of segment k at time t.  Mixed path: the phase is
+// formed and reduced to [-1/2, 1/2] turns in FP64 (ocean edges are few), the sine is the
+// accurate FP32 sinpi of the reduced phase; the FP64 path evaluates it in FP64.
+template <class T>
+__device__ __forceinline__ T tide_at(const ScenDev& S, int k, double t);
+template <>
+__device__ __forceinline__ float tide_at<float>(const ScenDev& S, int k, double t) {
+  const double u = fma(t, S.d.tide[k][1], S.d.tide[k][2]) * 0.15915494309189535;  // turns
+  const float r = (float)(u - rint(u));
+  return S.f.tide[k][0] * sinpif(2.0f * r);
 }
-__device__ __forceinline__ double tide_at(const ForcingT<double>& F, int k, double t) {
-  return F.tide[k][0] * sin(F.tide[k][1] * t + F.tide[k][2]);
+template <>
+__device__ __forceinline__ double tide_at<double>(const ScenDev& S, int k, double t) {
+  return S.d.tide[k][0] * sin(S.d.tide[k][1] * t + S.d.tide[k][2]);
 }
 
 template <class T>
@@ -416,6 +424,19 @@ __device__ __forceinline__ void edge_flux(const Trace<T>& L, const Trace<T>& R, 
   T utn = ut * nx + vt * ny, utt = vt * nx - ut * ny;
   T dqn = dqx * nx + dqy * ny, dqt = dqy * nx - dqx * ny;
   T w = (dqn - utn * dz) * ic;
+#if DG_ROE_FORM == 1
+  if (sizeof(T) == 4 && abs_r(utn) < c) {
+    // subcritical: with |utn - c| = c - utn and |utn + c| = c + utn the dissipation collapses to
+    // D0 = c dz + utn w, D1 = ut D0 + c nx dqn - l2 ny, D2 = vt D0 + c ny dqn + l2 nx, the same
+    // values without the c^2 dz intermediates that cancel in the eigen form
+    const T l2 = abs_r(utn) * (dqt - utt * dz);
+    const T D0 = c * dz + utn * w;
+    fz = cz - T(0.5) * D0;
+    fx = cx - T(0.5) * (ut * D0 + c * nx * dqn - l2 * ny);
+    fy = cy - T(0.5) * (vt * D0 + c * ny * dqn + l2 * nx);
+    return;
+  }
+#endif
   T a1 = T(0.5) * (dz - w), a3 = T(0.5) * (dz + w), a2 = dqt - utt * dz;
   T l1 = abs_r(utn - c) * a1, l2 = abs_r(utn) * a2, l3 = abs_r(utn + c) * a3;
   T D0 = l1 + l3;
@@ -938,37 +959,18 @@ __global__ void __launch_bounds__(256, DG_STAGE_MIN_BLOCKS) stage_kernel(const S
   const T g = a.g, H0 = a.H0;
   Acc rain_acc = acc_make<Acc>(0.f, 0.f, 0.0), bdry_acc = acc_make<Acc>(0.f, 0.f, 0.0);
   int cur = -1;
-  // constants of the current scenario, loaded once per warp when the scenario changes
-  long long s_end = 0;
-  int s_rain = 0, s_press = 0;
-  T t = 0, s_xc = 0, s_yc = 0, s_rp = 0, s_rm = 0, s_irm = 0, s_ire = 0;
-  Acc bdt = acc_make<Acc>(0.f, 0.f, 0.0);
-  const ScenDev* Sp = a.scen;
 
   for (long long tile = gw; tile < a.ntiles; tile += W) {
     const int sc = a.tile_scen[tile];
     if (sc != cur) {
       if (cur >= 0 && !a.tune) flush_ledger<P, Pol>(a, cur, gw, rain_acc, bdry_acc);
       cur = sc;
-      Sp = a.scen + sc;
-      const ForcingT<T>& F0 = forcing<T>(*Sp);
-      s_end = Sp->elem_end;
-      s_rain = Sp->rain_kind;
-      s_press = Sp->press;
-      t = F0.t0 + stepc * F0.dt;
-      const T tt = t - F0.storm[7];
-      s_xc = F0.storm[0] + F0.storm[2] * tt;  // storm centre at the stage time
-      s_yc = F0.storm[1] + F0.storm[3] * tt;
-      s_rp = F0.storm[4];
-      s_rm = F0.storm[5];
-      s_irm = s_rain == 2 ? frcp(F0.storm[5]) : T(0);
-      s_ire = s_rain == 2 ? frcp(F0.storm[6]) : T(0);
-      bdt = acc_make<Acc>(Sp->bdt_hi[a.stage], Sp->bdt_lo[a.stage], Sp->bdt[a.stage]);
     }
-    const ScenDev& S = *Sp;
+    const ScenDev& S = a.scen[sc];
     const ForcingT<T>& F = forcing<T>(S);
     const long long e = tile * TILE + lane;
-    if (e >= s_end) continue;
+    if (e >= S.elem_end) continue;
+    const T t = F.t0 + stepc * F.dt;
 
     const int4 nb = __ldg(a.nbr + e);
     // stage what the edge loop and the combination need, asynchronously
@@ -998,7 +1000,7 @@ __global__ void __launch_bounds__(256, DG_STAGE_MIN_BLOCKS) stage_kernel(const S
     load_raw<RV>(a.in, e, rme);
     Elem<P, Pol> E;
     unpack<P>(rme, E);
-    const int4 nd = (s_rain >= 2 || s_press) ? __ldg(a.nodes + e) : make_int4(0, 0, 0, 0);
+    const int4 nd = (S.rain_kind >= 2 || S.press) ? __ldg(a.nodes + e) : make_int4(0, 0, 0, 0);
     const bool dry_me = (E.flags & FLAG_DRY) != 0;
     const T detJ = T(0.5) * acc_r(G.A);
     const T idetJ = T(2) * acc_r(G.invA);
@@ -1017,10 +1019,8 @@ __global__ void __launch_bounds__(256, DG_STAGE_MIN_BLOCKS) stage_kernel(const S
     const T g2x = tab.qdr[0][2] * rx + tab.qds[0][2] * sx, g2y = tab.qdr[0][2] * ry + tab.qds[0][2] * sy;
     const T hbx = E.hb1 * g1x + E.hb2 * g2x, hby = E.hb1 * g1y + E.hb2 * g2y;  // constant grad(hb)
     const T cfm = (a.friction == 0) ? g * G.man * G.man : a.cf;
-    // vertex coordinates (rain at the nodes, pressure set-up), loaded before the area loop so
-    // their latency overlaps it
     T vx[3] = {0, 0, 0}, vy[3] = {0, 0, 0};
-    if (s_rain >= 2 || s_press) {
+    if (S.press) {
       vx[0] = a.node_xy[2 * (long long)nd.x]; vy[0] = a.node_xy[2 * (long long)nd.x + 1];
       vx[1] = a.node_xy[2 * (long long)nd.y]; vy[1] = a.node_xy[2 * (long long)nd.y + 1];
       vx[2] = a.node_xy[2 * (long long)nd.z]; vy[2] = a.node_xy[2 * (long long)nd.z + 1];
@@ -1042,7 +1042,7 @@ __global__ void __launch_bounds__(256, DG_STAGE_MIN_BLOCKS) stage_kernel(const S
       if (a.friction == 0) tau = cfm * fsqrt0(u * u + v * v) * fpowm43(Hs);
       else if (a.friction == 1) tau = cfm * fsqrt0(u * u + v * v) * iH;
       T Fxs = 0, Fys = 0;
-      if (s_press) {
+      if (S.press) {
         const T px = tab.ql[q][0] * vx[0] + tab.ql[q][1] * vx[1] + tab.ql[q][2] * vx[2];
         const T py = tab.ql[q][0] * vy[0] + tab.ql[q][1] * vy[1] + tab.ql[q][2] * vy[2];
         const T dx = px - F.ps[0], dy = py - F.ps[1], is2 = frcp(F.ps[2] * F.ps[2]);
@@ -1093,17 +1093,20 @@ __global__ void __launch_bounds__(256, DG_STAGE_MIN_BLOCKS) stage_kernel(const S
 
     // ---- forcing: element rain = mean of the three nodal rates (Eq. rain)
     T Re = 0;
-    if (s_rain == 1) {
+    if (S.rain_kind == 1) {
       Re = a.rain_e[e];
-    } else if (s_rain >= 2) {
+    } else if (S.rain_kind >= 2) {
       T acc = 0;
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        const T px = vx[i], py = vy[i];
-        if (s_rain == 2) {
-          const T dx = px - s_xc, dy = py - s_yc;
+        const long long n = (i == 0) ? nd.x : (i == 1 ? nd.y : nd.z);
+        const T px = a.node_xy[2 * n], py = a.node_xy[2 * n + 1];
+        if (S.rain_kind == 2) {
+          const T tt = t - F.storm[7];
+          const T dx = px - (F.storm[0] + F.storm[2] * tt), dy = py - (F.storm[1] + F.storm[3] * tt);
           const T r = fsqrt0(dx * dx + dy * dy);
-          acc += (r < s_rm) ? s_rp * (T(0.5) + T(0.5) * (r * s_irm)) : s_rp * fexp(-(r - s_rm) * s_ire);
+          const T rp = F.storm[4], rm = F.storm[5], re = F.storm[6];
+          acc += (r < rm) ? rp * (T(0.5) + T(0.5) * fdiv(r, rm)) : rp * fexp(-fdiv(r - rm, re));
         } else {
           T gx = (px - F.grid[0]) * F.grid[2], gy = (py - F.grid[1]) * F.grid[3];
           T gt = (t - F.grid[4]) * F.grid[5];
@@ -1179,7 +1182,8 @@ __global__ void __launch_bounds__(256, DG_STAGE_MIN_BLOCKS) stage_kernel(const S
         for (int k = 0; k < NG; ++k) to[k] = trace_at<P, Pol>(N, s_ephi[jn][NG - 1 - k]);  // same point
       } else if (code < -1) {  // ocean: tidal elevation, interior discharge
         const int seg = min(-2 - code, MAXSEG - 1);
-        const T zbc = tide_at(F, seg, t);
+        const double t64 = S.d.t0 + ((double)a.ctl->step + a.cst) * S.d.dt;  // stage time in FP64
+        const T zbc = tide_at<T>(S, seg, t64);
         const T dgh = acc_r(acc_addr(acc_neg(E.zb), zbc));  // ghost zeta - my mean
 #pragma unroll
         for (int k = 0; k < NG; ++k) {
@@ -1255,6 +1259,7 @@ __global__ void __launch_bounds__(256, DG_STAGE_MIN_BLOCKS) stage_kernel(const S
     // ---- Shu-Osher combination: out = a_n w^n + a_in w^in + beta dt M^{-1} R
     const Acc an = acc_make<Acc>(a.a_n_hi, a.a_n_lo, a.a_n);
     const Acc ain = acc_make<Acc>(a.a_in_hi, a.a_in_lo, a.a_in);
+    const Acc bdt = acc_make<Acc>(S.bdt_hi[a.stage], S.bdt_lo[a.stage], S.bdt[a.stage]);
     // mean rates: d(zeta_bar)/dt = R_e - massout / A;  d(q_bar)/dt = phi_0 R_0 / detJ
     const Acc zrate = acc_addr(acc_neg(acc_mul(massout, G.invA)), Re);
     const T xrate = tab.phi0 * Rx[0] * idetJ, yrate = tab.phi0 * Ry[0] * idetJ;
@@ -1267,14 +1272,11 @@ __global__ void __launch_bounds__(256, DG_STAGE_MIN_BLOCKS) stage_kernel(const S
       unpack<P>(rn, Wn);
     }
     {
-      // a.pow2: both weights are exact powers of two (SSP(2,2)), so scaling is exact per part
-      Acc z = a.pow2 ? acc_scale2(E.zb, a.a_in_hi, a.a_in) : acc_mul(ain, E.zb);
-      Acc x = a.pow2 ? acc_scale2(E.xb, a.a_in_hi, a.a_in) : acc_mul(ain, E.xb);
-      Acc y = a.pow2 ? acc_scale2(E.yb, a.a_in_hi, a.a_in) : acc_mul(ain, E.yb);
+      Acc z = acc_mul(ain, E.zb), x = acc_mul(ain, E.xb), y = acc_mul(ain, E.yb);
       if (a.has_n) {
-        z = acc_add(z, a.pow2 ? acc_scale2(Wn.zb, a.a_n_hi, a.a_n) : acc_mul(an, Wn.zb));
-        x = acc_add(x, a.pow2 ? acc_scale2(Wn.xb, a.a_n_hi, a.a_n) : acc_mul(an, Wn.xb));
-        y = acc_add(y, a.pow2 ? acc_scale2(Wn.yb, a.a_n_hi, a.a_n) : acc_mul(an, Wn.yb));
+        z = acc_add(z, acc_mul(an, Wn.zb));
+        x = acc_add(x, acc_mul(an, Wn.xb));
+        y = acc_add(y, acc_mul(an, Wn.yb));
       }
       O.zb = acc_add(z, acc_mul(bdt, zrate));
       O.xb = acc_addr(x, acc_r(bdt) * xrate);
