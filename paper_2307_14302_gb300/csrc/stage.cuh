@@ -25,8 +25,8 @@
 #include "args.h"
 #include "layout.h"
 
-#ifndef DG_ROE_FORM
-#define DG_ROE_FORM 0  // 1: FP32 Roe dissipation in the subcritical cancellation-free form
+#ifndef DG_OCEAN64
+#define DG_OCEAN64 0  // 1: mixed path evaluates ocean-boundary edges in FP64
 #endif
 
 namespace dg {
@@ -424,19 +424,6 @@ __device__ __forceinline__ void edge_flux(const Trace<T>& L, const Trace<T>& R, 
   T utn = ut * nx + vt * ny, utt = vt * nx - ut * ny;
   T dqn = dqx * nx + dqy * ny, dqt = dqy * nx - dqx * ny;
   T w = (dqn - utn * dz) * ic;
-#if DG_ROE_FORM == 1
-  if (sizeof(T) == 4 && abs_r(utn) < c) {
-    // subcritical: with |utn - c| = c - utn and |utn + c| = c + utn the dissipation collapses to
-    // D0 = c dz + utn w, D1 = ut D0 + c nx dqn - l2 ny, D2 = vt D0 + c ny dqn + l2 nx, the same
-    // values without the c^2 dz intermediates that cancel in the eigen form
-    const T l2 = abs_r(utn) * (dqt - utt * dz);
-    const T D0 = c * dz + utn * w;
-    fz = cz - T(0.5) * D0;
-    fx = cx - T(0.5) * (ut * D0 + c * nx * dqn - l2 * ny);
-    fy = cy - T(0.5) * (vt * D0 + c * ny * dqn + l2 * nx);
-    return;
-  }
-#endif
   T a1 = T(0.5) * (dz - w), a3 = T(0.5) * (dz + w), a2 = dqt - utt * dz;
   T l1 = abs_r(utn - c) * a1, l2 = abs_r(utn) * a2, l3 = abs_r(utn + c) * a3;
   T D0 = l1 + l3;
@@ -920,9 +907,6 @@ __host__ __device__ constexpr int staging_bytes(int block) {
   return 16 * Staging<P, Pol, SPLIT>::VEC * block;
 }
 
-#ifndef DG_STAGE_MIN_BLOCKS
-#define DG_STAGE_MIN_BLOCKS 1  // CTAs of 256 threads the element kernel must fit per SM (register budget)
-#endif
 #ifndef DG_AREA_UNROLL
 #define DG_AREA_UNROLL 1  // unroll factor of the area-quadrature loop
 #endif
@@ -933,7 +917,12 @@ constexpr int kAreaUnroll = DG_AREA_UNROLL;
 constexpr int kEdgeUnroll = DG_EDGE_UNROLL;
 
 template <int P, int FLUX, class Pol, bool SPLIT>
-__global__ void __launch_bounds__(256, DG_STAGE_MIN_BLOCKS) stage_kernel(const StageArgs<Pol> a) {
+#ifdef DG_MAXNREG
+#define DG_STAGE_BOUNDS __maxnreg__(DG_MAXNREG)
+#else
+#define DG_STAGE_BOUNDS __launch_bounds__(256)
+#endif
+__global__ void DG_STAGE_BOUNDS stage_kernel(const StageArgs<Pol> a) {
   using T = typename Pol::T;
   using Acc = typename Pol::Acc;
   using St = Staging<P, Pol, SPLIT>;
@@ -1194,6 +1183,36 @@ __global__ void __launch_bounds__(256, DG_STAGE_MIN_BLOCKS) stage_kernel(const S
       }
       T Fz[NG], Fx[NG], Fy[NG];  // flux along my outward normal at my points
       T emine = 0;              // mass flux integral along my outward normal
+#if DG_OCEAN64
+      if (sizeof(T) == 4 && code < -1) {  // ocean edge evaluated in FP64 from my FP32 trace
+        const int seg = min(-2 - code, MAXSEG - 1);
+        const double t64 = S.d.t0 + ((double)a.ctl->step + a.cst) * S.d.dt;
+        const double dgh = tide_at<double>(S, seg, t64) - acc_d(E.zb);
+        const double nxd = (double)lnx / (double)len, nyd = (double)lny / (double)len;
+        double fz[NG], fx[NG], fy[NG], pp[NG], ec = 0.0;
+#pragma unroll
+        for (int k = 0; k < NG; ++k) {
+          const Trace<double> L{(double)tm[k].d, (double)tm[k].H, (double)tm[k].qx, (double)tm[k].qy};
+          Trace<double> R = L;
+          R.H = L.H + (dgh - L.d);
+          R.d = dgh;
+          edge_flux<FLUX, double>(L, R, 0.0, nxd, nyd, (double)g, (double)H0, fz[k], fx[k], fy[k]);
+          pp[k] = 0.5 * (pdev(L.d, L.H, (double)g) + pdev(R.d, R.H, (double)g));
+          ec = fma((double)tab.gw[k], fz[k], ec);
+        }
+        ec *= 0.5 * (double)len;
+        wall = dry_me && ec > 0.0;
+        if (!wall) {
+          emine = (T)ec;
+#pragma unroll
+          for (int k = 0; k < NG; ++k) {
+            Fz[k] = (T)fz[k];
+            Fx[k] = (T)(fx[k] + pp[k] * nxd);
+            Fy[k] = (T)(fy[k] + pp[k] * nyd);
+          }
+        }
+      } else
+#endif
       if (!wall) {
         const T sgn = me_L ? T(1) : T(-1);
         T fzc[NG], fxc[NG], fyc[NG];
