@@ -50,6 +50,7 @@ def lib():
         L.orc_set_rain_parametric.argtypes = [C.c_void_p] + [C.c_double] * 8
         L.orc_set_rain_grid.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int] + [C.c_double] * 6 + [_f]
         L.orc_set_tide.argtypes = [C.c_void_p, C.c_int, _d, _d, _d]
+        L.orc_set_river.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_double, _d]
         L.orc_set_pressure.argtypes = [C.c_void_p] + [C.c_double] * 4
         L.orc_set_exact_wave.argtypes = [C.c_void_p] + [C.c_double] * 5
         L.orc_set_exact_linear.argtypes = [C.c_void_p, _d]
@@ -141,6 +142,10 @@ class Oracle:
     def set_tide(self, t):
         lib().orc_set_tide(self.h, len(t.amp), _p(_f64(t.amp)), _p(_f64(t.period)), _p(_f64(t.phase)))
 
+    def set_river(self, r):
+        q = np.ascontiguousarray(np.atleast_2d(np.asarray(r.q, dtype=np.float64)))
+        lib().orc_set_river(self.h, q.shape[1], q.shape[0], r.t0, r.dt, _p(q))
+
     def set_pressure(self, x0, y0, sigma, peak):
         lib().orc_set_pressure(self.h, x0, y0, sigma, peak)
 
@@ -216,6 +221,8 @@ def from_workload(w, flux=ROE, ssp=None, dt=None, friction=MANNING, cf=0.0) -> O
         o.set_tide(w.tide)
     if w.pressure is not None:
         o.set_pressure(*w.pressure)
+    if getattr(w, "river", None) is not None:
+        o.set_river(w.river)
     o.set_state_nodal(w.zeta0)
     o.set_dt(dt if dt is not None else o.cfl_dt(w.cfl))
     return o

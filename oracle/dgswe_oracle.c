@@ -26,7 +26,9 @@
  *   - Roe flux with Roe averages (arithmetic Hs, sqrt(Hs)-weighted velocity), no entropy fix;
  *     LLF with the larger of |u.n| + sqrt(g Hs) over both sides; the jump is in (zeta, q);
  *   - ghost states: land mirrors q.n and carries zero mass flux; ocean takes zeta = tide(t)
- *     with the interior q; "exact" boundaries (verification only) take a prescribed field;
+ *     with the interior q; river edges (Eq. river_bc) carry exactly the prescribed normal
+ *     discharge as the mass component of the flux, and the momentum components of the
+ *     numerical flux between the interior trace and the ghost (zeta, -q_river n); "exact" boundaries (verification only) take a prescribed field;
  *   - bathymetry is continuous and piecewise linear from nodal values;
  *   - area rule exact to degree 2p+1 (p=1: 7-point degree 3; p=2: 7-point degree 5), edge
  *     rule Gauss-Legendre with p+1 points;
@@ -82,6 +84,9 @@ struct orc {
   double gx0, gy0, gdx, gdy, gt0, gdt;
   float* grid;
   int ntide;
+  int nriv, rnt;
+  double rt0, rdt;
+  double* rq; /* [rnt][nriv] */
   double *tamp, *tper, *tpha;
   int press;
   double pr[4];
@@ -257,7 +262,7 @@ void orc_destroy(orc_t* o) {
   if (!o) return;
   void* ptrs[] = {o->x, o->y, o->tri, o->edn, o->ede, o->edj, o->edt, o->eds, o->order, o->det, o->rx, o->ry,
                   o->sx, o->sy, o->area, o->hb, o->man, o->rain_nodal, o->grid, o->tamp, o->tper, o->tpha,
-                  o->w, o->wk[0], o->wk[1], o->wk[2], o->wk[3], o->Lw, o->rhs, o->rnode, o->Re, o->dry};
+                  o->w, o->wk[0], o->wk[1], o->wk[2], o->wk[3], o->Lw, o->rhs, o->rnode, o->Re, o->dry, o->rq};
   for (size_t i = 0; i < sizeof ptrs / sizeof ptrs[0]; ++i) freep(ptrs[i]);
   free(o);
 }
@@ -310,7 +315,9 @@ int orc_set_mesh(orc_t* o, int nn, const double* xy, int ne, const int32_t* tri,
   qsort(he, 3 * ne, sizeof(halfedge), cmp_he);
   halfedge* bk = (halfedge*)malloc(sizeof(halfedge) * (nb > 0 ? nb : 1)); /* e = boundary index */
   for (int b = 0; b < nb; ++b) {
-    if (btype[b] != ORC_BT_LAND && btype[b] != ORC_BT_OCEAN && btype[b] != ORC_BT_EXACT) { free(he); free(bk); return -2; }
+    if (btype[b] != ORC_BT_LAND && btype[b] != ORC_BT_OCEAN && btype[b] != ORC_BT_RIVER && btype[b] != ORC_BT_EXACT) {
+      free(he); free(bk); return -2;
+    }
     bk[b].key = pair_key(bedge[2 * b], bedge[2 * b + 1], nn); bk[b].e = b; bk[b].j = 0;
   }
   qsort(bk, nb, sizeof(halfedge), cmp_he);
@@ -346,12 +353,12 @@ int orc_set_mesh(orc_t* o, int nn, const double* xy, int ne, const int32_t* tri,
   }
   o->ned = ned;
   free(he); free(bk);
-  /* loop order of Sec. 2.3: elevation-specified edges, land edges, (verification) exact
-   * edges, then inner edges */
+  /* loop order of Sec. 2.3: elevation-specified edges, land edges, river edges, (verification)
+   * exact edges, then inner edges */
   o->order = (int*)malloc(sizeof(int) * ned);
   int k = 0;
-  const int seq[4] = {ORC_BT_OCEAN, ORC_BT_LAND, ORC_BT_EXACT, -1};
-  for (int q = 0; q < 4; ++q)
+  const int seq[5] = {ORC_BT_OCEAN, ORC_BT_LAND, ORC_BT_RIVER, ORC_BT_EXACT, -1};
+  for (int q = 0; q < 5; ++q)
     for (int i = 0; i < ned; ++i)
       if (o->edt[i] == seq[q]) o->order[k++] = i;
   o->ned = k;
@@ -483,6 +490,31 @@ static double rain_at(const orc_t* o, int n, double t) {
   return 0.0;
 }
 
+/* river discharge of segment seg at time t (m^2/s into the domain) */
+static double river_at(const orc_t* o, int seg, double t) {
+  if (seg < 0 || seg >= o->nriv || o->rnt < 1) return 0.0;
+  if (o->rnt == 1) return o->rq[seg];
+  double f = (t - o->rt0) / o->rdt;
+  if (f <= 0.0) return o->rq[seg];
+  if (f >= o->rnt - 1) return o->rq[(size_t)(o->rnt - 1) * o->nriv + seg];
+  int i = (int)floor(f);
+  double a = f - i;
+  return (1.0 - a) * o->rq[(size_t)i * o->nriv + seg] + a * o->rq[(size_t)(i + 1) * o->nriv + seg];
+}
+
+void orc_set_river(orc_t* o, int nseg, int nt, double t0, double dt, const double* q) {
+  free(o->rq);
+  o->rq = NULL;
+  o->nriv = o->rnt = 0;
+  if (nseg <= 0 || nt <= 0 || !q) return;
+  o->rq = (double*)malloc(sizeof(double) * (size_t)nseg * nt);
+  memcpy(o->rq, q, sizeof(double) * (size_t)nseg * nt);
+  o->nriv = nseg;
+  o->rnt = nt;
+  o->rt0 = t0;
+  o->rdt = dt > 0.0 ? dt : 1.0;
+}
+
 static double tide_at(const orc_t* o, int seg, double t) {
   if (seg < 0 || seg >= o->ntide) return 0.0;
   return o->tamp[seg] * sin(2.0 * M_PI * t / o->tper[seg] + o->tpha[seg]);
@@ -607,12 +639,17 @@ static void compute_L(orc_t* o, const double* W, double t, double* rain_out, dou
         wall_flux(o, wl[k], hbl[k], nx, ny, fl[k]);
       } else {
         double xp = interp_nodal(o, o->x, L, o->le[jL][k]), yp = interp_nodal(o, o->y, L, o->le[jL][k]);
+        double qr = 0.0;
         if (type == ORC_BT_OCEAN) {
           wr[k][0] = tide_at(o, o->eds[i], t); wr[k][1] = wl[k][1]; wr[k][2] = wl[k][2];
+        } else if (type == ORC_BT_RIVER) {
+          qr = river_at(o, o->eds[i], t);
+          wr[k][0] = wl[k][0]; wr[k][1] = -qr * nx; wr[k][2] = -qr * ny;
         } else {
           exact_state(o, xp, yp, t, wr[k]);
         }
         numflux_o(o, o->flux, wl[k], hbl[k], wr[k], hbl[k], nx, ny, fl[k]);
+        if (type == ORC_BT_RIVER) fl[k][0] = -qr; /* the specified normal flow, outward positive */
       }
       massflux += o->gw[k] * 0.5 * len * fl[k][0];
     }

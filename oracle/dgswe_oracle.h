@@ -20,7 +20,7 @@ typedef struct orc orc_t;
 
 enum { ORC_ROE = 0, ORC_LLF = 1 };
 enum { ORC_MANNING = 0, ORC_QUADRATIC = 1, ORC_NOFRICTION = 2 };
-enum { ORC_BT_LAND = 0, ORC_BT_OCEAN = 1, ORC_BT_EXACT = 3 };
+enum { ORC_BT_LAND = 0, ORC_BT_OCEAN = 1, ORC_BT_RIVER = 2, ORC_BT_EXACT = 3 };
 
 orc_t* orc_create(int p, int flux, int ssp_stages, double g, double H0, int friction, double cf);
 void orc_destroy(orc_t*);
@@ -33,6 +33,10 @@ void orc_set_rain_parametric(orc_t*, double x0, double y0, double heading, doubl
 void orc_set_rain_grid(orc_t*, int nx, int ny, int nt, double x0, double y0, double dx, double dy, double t0,
                        double dt_rec, const float* mm_per_h);
 void orc_set_tide(orc_t*, int nseg, const double* amp, const double* period, const double* phase);
+/* River boundaries (Sec. 2.1, Eq. river_bc): specified normal discharge q_river (m^2/s, positive
+ * into the domain) per river segment, nt records from t0 every dt (linear in time, held at the
+ * ends; nt = 1: constant).  q is [nt][nseg]. */
+void orc_set_river(orc_t* o, int nseg, int nt, double t0, double dt, const double* q);
 void orc_set_pressure(orc_t*, double x0, double y0, double sigma, double peak);
 void orc_set_exact_wave(orc_t*, double a, double k, double l, double c, double h0);
 void orc_set_exact_linear(orc_t*, const double* coef9);

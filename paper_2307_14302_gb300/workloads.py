@@ -26,7 +26,7 @@ import numpy as np
 
 G = 9.81
 MMH = 1.0 / 3.6e6  # (mm/h) -> (m/s)
-LAND, OCEAN = 0, 1
+LAND, OCEAN, RIVER = 0, 1, 2
 
 
 @dataclasses.dataclass
@@ -81,6 +81,15 @@ class Tide:
 
 
 @dataclasses.dataclass
+class River:
+    """Specified normal discharge (m^2/s, positive into the domain) per river segment: nt records
+    from t0 every dt, linear in time (nt = 1: constant); q is [nt, nseg]."""
+    q: np.ndarray
+    t0: float = 0.0
+    dt: float = 3600.0
+
+
+@dataclasses.dataclass
 class Workload:
     name: str
     mesh: Mesh
@@ -95,6 +104,7 @@ class Workload:
     rain_grid: RainGrid | None = None
     tide: Tide | None = None
     pressure: tuple | None = None  # (x0, y0, sigma, peak)
+    river: River | None = None
     h0: float = 0.01
     meta: dict = dataclasses.field(default_factory=dict)
 
@@ -362,6 +372,35 @@ def basin_c1(seed=1, hump=True, rain=True, mirror=False, nx=20, ny=10) -> Worklo
         name="basin-400tri-p1", mesh=mesh, hb=hb, manning=np.full(mesh.n_tri, 0.025), zeta0=zeta0,
         p=1, steps=200, cfl=0.3, rain_nodal=rain_nodal, meta={"seed": seed, "hump_centre": (xc, yc)},
     )
+
+
+def river_basin(q=(2.0, 0.5), ramp_s=600.0, nx=20, ny=10, wet=True, seed=7) -> Workload:
+    """The basin of ``basin_c1`` (no hump, no rain) with two river inflow segments on its walls:
+    segment 0 on the x = 0 wall for 1 km <= y <= 3 km, segment 1 on the y = 5 km wall for
+    6 km <= x <= 8 km.  Discharge per unit width ramps linearly from 0 to q over ramp_s seconds
+    (records every ramp_s / 4 s).  With wet=False the bathymetry rises above the geoid near the
+    x = 0 river so that the river first flows onto dry land; the CFL number is then 0.04, since
+    explicit Manning friction on films of about H0 (tau ~ 3/s) needs dt * tau < 1."""
+    w = basin_c1(seed=seed, hump=False, rain=False, nx=nx, ny=ny)
+    m = w.mesh
+    mid = 0.5 * (m.xy[m.bedge[:, 0]] + m.xy[m.bedge[:, 1]])
+    btype = m.btype.copy()
+    bseg = m.bseg.copy()
+    r0 = (mid[:, 0] < 1e-6) & (mid[:, 1] > 1000.0) & (mid[:, 1] < 3000.0)
+    r1 = (mid[:, 1] > 5000.0 - 1e-6) & (mid[:, 0] > 6000.0) & (mid[:, 0] < 8000.0)
+    btype[r0 | r1] = RIVER
+    bseg[r0] = 0
+    bseg[r1] = 1
+    w.mesh = Mesh(m.xy, m.tri, m.bedge, btype, bseg)
+    if not wet:
+        x = m.xy[:, 0]
+        w.hb = w.hb - 8.0 * np.clip(1.0 - x / 2500.0, 0.0, None)
+        w.zeta0 = _initial_dry(w.hb, w.h0)
+        w.cfl = 0.04
+    tq = np.linspace(0.0, 1.0, 5)[:, None] * np.asarray(q, float)[None, :]
+    w.river = River(q=tq, t0=0.0, dt=ramp_s / 4.0)
+    w.name = f"river-basin-{m.n_tri}tri-p1"
+    return w
 
 
 def bathtub(nx=25, ny=4) -> Workload:

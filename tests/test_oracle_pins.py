@@ -277,6 +277,51 @@ def test_p1_modal_operator_equals_vertex_operator():
         assert dry == bool(dv.any())
 
 
+# ---------------------------------------------------------------------------- rivers --
+def _river_lengths(w):
+    m = w.mesh
+    L = np.hypot(*(m.xy[m.bedge[:, 0]] - m.xy[m.bedge[:, 1]]).T)
+    return np.array([L[(m.btype == W.RIVER) & (m.bseg == k)].sum() for k in range(w.river.q.shape[1])])
+
+
+def test_river_inflow_volume_is_the_prescribed_discharge():
+    """Eq. river_bc: the normal flow through a river edge is the prescribed q_river, so in a
+    walled basin without rain the volume gained is the time integral of q_river times the
+    river length: q T^2 / (2 T_ramp) during a linear ramp (SSP(2,2) integrates it exactly)."""
+    w = W.river_basin(q=(2.0, 0.5), ramp_s=600.0)
+    lens = _river_lengths(w)
+    assert np.allclose(lens, [2000.0, 2000.0])
+    o = O.from_workload(w)
+    o.step(200)
+    led = o.ledger()
+    T = led["t"]
+    assert T < 600.0
+    expect = float((np.array([2.0, 0.5]) * lens).sum() * T * T / 1200.0)
+    assert abs((led["V"] - led["V0"]) - expect) <= 1e-9 * expect
+    assert abs(led["bdry_in"] - expect) <= 1e-9 * expect
+    assert led["rel_err"] < 1e-14
+
+
+def test_river_with_zero_discharge_keeps_the_lake_at_rest():
+    w = W.river_basin(q=(0.0, 0.0))
+    o = O.from_workload(w)
+    L = o.rhs()
+    assert np.abs(L).max() < 1e-12
+    o.step(100)
+    st = o.state()
+    assert np.abs(st[:, 0]).max() < 1e-12 and np.abs(st[:, 1:]).max() < 1e-11
+
+
+def test_river_onto_dry_land_wets_it_and_conserves_mass():
+    w = W.river_basin(q=(0.05, 0.0), ramp_s=60.0, wet=False)
+    o = O.from_workload(w)
+    dry0 = o.dry().sum()
+    assert dry0 > 0
+    o.step(800)
+    assert o.dry().sum() < dry0
+    assert o.ledger()["rel_err"] < 1e-13
+
+
 # --------------------------------------------------------------------------- SSP-RK --
 def test_ssp_stability_polynomials_are_truncated_taylor_series():
     for z in np.linspace(-2.5, 0.5, 13):
