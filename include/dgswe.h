@@ -52,7 +52,7 @@ enum {
 enum { DGSWE_FLUX_ROE = 0, DGSWE_FLUX_LLF = 1 };             /* Sec. 2.3 numerical fluxes */
 enum { DGSWE_FP64 = 0, DGSWE_MIXED = 1 };                    /* arithmetic of the device path */
 enum { DGSWE_MANNING = 0, DGSWE_QUADRATIC = 1, DGSWE_NOFRICTION = 2 };
-enum { DGSWE_BT_LAND = 0, DGSWE_BT_OCEAN = 1 };              /* boundary types, Sec. 2.1 */
+enum { DGSWE_BT_LAND = 0, DGSWE_BT_OCEAN = 1, DGSWE_BT_RIVER = 2 };  /* boundary types, Sec. 2.1 */
 enum { DGSWE_LAYOUT_MODAL = 0, DGSWE_LAYOUT_NODAL = 1 };
 
 typedef struct dgswe_ctx* dgswe_h;
@@ -140,6 +140,17 @@ int dgswe_set_rain_grid(dgswe_h, int32_t nx, int32_t ny, int32_t nt, double x0, 
 
 /* Tidal elevation on ocean edges of segment s: amp[s] sin(2 pi t / period[s] + phase[s]). */
 int dgswe_set_tide(dgswe_h, int32_t n_seg, const double* amp, const double* period, const double* phase);
+
+/* River (specified normal flow) boundaries, Sec. 2.1 Eq. river_bc: edges of type
+ * DGSWE_BT_RIVER with bseg = river segment in [0, 8).  q is [n_t][n_seg]: discharge per unit
+ * width in m^2/s, positive INTO the domain, n_t records from t0 every dt_rec seconds, linear in
+ * time and held constant before the first and after the last record (n_t = 1: constant).
+ * The mass component of the numerical flux on a river edge is exactly -q (outward), the
+ * momentum components are those of the numerical flux between the interior trace and the ghost
+ * state (zeta, -q n); the inflow counts as boundary inflow in the ledger.  Copied; a later call
+ * replaces the series.  Returns DGSWE_EINVAL for n_seg outside [1, 8], n_t < 1, dt_rec <= 0
+ * with n_t > 1, or non-finite values. */
+int dgswe_set_river(dgswe_h, int32_t n_seg, int32_t n_t, double t0, double dt_rec, const double* q);
 
 /* Gaussian pressure set-up forcing (F_x, F_y of Eq. SWE); NULL removes it. */
 int dgswe_set_pressure_setup(dgswe_h, const dgswe_gauss_setup* setup);

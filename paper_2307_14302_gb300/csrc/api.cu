@@ -58,6 +58,9 @@ struct Scenario {
   double gx0 = 0, gy0 = 0, gdx = 1, gdy = 1, gt0 = 0, gdt = 1;
   std::vector<float> grid;
   std::vector<double> tamp, tper, tpha;
+  int rnseg = 0, rnt = 0;          // river segments and records
+  double rt0 = 0.0, rdt = 1.0;
+  std::vector<double> river;       // [rnt][rnseg] m^2/s into the domain
   bool press = false;
   dgswe_gauss_setup ps{};
   std::vector<double> w;           // caller's state, modal [ne][3][np], new element order
@@ -109,7 +112,7 @@ struct dgswe_ctx {
   int np = 0, rv = 0, gv = 0;      // modes, record and geometry sizes (16-byte units)
   long long E = 0, N = 0;          // padded element count, node count
   std::vector<long long> eoff, noff;
-  DevBuf rec[3], nbr, geo, nodes, node_xy, xy64, hbn, rain_e, scen, tile_scen, ledger, ctl, eorig, grids, scratch,
+  DevBuf rec[3], nbr, geo, nodes, node_xy, xy64, hbn, rain_e, scen, tile_scen, ledger, ctl, eorig, grids, rivers, scratch,
       gather_buf, edges, slots;
   long long nedges = 0;
   int ntiles = 0;                          // 32-element tiles
@@ -130,7 +133,7 @@ struct dgswe_ctx {
   ~dgswe_ctx() {
     DeviceGuard dg_(device);
     DevBuf* bufs[] = {&rec[0], &rec[1], &rec[2], &nbr, &geo, &nodes, &node_xy, &xy64, &hbn, &rain_e, &scen,
-                      &tile_scen, &ledger, &ctl, &eorig, &grids, &scratch, &gather_buf, &edges, &slots};
+                      &tile_scen, &ledger, &ctl, &eorig, &grids, &rivers, &scratch, &gather_buf, &edges, &slots};
     for (DevBuf* b : bufs) b->alloc(0);
     if (g1) cudaGraphExecDestroy(g1);
     if (gK) cudaGraphExecDestroy(gK);
@@ -256,6 +259,8 @@ static int build_layout(dgswe_h h) {
   std::vector<double> rain64(mx ? 0 : E);
   std::vector<float> grids;
   std::vector<size_t> grid_off(ns, 0);
+  std::vector<double> rivers;
+  std::vector<size_t> river_off(ns, 0);
   for (size_t s = 0; s < ns; ++s) {
     const Scenario& S = h->sc[s];
     const HostMesh& M = S.m;
@@ -267,6 +272,7 @@ static int build_layout(dgswe_h h) {
       if (mx) { xyf[2 * (no + i)] = (float)M.x[i]; xyf[2 * (no + i) + 1] = (float)M.y[i]; }
     }
     if (S.rain_kind == 3) { grid_off[s] = grids.size(); grids.insert(grids.end(), S.grid.begin(), S.grid.end()); }
+    if (S.rnseg > 0) { river_off[s] = rivers.size(); rivers.insert(rivers.end(), S.river.begin(), S.river.end()); }
     for (int e = 0; e < M.ne; ++e) {
       const long long ge = eo + e;
       const int32_t* v = &M.tri[3 * (size_t)e];
@@ -374,6 +380,7 @@ static int build_layout(dgswe_h h) {
       h->xy64.alloc(16 * (size_t)N) || h->hbn.alloc(8 * (size_t)N) || h->eorig.alloc(4 * (size_t)E) ||
       h->node_xy.alloc(mx ? 8 * (size_t)N : 16 * (size_t)N) || h->rain_e.alloc(mx ? 4 * (size_t)E : 8 * (size_t)E) ||
       h->ctl.alloc(sizeof(Ctl)) || h->scen.alloc(sizeof(ScenDev) * ns) || h->grids.alloc(4 * grids.size()) ||
+      h->rivers.alloc(8 * rivers.size()) ||
       h->scratch.alloc(sizeof(double) * 4 * 4096))
     return fail(DGSWE_ENOMEM, "device allocation failed");
   CU(cudaMemcpy(h->rec[0].p, rec.data(), rbytes, cudaMemcpyHostToDevice));
@@ -393,6 +400,7 @@ static int build_layout(dgswe_h h) {
     CU(cudaMemcpy(h->rain_e.p, rain64.data(), 8 * rain64.size(), cudaMemcpyHostToDevice));
   }
   if (!grids.empty()) CU(cudaMemcpy(h->grids.p, grids.data(), 4 * grids.size(), cudaMemcpyHostToDevice));
+  if (!rivers.empty()) CU(cudaMemcpy(h->rivers.p, rivers.data(), 8 * rivers.size(), cudaMemcpyHostToDevice));
   CU(cudaMemset(h->ctl.p, 0, sizeof(Ctl)));
   // per-scenario parameter blocks (dt filled in later)
   std::vector<ScenDev> sd(ns);
@@ -407,6 +415,11 @@ static int build_layout(dgswe_h h) {
     D.gnx = S.gnx; D.gny = S.gny; D.gnt = S.gnt;
     D.grid = S.rain_kind == 3 ? h->grids.as<float>() + grid_off[s] : nullptr;
     D.nseg = (int32_t)S.tamp.size();
+    D.rnseg = S.rnseg;
+    D.rnt = S.rnt;
+    D.rt0 = S.rt0;
+    D.ridt = 1.0 / S.rdt;
+    D.river = S.rnseg > 0 ? h->rivers.as<double>() + river_off[s] : nullptr;
     D.press = S.press ? 1 : 0;
     const double st[8] = {S.storm.x0, S.storm.y0, S.storm.speed * std::cos(S.storm.heading),
                           S.storm.speed * std::sin(S.storm.heading), S.storm.rpeak, S.storm.rm, S.storm.re, S.storm.t0};
@@ -855,6 +868,24 @@ int dgswe_set_tide(dgswe_h h, int32_t n, const double* amp, const double* per, c
   return 0;
 }
 
+int dgswe_set_river(dgswe_h h, int32_t n, int32_t nt, double t0, double dt_rec, const double* q) {
+  if (int rc = check_handle(h)) return rc;
+  Scenario* S = scen_at(h, 1);
+  if (!S) return fail(DGSWE_ESTATE, "set_mesh must precede set_river");
+  if (n < 1 || n > MAXRIV || nt < 1 || !q) return fail(DGSWE_EINVAL, "river: 1 to %d segments and at least one record", MAXRIV);
+  if (nt > 1 && !(dt_rec > 0)) return fail(DGSWE_EINVAL, "river: record interval must be positive");
+  if (!std::isfinite(t0)) return fail(DGSWE_EINVAL, "river: non-finite t0");
+  for (size_t k = 0; k < (size_t)n * nt; ++k)
+    if (!std::isfinite(q[k])) return fail(DGSWE_EINVAL, "river: non-finite discharge");
+  S->rnseg = n;
+  S->rnt = nt;
+  S->rt0 = t0;
+  S->rdt = nt > 1 ? dt_rec : 1.0;
+  S->river.assign(q, q + (size_t)n * nt);
+  h->ready = false;
+  return 0;
+}
+
 int dgswe_set_pressure_setup(dgswe_h h, const dgswe_gauss_setup* ps) {
   if (int rc = check_handle(h)) return rc;
   Scenario* S = scen_at(h, 1);
@@ -874,6 +905,7 @@ int dgswe_set_state(dgswe_h h, const double* zeta, const double* qx, const doubl
   const int p = h->prm.p, np = np_of(p);
   const HostMesh& M = S->m;
   if (M.nseg > (int)S->tamp.size()) return fail(DGSWE_EINVAL, "ocean edges use %d tidal segments, %zu given", M.nseg, S->tamp.size());
+  if (M.nriv > S->rnseg) return fail(DGSWE_EINVAL, "river edges use %d river segments, %d given", M.nriv, S->rnseg);
   S->w.assign((size_t)M.ne * 3 * np, 0.0);
   const double* f[3] = {zeta, qx, qy};
   if (layout == DGSWE_LAYOUT_MODAL) {

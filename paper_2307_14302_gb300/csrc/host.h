@@ -21,6 +21,7 @@ struct HostMesh {
   std::vector<double> lnx, lny;    // [ne][3] outward normal scaled by the edge length
   std::vector<double> area;        // [ne]
   int nseg = 0;                    // 1 + largest tidal segment index used
+  int nriv = 0;                    // 1 + largest river segment index used
 };
 
 int build_mesh(int nn, const double* xy, int ne, const int32_t* tri, int nb, const int32_t* bedge,

@@ -22,7 +22,8 @@
 
 namespace dg {
 
-constexpr int MAXSEG = 8;
+constexpr int MAXSEG = 8;   // tidal segments: ocean edge code -2 - seg
+constexpr int MAXRIV = 8;   // river segments: river edge code -2 - MAXSEG - seg
 constexpr int MAXNP = 6;
 constexpr int MAXNQ = 7;
 constexpr int MAXNG = 3;
@@ -84,6 +85,9 @@ struct ScenDev {
   int32_t gnx, gny, gnt;
   int32_t nseg;
   int32_t press;
+  int32_t rnseg, rnt;              // river segments and records
+  double rt0, ridt;                // first record time, 1 / record interval
+  const double* river;             // [rnt][rnseg] m^2/s into the domain
   const float* grid;               // [gnt][gny][gnx] mm/h
   ForcingT<float> f;
   ForcingT<double> d;

@@ -5,8 +5,9 @@
 //    neighbours of an element sit at nearby indices and their records are L2 hits;
 // 3. nodes are renumbered by first use in that order;
 // 4. edges are paired by their node pair; each local edge j (vertex j -> j+1) gets a code:
-//    (neighbour << 2 | neighbour's local edge), -1 for land, -2 - segment for ocean edges
-//    (Sec. 2.1: ocean = specified elevation, land = zero normal flow);
+//    (neighbour << 2 | neighbour's local edge), -1 for land, -2 - segment for ocean edges,
+//    -2 - MAXSEG - segment for river edges (Sec. 2.1: ocean = specified elevation, land = zero
+//    normal flow, river = specified normal flow);
 // 5. scaled outward normals ln_j = (dy, -dx) of each local edge are computed in FP64 from node
 //    differences, so the two sides of an interior edge hold exactly opposite values.
 #include <algorithm>
@@ -112,13 +113,18 @@ int build_mesh(int nn, const double* xy, int ne, const int32_t* tri_in, int nb, 
   for (int b = 0; b < nb; ++b) {
     const int32_t a0 = bedge[2 * b], b0 = bedge[2 * b + 1];
     if (a0 < 0 || a0 >= nn || b0 < 0 || b0 >= nn) { err = "set_mesh: boundary edge node out of range"; return DGSWE_EINVAL; }
-    if (btype[b] != DGSWE_BT_LAND && btype[b] != DGSWE_BT_OCEAN) {
+    if (btype[b] != DGSWE_BT_LAND && btype[b] != DGSWE_BT_OCEAN && btype[b] != DGSWE_BT_RIVER) {
       snprintf(buf, sizeof buf, "set_mesh: boundary edge %d has unknown type %d", b, btype[b]);
       err = buf;
       return DGSWE_EINVAL;
     }
     if (btype[b] == DGSWE_BT_OCEAN && (!bseg || bseg[b] < 0 || bseg[b] >= MAXSEG)) {
       snprintf(buf, sizeof buf, "set_mesh: ocean edge %d needs a segment in [0,%d)", b, MAXSEG);
+      err = buf;
+      return DGSWE_EINVAL;
+    }
+    if (btype[b] == DGSWE_BT_RIVER && (!bseg || bseg[b] < 0 || bseg[b] >= MAXRIV)) {
+      snprintf(buf, sizeof buf, "set_mesh: river edge %d needs a segment in [0,%d)", b, MAXRIV);
       err = buf;
       return DGSWE_EINVAL;
     }
@@ -131,6 +137,7 @@ int build_mesh(int nn, const double* xy, int ne, const int32_t* tri_in, int nb, 
   for (int b = 0; b < nb; ++b) bsorted[b] = bkey[bid[b]];
   M.code.assign(3 * (size_t)ne, -1);
   M.nseg = 0;
+  M.nriv = 0;
   for (size_t i = 0; i < he.size();) {
     size_t k = i + 1;
     while (k < he.size() && he[k].k == he[i].k) ++k;
@@ -156,6 +163,9 @@ int build_mesh(int nn, const double* xy, int ne, const int32_t* tri_in, int nb, 
         if (btype[b] == DGSWE_BT_OCEAN) {
           c = -2 - bseg[b];
           M.nseg = std::max(M.nseg, bseg[b] + 1);
+        } else if (btype[b] == DGSWE_BT_RIVER) {
+          c = -2 - MAXSEG - bseg[b];
+          M.nriv = std::max(M.nriv, bseg[b] + 1);
         }
       }
       M.code[3 * (size_t)p.e + p.j] = c;

@@ -25,9 +25,6 @@
 #include "args.h"
 #include "layout.h"
 
-#ifndef DG_OCEAN64
-#define DG_OCEAN64 0  // 1: mixed path evaluates ocean-boundary edges in FP64
-#endif
 
 namespace dg {
 
@@ -156,6 +153,21 @@ __device__ __forceinline__ float tide_at<float>(const ScenDev& S, int k, double 
 template <>
 __device__ __forceinline__ double tide_at<double>(const ScenDev& S, int k, double t) {
   return S.d.tide[k][0] * sin(S.d.tide[k][1] * t + S.d.tide[k][2]);
+}
+
+// river discharge (m^2/s into the domain) of segment k at time t: linear between records, held
+// at both ends (Eq. river_bc)
+template <class T>
+__device__ __forceinline__ T river_at(const ScenDev& S, int k, double t) {
+  if (k >= S.rnseg) return T(0);
+  const double* q = S.river;
+  if (S.rnt == 1) return (T)q[k];
+  const double f = (t - S.rt0) * S.ridt;
+  if (f <= 0.0) return (T)q[k];
+  if (f >= (double)(S.rnt - 1)) return (T)q[(size_t)(S.rnt - 1) * S.rnseg + k];
+  const int i = (int)floor(f);
+  const double w = f - (double)i;
+  return (T)((1.0 - w) * q[(size_t)i * S.rnseg + k] + w * q[(size_t)(i + 1) * S.rnseg + k]);
 }
 
 template <class T>
@@ -1153,8 +1165,8 @@ __global__ void DG_STAGE_BOUNDS stage_kernel(const StageArgs<Pol> a) {
       Trace<T> tm[NG], to[NG];  // my trace and the other side's, at my edge points
 #pragma unroll
       for (int k = 0; k < NG; ++k) tm[k] = trace_at<P, Pol>(E, s_ephi[j][k]);
-      bool me_L = true, dry_o = false;
-      T dcRL = 0, dc_nm = 0;
+      bool me_L = true, dry_o = false, river = false;
+      T dcRL = 0, dc_nm = 0, qr = 0;
       if (!SPLIT && code >= 0) {
         const long long ne_ = code >> 2;
         const int jn = code & 3;
@@ -1169,6 +1181,16 @@ __global__ void DG_STAGE_BOUNDS stage_kernel(const StageArgs<Pol> a) {
         dry_o = (N.flags & FLAG_DRY) != 0;
 #pragma unroll
         for (int k = 0; k < NG; ++k) to[k] = trace_at<P, Pol>(N, s_ephi[jn][NG - 1 - k]);  // same point
+      } else if (code <= -2 - MAXSEG) {  // river: interior elevation, prescribed normal discharge
+        const int rs = min(-2 - MAXSEG - code, MAXRIV - 1);
+        qr = river_at<T>(S, rs, S.d.t0 + ((double)a.ctl->step + a.cst) * S.d.dt);
+        river = true;
+#pragma unroll
+        for (int k = 0; k < NG; ++k) {
+          to[k] = tm[k];
+          to[k].qx = -qr * nx;
+          to[k].qy = -qr * ny;
+        }
       } else if (code < -1) {  // ocean: tidal elevation, interior discharge
         const int seg = min(-2 - code, MAXSEG - 1);
         const double t64 = S.d.t0 + ((double)a.ctl->step + a.cst) * S.d.dt;  // stage time in FP64
@@ -1183,36 +1205,6 @@ __global__ void DG_STAGE_BOUNDS stage_kernel(const StageArgs<Pol> a) {
       }
       T Fz[NG], Fx[NG], Fy[NG];  // flux along my outward normal at my points
       T emine = 0;              // mass flux integral along my outward normal
-#if DG_OCEAN64
-      if (sizeof(T) == 4 && code < -1) {  // ocean edge evaluated in FP64 from my FP32 trace
-        const int seg = min(-2 - code, MAXSEG - 1);
-        const double t64 = S.d.t0 + ((double)a.ctl->step + a.cst) * S.d.dt;
-        const double dgh = tide_at<double>(S, seg, t64) - acc_d(E.zb);
-        const double nxd = (double)lnx / (double)len, nyd = (double)lny / (double)len;
-        double fz[NG], fx[NG], fy[NG], pp[NG], ec = 0.0;
-#pragma unroll
-        for (int k = 0; k < NG; ++k) {
-          const Trace<double> L{(double)tm[k].d, (double)tm[k].H, (double)tm[k].qx, (double)tm[k].qy};
-          Trace<double> R = L;
-          R.H = L.H + (dgh - L.d);
-          R.d = dgh;
-          edge_flux<FLUX, double>(L, R, 0.0, nxd, nyd, (double)g, (double)H0, fz[k], fx[k], fy[k]);
-          pp[k] = 0.5 * (pdev(L.d, L.H, (double)g) + pdev(R.d, R.H, (double)g));
-          ec = fma((double)tab.gw[k], fz[k], ec);
-        }
-        ec *= 0.5 * (double)len;
-        wall = dry_me && ec > 0.0;
-        if (!wall) {
-          emine = (T)ec;
-#pragma unroll
-          for (int k = 0; k < NG; ++k) {
-            Fz[k] = (T)fz[k];
-            Fx[k] = (T)(fx[k] + pp[k] * nxd);
-            Fy[k] = (T)(fy[k] + pp[k] * nyd);
-          }
-        }
-      } else
-#endif
       if (!wall) {
         const T sgn = me_L ? T(1) : T(-1);
         T fzc[NG], fxc[NG], fyc[NG];
@@ -1221,6 +1213,7 @@ __global__ void DG_STAGE_BOUNDS stage_kernel(const StageArgs<Pol> a) {
           const Trace<T> tL = me_L ? tm[k] : to[k];
           const Trace<T> tR = me_L ? to[k] : tm[k];
           edge_flux<FLUX, T>(tL, tR, dcRL, sgn * nx, sgn * ny, g, H0, fzc[k], fxc[k], fyc[k]);
+          if (river) fzc[k] = -qr;  // the specified normal flow is the mass flux
         }
         T ecanon = 0;  // in L's point order: identical bits on both sides of the edge
 #pragma unroll

@@ -57,7 +57,7 @@ class Ledger(C.Structure):
 
 EXPORTS = [
     "dgswe_create", "dgswe_set_params", "dgswe_set_mesh", "dgswe_set_fields", "dgswe_set_rain_nodal",
-    "dgswe_set_rain_parametric", "dgswe_set_rain_grid", "dgswe_set_tide", "dgswe_set_pressure_setup",
+    "dgswe_set_rain_parametric", "dgswe_set_rain_grid", "dgswe_set_tide", "dgswe_set_river", "dgswe_set_pressure_setup",
     "dgswe_set_state", "dgswe_load_state", "dgswe_step", "dgswe_sync", "dgswe_get_dt", "dgswe_get_state", "dgswe_get_state_device",
     "dgswe_get_dry", "dgswe_get_ledger", "dgswe_volume", "dgswe_volume_sum_noalloc", "dgswe_ensemble_create", "dgswe_ensemble_step",
     "dgswe_ensemble_get_state", "dgswe_ensemble_get_ledger", "dgswe_set_launch", "dgswe_get_launch",
@@ -91,6 +91,7 @@ def lib():
         "dgswe_set_rain_parametric": ([_h, C.POINTER(Storm)], C.c_int),
         "dgswe_set_rain_grid": ([_h, C.c_int32, C.c_int32, C.c_int32] + [C.c_double] * 6 + [_f], C.c_int),
         "dgswe_set_tide": ([_h, C.c_int32, _d, _d, _d], C.c_int),
+        "dgswe_set_river": ([_h, C.c_int32, C.c_int32, C.c_double, C.c_double, _d], C.c_int),
         "dgswe_set_pressure_setup": ([_h, C.POINTER(GaussSetup)], C.c_int),
         "dgswe_set_state": ([_h, _d, _d, _d, C.c_int32, C.c_double], C.c_int),
         "dgswe_load_state": ([_h, _d, _d, _d], C.c_int),
@@ -192,6 +193,11 @@ class Solver:
 
     def set_tide(self, t):
         _check(lib().dgswe_set_tide(self.h, len(t.amp), _p(_f64(t.amp)), _p(_f64(t.period)), _p(_f64(t.phase))))
+
+    def set_river(self, r):
+        """River discharge series (workloads.River: q [nt, nseg] m^2/s into the domain)."""
+        q = np.ascontiguousarray(np.atleast_2d(np.asarray(r.q, dtype=np.float64)))
+        _check(lib().dgswe_set_river(self.h, q.shape[1], q.shape[0], float(r.t0), float(r.dt), _p(q)))
 
     def set_pressure_setup(self, x0, y0, sigma, peak):
         gs = GaussSetup(x0, y0, sigma, peak)
@@ -343,5 +349,7 @@ def from_workload(w, precision=MIXED, flux=FLUX_ROE, ssp_stages=None, dt=0.0, fr
         s.set_tide(w.tide)
     if w.pressure is not None:
         s.set_pressure_setup(*w.pressure)
+    if getattr(w, "river", None) is not None:
+        s.set_river(w.river)
     s.set_state(w.zeta0)
     return s

@@ -231,6 +231,27 @@ def test_hurricane_full_size_two_steps():
     assert dev.ledger()["rel_err"] < 1e-12
 
 
+# ------------------------------------------------------------------------- rivers ------
+@pytest.mark.parametrize("prec", [D.FP64, D.MIXED])
+@pytest.mark.parametrize("wet", [True, False])
+def test_river_boundaries_match_oracle(prec, wet):
+    """Eq. river_bc: two ramped river inflows into the walled basin (wet, and onto dry land):
+    state against the oracle and the boundary inflow against the prescribed discharge."""
+    w = W.river_basin(q=(2.0, 0.5) if wet else (0.05, 0.0), ramp_s=600.0 if wet else 60.0, wet=wet)
+    steps = 200
+    ref, dev = _pair(w, steps, prec)
+    got, want = dev.state(), ref.state()
+    if prec == D.FP64:
+        assert _fp64_err(got, want) <= FP64_TOL
+    else:
+        ez, eq = _mixed_err(got, want)
+        assert ez <= MIXED_TOL and eq <= MIXED_TOL, (ez, eq)
+    led, rl = dev.ledger(), ref.ledger()
+    assert led["rel_err"] < 1e-12
+    assert abs(led["bdry_in"] - rl["bdry_in"]) <= 1e-9 * abs(rl["bdry_in"])
+    assert np.array_equal(dev.dry(), ref.dry())
+
+
 # -------------------------------------------------------------------- forcing paths ------
 @pytest.mark.parametrize("prec", [D.FP64, D.MIXED])
 def test_gridded_rain_and_pressure_setup(prec):
