@@ -32,7 +32,9 @@
  *   - bathymetry is continuous and piecewise linear from nodal values;
  *   - area rule exact to degree 2p+1 (p=1: 7-point degree 3; p=2: 7-point degree 5), edge
  *     rule Gauss-Legendre with p+1 points;
- *   - SSP(2,2) and SSP(3,3) in Shu-Osher form (SSP(1,1) for the finite-volume check);
+ *   - SSP(2,2) and SSP(3,3) in Shu-Osher form (SSP(1,1) for the finite-volume check); the
+ *     five-stage scheme of the production runs (Sec. 3) as the optimal five-stage second-order
+ *     SSP method, its DG-optimised coefficients not being given;
  *   - M Pi^d case 3 lifts the lowest vertex to H0 and takes the deficit evenly from the other
  *     two, or lifts the middle one too when that would push it below H0;  a vertex is dry
  *     when its updated depth is below H0 and all three are dry in case 2;  M Pi^f zeroes dry
@@ -61,7 +63,7 @@ struct orc {
   int p, np, flux, nstage, friction;
   double g, H0, cf, dt, t;
   long nstep;
-  double alpha[3][3], beta[3], cst[3], bw[3];
+  double alpha[5][5], beta[5], cst[5], bw[5];
   /* mesh */
   int nn, ne, ned;
   double *x, *y;
@@ -93,7 +95,7 @@ struct orc {
   int exact;
   double ex[9];
   /* state and work */
-  double *w, *wk[4], *Lw, *rhs, *rnode, *Re;
+  double *w, *wk[6], *Lw, *rhs, *rnode, *Re;
   uint8_t* dry;
   /* ledger (Neumaier-compensated) */
   double V0, VH0, rain_s, rain_c, bd_s, bd_c, stage_bdry;
@@ -205,7 +207,7 @@ int orc_edge_rule(int p, double* xi, double* w) {
 
 /* --------------------------------------------------------------------------- setup --- */
 orc_t* orc_create(int p, int flux, int ssp_stages, double g, double H0, int friction, double cf) {
-  if (p < 0 || p > 2 || ssp_stages < 1 || ssp_stages > 3) return NULL;
+  if (p < 0 || p > 2 || ssp_stages < 1 || ssp_stages > 5 || ssp_stages == 4) return NULL;
   orc_t* o = (orc_t*)calloc(1, sizeof(orc_t));
   o->p = p; o->np = (p + 1) * (p + 2) / 2; o->flux = flux; o->nstage = ssp_stages;
   o->g = g; o->H0 = H0; o->friction = friction; o->cf = cf;
@@ -216,14 +218,21 @@ orc_t* orc_create(int p, int flux, int ssp_stages, double g, double H0, int fric
     o->alpha[0][0] = 1.0; o->beta[0] = 1.0;
     o->alpha[1][0] = 0.5; o->alpha[1][1] = 0.5; o->beta[1] = 0.5;
     o->cst[0] = 0.0; o->cst[1] = 1.0;
-  } else {
+  } else if (ssp_stages == 3) {
     o->alpha[0][0] = 1.0; o->beta[0] = 1.0;
     o->alpha[1][0] = 0.75; o->alpha[1][1] = 0.25; o->beta[1] = 0.25;
     o->alpha[2][0] = 1.0 / 3.0; o->alpha[2][1] = 0.0; o->alpha[2][2] = 2.0 / 3.0; o->beta[2] = 2.0 / 3.0;
     o->cst[0] = 0.0; o->cst[1] = 1.0; o->cst[2] = 0.5;
+  } else {
+    /* optimal five-stage second-order SSP method: four forward-Euler substeps of dt/4, then
+     * w(5) = w(0)/5 + 4/5 (w(4) + dt/4 L(w(4))); stage times t + i dt / 4 */
+    for (int i = 0; i < 4; ++i) {
+      o->alpha[i][i] = 1.0; o->beta[i] = 0.25; o->cst[i] = 0.25 * i;
+    }
+    o->alpha[4][0] = 0.2; o->alpha[4][4] = 0.8; o->beta[4] = 0.2; o->cst[4] = 1.0;
   }
   /* weight of dt*L(w(s)) in the final stage, for the mass ledger */
-  double coef[4][3] = {{0}};
+  double coef[6][5] = {{0}};
   for (int i = 0; i < ssp_stages; ++i)
     for (int s = 0; s < ssp_stages; ++s) {
       double c = (s == i) ? o->beta[i] : 0.0;
@@ -262,7 +271,8 @@ void orc_destroy(orc_t* o) {
   if (!o) return;
   void* ptrs[] = {o->x, o->y, o->tri, o->edn, o->ede, o->edj, o->edt, o->eds, o->order, o->det, o->rx, o->ry,
                   o->sx, o->sy, o->area, o->hb, o->man, o->rain_nodal, o->grid, o->tamp, o->tper, o->tpha,
-                  o->w, o->wk[0], o->wk[1], o->wk[2], o->wk[3], o->Lw, o->rhs, o->rnode, o->Re, o->dry, o->rq};
+                  o->w, o->wk[0], o->wk[1], o->wk[2], o->wk[3], o->wk[4], o->wk[5], o->Lw, o->rhs, o->rnode,
+                  o->Re, o->dry, o->rq};
   for (size_t i = 0; i < sizeof ptrs / sizeof ptrs[0]; ++i) freep(ptrs[i]);
   free(o);
 }
@@ -364,7 +374,7 @@ int orc_set_mesh(orc_t* o, int nn, const double* xy, int ne, const int32_t* tri,
   o->ned = k;
   size_t nw = (size_t)ne * 3 * o->np;
   o->w = (double*)calloc(nw, sizeof(double));
-  for (int i = 0; i < 4; ++i) o->wk[i] = (double*)calloc(nw, sizeof(double));
+  for (int i = 0; i < 6; ++i) o->wk[i] = (double*)calloc(nw, sizeof(double));
   o->Lw = (double*)calloc(nw, sizeof(double));
   o->rhs = (double*)calloc(nw, sizeof(double));
   o->rnode = (double*)calloc(nn, sizeof(double));
@@ -967,7 +977,7 @@ void orc_set_time(orc_t* o, double t) { o->t = t; }
 void orc_step(orc_t* o, long n) {
   size_t nw = (size_t)o->ne * 3 * o->np;
   for (long it = 0; it < n; ++it) {
-    double* st[4] = {o->wk[0], o->wk[1], o->wk[2], o->wk[3]};
+    double* st[6] = {o->wk[0], o->wk[1], o->wk[2], o->wk[3], o->wk[4], o->wk[5]};
     memcpy(st[0], o->w, sizeof(double) * nw);
     for (int i = 0; i < o->nstage; ++i) {
       double rain, bdry;
@@ -1014,7 +1024,7 @@ double orc_l2_error_exact(const orc_t* o, int var) {
 /* amplification factor of the stepper's Shu-Osher table on y' = lambda y, z = lambda dt */
 double orc_ssp_amplification(int stages, double z) {
   orc_t* o = orc_create(1, 0, stages, 9.81, 0.01, 2, 0.0);
-  double y[4] = {1.0, 0, 0, 0};
+  double y[6] = {1.0, 0, 0, 0, 0, 0};
   for (int i = 0; i < stages; ++i) {
     double s = o->beta[i] * z * y[i];
     for (int j = 0; j <= i; ++j) s += o->alpha[i][j] * y[j];

@@ -330,6 +330,44 @@ def test_ssp_stability_polynomials_are_truncated_taylor_series():
         assert abs(O.ssp_amplification(3, z) - (1 + z + z * z / 2 + z ** 3 / 6)) < 1e-14
 
 
+def test_five_stage_ssp_is_second_order_with_radius_four():
+    """The five-stage scheme: four forward-Euler substeps of dt/4 and a final convex
+    combination.  On y' = z y its amplification agrees with exp(z) through z^2 but not z^3
+    (order exactly 2); it is a polynomial of degree 5 whose z^5 coefficient is the product of
+    the substep weights 4/5 (1/4)^5; and, being a convex combination of forward-Euler steps of
+    dt/4, it is bounded by 1 on the disk |z + 4| <= 4 (SSP coefficient 4)."""
+    R = lambda z: O.ssp_amplification(5, z)
+    for h in (1e-2, 5e-3):
+        assert abs(R(h) - (1 + h + h * h / 2)) < 1.0 * h ** 3    # second order ...
+        assert abs(R(h) - np.exp(h)) > 0.01 * h ** 3              # ... and not third
+    zs = np.linspace(-3.0, 1.0, 9)
+    coef = np.polyfit(zs, [R(z) for z in zs], 5)
+    assert abs(coef[0] - 0.8 / 4 ** 5) < 1e-12 and abs(coef[-1] - 1.0) < 1e-12
+    th = np.linspace(0, 2 * np.pi, 73)
+    for rad in (1.0, 2.0, 3.0, 4.0):
+        for z in -4.0 + rad * np.exp(1j * th):
+            y = [1.0 + 0j]
+            for _ in range(4):
+                y.append(y[-1] * (1 + z / 4))
+            r = 0.2 * y[0] + 0.8 * y[4] * (1 + z / 4)
+            assert abs(r) <= 1.0 + 1e-12
+    for z in np.linspace(-8.0, 0.0, 33):                           # the real section of the disk
+        assert abs(R(z)) <= 1.0 + 1e-12
+    assert abs(R(-8.5)) > 1.0
+
+
+def test_five_stage_ssp_run_conserves_mass_and_keeps_lake_at_rest():
+    w = W.basin_c1(hump=False, rain=True)
+    o = O.from_workload(w, ssp=5)
+    o.step(100)
+    st = o.state()
+    led = o.ledger()
+    assert led["rel_err"] < 1e-14
+    assert np.abs(st[:, 1:]).max() < 1e-11                         # rain on a lake: no flow
+    # element mean of zeta = mode 0 times the constant basis value: rain R t everywhere
+    assert np.abs(st[:, 0, 0] * O.basis(1, -1 / 3, -1 / 3)[0][0] - 50.0 / 3.6e6 * led["t"]).max() < 1e-12
+
+
 # -------------------------------------------------------------------- hand-made RHS --
 def _two_triangles():
     xy = np.array([[0.0, 0.0], [1000.0, 0.0], [1000.0, 800.0], [0.0, 800.0]])
