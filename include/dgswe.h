@@ -60,8 +60,11 @@ typedef struct dgswe_ctx* dgswe_h;
 /* Run parameters (Sec. 2.2-2.4, Sec. 3).
  *   p           polynomial degree 1 or 2 (Eq. dubiner);
  *   flux        DGSWE_FLUX_ROE or DGSWE_FLUX_LLF;
- *   ssp_stages  2 or 3: SSP(2,2) or SSP(3,3) in Shu-Osher form (Sec. 2.2; order p+1 is the
- *               usual choice);
+ *   ssp_stages  2, 3 or 5: SSP(2,2) or SSP(3,3) in Shu-Osher form (Sec. 2.2; order p+1 is the
+ *               usual choice), or the five-stage second-order SSP(5,2) (four forward-Euler
+ *               substeps of dt/4, then w = w^n/5 + 4/5 (w4 + dt/4 L(w4)); SSP coefficient 4,
+ *               so CFL numbers up to four times those of SSP(2,2) keep its stability bound)
+ *               for the five-stage runs of Sec. 3;
  *   precision   DGSWE_FP64 (every operation in double) or DGSWE_MIXED (FP32 bulk; float-float
  *               element means; FP64 for the depth test near H0 and the global ledger);
  *   g           gravity [m/s^2];  H0 thin-layer depth threshold [m] (Sec. 2.4);

@@ -191,6 +191,11 @@ static std::vector<Stage> ssp_table(int s) {
   std::vector<Stage> t;
   if (s == 2) {
     t = {{0.0, 1.0, 1.0, 0.0, 0}, {0.5, 0.5, 0.5, 1.0, 0}};
+  } else if (s == 5) {
+    // optimal five-stage second-order SSP: four forward-Euler substeps of dt/4, then a convex
+    // combination with w^n
+    t = {{0.0, 1.0, 0.25, 0.0, 0}, {0.0, 1.0, 0.25, 0.25, 0}, {0.0, 1.0, 0.25, 0.5, 0},
+         {0.0, 1.0, 0.25, 0.75, 0}, {0.2, 0.8, 0.2, 1.0, 0}};
   } else {
     t = {{0.0, 1.0, 1.0, 0.0, 0}, {0.75, 0.25, 0.25, 1.0, 0}, {1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, 0.5, 0}};
   }
@@ -509,9 +514,10 @@ static StageArgs<Pol> make_args(dgswe_h h, int stage, int tune) {
   std::memset(&a, 0, sizeof a);
   const int S = (int)h->stages.size();
   const Stage& st = h->stages[stage];
-  a.in = h->rec[stage].as<uint4>();
+  // rec[0] holds w^n (and receives the step's result); stage outputs alternate in rec[1], rec[2]
+  a.in = h->rec[stage == 0 ? 0 : 1 + (stage - 1) % 2].as<uint4>();
   a.wn = h->rec[0].as<uint4>();
-  a.out = (stage == S - 1) ? h->rec[0].as<uint4>() : h->rec[stage + 1].as<uint4>();
+  a.out = (stage == S - 1) ? h->rec[0].as<uint4>() : h->rec[1 + stage % 2].as<uint4>();
   a.nbr = h->nbr.as<int4>();
   a.geo = h->geo.as<uint4>();
   a.nodes = h->nodes.as<int4>();
@@ -757,7 +763,8 @@ int dgswe_set_params(dgswe_h h, const dgswe_params* p) {
   if (!p) return fail(DGSWE_EINVAL, "null params");
   if (p->p < 1 || p->p > 2) return fail(DGSWE_EINVAL, "p = %d: the device path supports p = 1 and p = 2", p->p);
   if (p->flux != DGSWE_FLUX_ROE && p->flux != DGSWE_FLUX_LLF) return fail(DGSWE_EINVAL, "unknown flux %d", p->flux);
-  if (p->ssp_stages != 2 && p->ssp_stages != 3) return fail(DGSWE_EINVAL, "ssp_stages must be 2 or 3");
+  if (p->ssp_stages != 2 && p->ssp_stages != 3 && p->ssp_stages != 5)
+    return fail(DGSWE_EINVAL, "ssp_stages must be 2, 3 or 5");
   if (p->precision != DGSWE_FP64 && p->precision != DGSWE_MIXED) return fail(DGSWE_EINVAL, "unknown precision");
   if (!(p->g > 0) || !(p->H0 > 0)) return fail(DGSWE_EINVAL, "g and H0 must be positive");
   if (p->friction < 0 || p->friction > 2) return fail(DGSWE_EINVAL, "unknown friction law");

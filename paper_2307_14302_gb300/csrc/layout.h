@@ -24,6 +24,7 @@ namespace dg {
 
 constexpr int MAXSEG = 8;   // tidal segments: ocean edge code -2 - seg
 constexpr int MAXRIV = 8;   // river segments: river edge code -2 - MAXSEG - seg
+constexpr int MAXSTAGE = 5; // Runge-Kutta stages
 constexpr int MAXNP = 6;
 constexpr int MAXNQ = 7;
 constexpr int MAXNG = 3;
@@ -77,9 +78,9 @@ struct ForcingT {
 // per-scenario parameters (device array; an ensemble holds several)
 struct ScenDev {
   double t0, dt;
-  float bdt_hi[3], bdt_lo[3];      // beta_s * dt of each Shu-Osher stage, float-float
-  double bdt[3];                   // same in double
-  double bw[3];                    // weight of stage s in the final combination (ledger)
+  float bdt_hi[MAXSTAGE], bdt_lo[MAXSTAGE];  // beta_s * dt of each Shu-Osher stage, float-float
+  double bdt[MAXSTAGE];            // same in double
+  double bw[MAXSTAGE];             // weight of stage s in the final combination (ledger)
   int32_t elem_begin, elem_end;
   int32_t rain_kind;               // 0 none, 1 constant per element, 2 storm, 3 grid
   int32_t gnx, gny, gnt;
