@@ -112,7 +112,8 @@ struct dgswe_ctx {
   int np = 0, rv = 0, gv = 0;      // modes, record and geometry sizes (16-byte units)
   long long E = 0, N = 0;          // padded element count, node count
   std::vector<long long> eoff, noff;
-  DevBuf rec[3], nbr, geo, nodes, node_xy, xy64, hbn, rain_e, scen, tile_scen, ledger, ctl, eorig, grids, rivers, scratch,
+  DevBuf rec[3], nbr, geo, nodes, node_xy, xy64, hbn, rain_e, rain_node, node_scen, scen, tile_scen, ledger, ctl, eorig,
+      grids, rivers, scratch,
       gather_buf, edges, slots;
   long long nedges = 0;
   int ntiles = 0;                          // 32-element tiles
@@ -125,6 +126,8 @@ struct dgswe_ctx {
   int block = 128, waves = 1, split = 1;
   bool autotune = true;
   bool graphs = true;  // replay steps from CUDA graphs (else direct launches)
+  bool grid_rain = false;  // some scenario has gridded rain: a node kernel runs before each stage
+  long long nn_total = 0;
   int grid = 0;
   cudaGraphExec_t g1 = nullptr, gK = nullptr;
   int K = 8;
@@ -133,7 +136,8 @@ struct dgswe_ctx {
   ~dgswe_ctx() {
     DeviceGuard dg_(device);
     DevBuf* bufs[] = {&rec[0], &rec[1], &rec[2], &nbr, &geo, &nodes, &node_xy, &xy64, &hbn, &rain_e, &scen,
-                      &tile_scen, &ledger, &ctl, &eorig, &grids, &rivers, &scratch, &gather_buf, &edges, &slots};
+                      &tile_scen, &ledger, &ctl, &eorig, &grids, &rivers, &scratch, &gather_buf, &edges, &slots,
+                      &rain_node, &node_scen};
     for (DevBuf* b : bufs) b->alloc(0);
     if (g1) cudaGraphExecDestroy(g1);
     if (gK) cudaGraphExecDestroy(gK);
@@ -260,6 +264,7 @@ static int build_layout(dgswe_h h) {
   std::vector<uint32_t> rec(rw * E, 0u), geo(gw * E, 0u);
   std::vector<int32_t> nbr(4 * E, -1), nodes(4 * E, 0), eorig(E, 0);
   std::vector<double> xy64(2 * N), hbn(N);
+  std::vector<int32_t> nscen(N, 0);
   std::vector<float> xyf(mx ? 2 * N : 0), rainf(mx ? E : 0);
   std::vector<double> rain64(mx ? 0 : E);
   std::vector<float> grids;
@@ -271,6 +276,7 @@ static int build_layout(dgswe_h h) {
     const HostMesh& M = S.m;
     const long long eo = h->eoff[s], no = h->noff[s];
     for (int i = 0; i < M.nn; ++i) {
+      nscen[no + i] = (int32_t)s;
       xy64[2 * (no + i)] = M.x[i];
       xy64[2 * (no + i) + 1] = M.y[i];
       hbn[no + i] = S.hb[i];
@@ -385,7 +391,8 @@ static int build_layout(dgswe_h h) {
       h->xy64.alloc(16 * (size_t)N) || h->hbn.alloc(8 * (size_t)N) || h->eorig.alloc(4 * (size_t)E) ||
       h->node_xy.alloc(mx ? 8 * (size_t)N : 16 * (size_t)N) || h->rain_e.alloc(mx ? 4 * (size_t)E : 8 * (size_t)E) ||
       h->ctl.alloc(sizeof(Ctl)) || h->scen.alloc(sizeof(ScenDev) * ns) || h->grids.alloc(4 * grids.size()) ||
-      h->rivers.alloc(8 * rivers.size()) ||
+      h->rivers.alloc(8 * rivers.size()) || h->node_scen.alloc(4 * (size_t)N) ||
+      h->rain_node.alloc((mx ? 4 : 8) * (size_t)N) ||
       h->scratch.alloc(sizeof(double) * 4 * 4096))
     return fail(DGSWE_ENOMEM, "device allocation failed");
   CU(cudaMemcpy(h->rec[0].p, rec.data(), rbytes, cudaMemcpyHostToDevice));
@@ -406,6 +413,11 @@ static int build_layout(dgswe_h h) {
   }
   if (!grids.empty()) CU(cudaMemcpy(h->grids.p, grids.data(), 4 * grids.size(), cudaMemcpyHostToDevice));
   if (!rivers.empty()) CU(cudaMemcpy(h->rivers.p, rivers.data(), 8 * rivers.size(), cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(h->node_scen.p, nscen.data(), 4 * (size_t)N, cudaMemcpyHostToDevice));
+  CU(cudaMemset(h->rain_node.p, 0, (mx ? 4 : 8) * (size_t)N));
+  h->nn_total = N;
+  h->grid_rain = false;
+  for (size_t s = 0; s < ns; ++s) h->grid_rain = h->grid_rain || h->sc[s].rain_kind == 3;
   CU(cudaMemset(h->ctl.p, 0, sizeof(Ctl)));
   // per-scenario parameter blocks (dt filled in later)
   std::vector<ScenDev> sd(ns);
@@ -524,6 +536,8 @@ static StageArgs<Pol> make_args(dgswe_h h, int stage, int tune) {
   a.node_xy = h->node_xy.as<T>();
   a.hb_nodal = h->hbn.as<double>();
   a.rain_e = h->rain_e.as<T>();
+  a.rain_node = h->rain_node.as<T>();
+  a.node_scen = h->node_scen.as<int32_t>();
   a.scen = h->scen.as<ScenDev>();
   a.tile_scen = h->tile_scen.as<int32_t>();
   a.ledger = h->ledger.as<double>();
@@ -562,6 +576,12 @@ static int edge_grid(dgswe_h h) {
 static int launch_stage_once(dgswe_h h, int stage, int tune, cudaStream_t s) {
   const int grid = h->grid;
   cudaError_t e = cudaSuccess;
+  if (h->grid_rain) {  // nodal gridded rain at this stage's time
+    e = mixed(h) ? launch_node_rain<Mixed>(make_args<Mixed>(h, stage, tune), h->nn_total, s)
+                 : launch_node_rain<Fp64>(make_args<Fp64>(h, stage, tune), h->nn_total, s);
+    if (e != cudaSuccess) return fail(DGSWE_ECUDA, "node rain launch: %s", cudaGetErrorString(e));
+    h->launches++;
+  }
   if (h->split && h->nedges > 0) {
     if (mixed(h)) e = launch_edges<Mixed>(h->prm.p, h->prm.flux, make_args<Mixed>(h, stage, tune), edge_grid(h), 256, s);
     else e = launch_edges<Fp64>(h->prm.p, h->prm.flux, make_args<Fp64>(h, stage, tune), edge_grid(h), 256, s);
@@ -575,7 +595,7 @@ static int launch_stage_once(dgswe_h h, int stage, int tune, cudaStream_t s) {
   return 0;
 }
 
-static int launches_per_stage(dgswe_h h) { return (h->split && h->nedges > 0) ? 2 : 1; }
+static int launches_per_stage(dgswe_h h) { return 1 + ((h->split && h->nedges > 0) ? 1 : 0) + (h->grid_rain ? 1 : 0); }
 
 static int occupancy(dgswe_h h, int block) {
   return mixed(h) ? stage_blocks_per_sm<Mixed>(h->prm.p, h->prm.flux, block, h->split)

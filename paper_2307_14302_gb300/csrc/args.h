@@ -34,6 +34,8 @@ struct StageArgs {
   const T* node_xy;        // [2 * nodes] coordinates (rain, pressure set-up)
   const double* hb_nodal;  // [nodes] FP64 bathymetry (depth test near H0)
   const T* rain_e;         // [elements] constant element rain (rain_kind 1)
+  T* rain_node;            // [nodes] gridded rain at the stage time (rain_kind 3), node kernel output
+  const int32_t* node_scen;  // [nodes] scenario of each node
   const ScenDev* scen;
   const int32_t* tile_scen;  // scenario of each 32-element tile
   double* ledger;          // [scenario][wslots][2]: rain volume, boundary inflow volume per warp
@@ -74,6 +76,9 @@ cudaError_t launch_edges(int p, int flux, const StageArgs<Pol>& a, int grid, int
 // positive-depth operator on records [begin, end) in place (a.in == a.out)
 template <class Pol>
 cudaError_t launch_prepare(int p, const StageArgs<Pol>& a, long long begin, long long end, cudaStream_t s);
+// gridded rain (rain_kind 3) interpolated to every node at the stage time: a.rain_node[0, nn)
+template <class Pol>
+cudaError_t launch_node_rain(const StageArgs<Pol>& a, long long nn, cudaStream_t s);
 // partial FP64 sums of A*mean(zeta) and A*mean(H) over [begin, end): partials[4*block]
 template <class Pol>
 cudaError_t launch_volume(int p, const uint4* rec, const uint4* geo, long long begin, long long end,

@@ -875,6 +875,47 @@ __global__ void __launch_bounds__(256) edge_kernel(const StageArgs<Pol> a) {
   }
 }
 
+// gridded rain (mm/h records, bilinear in space, linear in time, clamped to the grid) at a
+// point and time, in m/s (Sec. 2.5)
+template <class T>
+__device__ __forceinline__ T grid_rain(const ScenDev& S, const ForcingT<T>& F, T px, T py, T t) {
+  T gx = (px - F.grid[0]) * F.grid[2], gy = (py - F.grid[1]) * F.grid[3];
+  T gt = (t - F.grid[4]) * F.grid[5];
+  gx = fmin(fmax(gx, T(0)), T(S.gnx - 1));
+  gy = fmin(fmax(gy, T(0)), T(S.gny - 1));
+  gt = fmin(fmax(gt, T(0)), T(S.gnt - 1));
+  const int ix = min(max((int)floor(gx), 0), max(S.gnx - 2, 0));
+  const int iy = min(max((int)floor(gy), 0), max(S.gny - 2, 0));
+  const int it = min(max((int)floor(gt), 0), max(S.gnt - 2, 0));
+  const T fx = gx - T(ix), fy = gy - T(iy), ft = gt - T(it);
+  const int ix1 = S.gnx > 1 ? ix + 1 : ix, iy1 = S.gny > 1 ? iy + 1 : iy;
+  T val[2];
+#pragma unroll
+  for (int qq = 0; qq < 2; ++qq) {
+    const int kk = S.gnt > 1 ? it + qq : 0;
+    const float* Gr = S.grid + (size_t)kk * S.gnx * S.gny;
+    const T v00 = Gr[(size_t)iy * S.gnx + ix], v10 = Gr[(size_t)iy * S.gnx + ix1];
+    const T v01 = Gr[(size_t)iy1 * S.gnx + ix], v11 = Gr[(size_t)iy1 * S.gnx + ix1];
+    val[qq] = (T(1) - fy) * ((T(1) - fx) * v00 + fx * v10) + fy * ((T(1) - fx) * v01 + fx * v11);
+  }
+  return ((T(1) - ft) * val[0] + ft * val[1]) * T(1.0 / 3.6e6);
+}
+
+// node kernel: the gridded rain of every node at this stage's time, once per node instead of
+// once per (element, vertex)
+template <class Pol>
+__global__ void __launch_bounds__(256) node_rain_kernel(const StageArgs<Pol> a, long long nn) {
+  using T = typename Pol::T;
+  const T stepc = (T)a.ctl->step + (sizeof(T) == 4 ? (T)a.cst_f : (T)a.cst);
+  for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < nn; n += (long long)gridDim.x * blockDim.x) {
+    const ScenDev& S = a.scen[a.node_scen[n]];
+    if (S.rain_kind != 3) continue;
+    const ForcingT<T>& F = forcing<T>(S);
+    const T t = F.t0 + stepc * F.dt;
+    a.rain_node[n] = grid_rain<T>(S, F, a.node_xy[2 * n], a.node_xy[2 * n + 1], t);
+  }
+}
+
 // ------------------------------------------------------------------------ stage kernel ----
 // Work split: 32-element tiles, warp w of the launch takes tiles w, w + W, w + 2W, ... (W warps
 // in the grid).  No block-wide barrier inside the loop; rain and boundary volumes accumulate per
@@ -1098,38 +1139,21 @@ __global__ void DG_STAGE_BOUNDS stage_kernel(const StageArgs<Pol> a) {
       Re = a.rain_e[e];
     } else if (S.rain_kind >= 2) {
       T acc = 0;
+      if (S.rain_kind == 2) {  // radial storm profile at the three vertices
 #pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const long long n = (i == 0) ? nd.x : (i == 1 ? nd.y : nd.z);
-        const T px = a.node_xy[2 * n], py = a.node_xy[2 * n + 1];
-        if (S.rain_kind == 2) {
+        for (int i = 0; i < 3; ++i) {
+          const long long n = (i == 0) ? nd.x : (i == 1 ? nd.y : nd.z);
+          const T px = a.node_xy[2 * n], py = a.node_xy[2 * n + 1];
           const T tt = t - F.storm[7];
           const T dx = px - (F.storm[0] + F.storm[2] * tt), dy = py - (F.storm[1] + F.storm[3] * tt);
           const T r = fsqrt0(dx * dx + dy * dy);
           const T rp = F.storm[4], rm = F.storm[5], re = F.storm[6];
           acc += (r < rm) ? rp * (T(0.5) + T(0.5) * fdiv(r, rm)) : rp * fexp(-fdiv(r - rm, re));
-        } else {
-          T gx = (px - F.grid[0]) * F.grid[2], gy = (py - F.grid[1]) * F.grid[3];
-          T gt = (t - F.grid[4]) * F.grid[5];
-          gx = fmin(fmax(gx, T(0)), T(S.gnx - 1));
-          gy = fmin(fmax(gy, T(0)), T(S.gny - 1));
-          gt = fmin(fmax(gt, T(0)), T(S.gnt - 1));
-          const int ix = min(max((int)floor(gx), 0), max(S.gnx - 2, 0));
-          const int iy = min(max((int)floor(gy), 0), max(S.gny - 2, 0));
-          const int it = min(max((int)floor(gt), 0), max(S.gnt - 2, 0));
-          const T fx = gx - T(ix), fy = gy - T(iy), ft = gt - T(it);
-          const int ix1 = S.gnx > 1 ? ix + 1 : ix, iy1 = S.gny > 1 ? iy + 1 : iy;
-          T val[2];
-#pragma unroll
-          for (int qq = 0; qq < 2; ++qq) {
-            const int kk = S.gnt > 1 ? it + qq : 0;
-            const float* Gr = S.grid + (size_t)kk * S.gnx * S.gny;
-            const T v00 = Gr[(size_t)iy * S.gnx + ix], v10 = Gr[(size_t)iy * S.gnx + ix1];
-            const T v01 = Gr[(size_t)iy1 * S.gnx + ix], v11 = Gr[(size_t)iy1 * S.gnx + ix1];
-            val[qq] = (T(1) - fy) * ((T(1) - fx) * v00 + fx * v10) + fy * ((T(1) - fx) * v01 + fx * v11);
-          }
-          acc += ((T(1) - ft) * val[0] + ft * val[1]) * T(1.0 / 3.6e6);
         }
+      } else {  // gridded: nodal rates interpolated by the node kernel of this stage
+        acc = a.rain_node[nd.x];
+        acc += a.rain_node[nd.y];
+        acc += a.rain_node[nd.z];
       }
       Re = acc * T(1.0 / 3.0);
     }
@@ -1584,6 +1608,11 @@ static inline int grid_for(long long n, int block) {
     int g = grid_for(e - b, 256);                                                                            \
     if (p == 1) prepare_kernel<1, POL><<<g, 256, 0, s>>>(a, b, e);                                           \
     else prepare_kernel<2, POL><<<g, 256, 0, s>>>(a, b, e);                                                  \
+    return cudaGetLastError();                                                                               \
+  }                                                                                                          \
+  template <>                                                                                                \
+  cudaError_t launch_node_rain<POL>(const StageArgs<POL>& a, long long nn, cudaStream_t s) {                 \
+    node_rain_kernel<POL><<<grid_for(nn, 256), 256, 0, s>>>(a, nn);                                          \
     return cudaGetLastError();                                                                               \
   }                                                                                                          \
   template <>                                                                                                \
