@@ -146,6 +146,8 @@ def _tag_rect(xy, bedge, lx, ly, ocean_side):
         ocean = mid[:, 0] < tol
     elif ocean_side == "y0":
         ocean = mid[:, 1] < tol
+    elif ocean_side == "x1":
+        ocean = mid[:, 0] > lx - tol
     else:
         raise ValueError(ocean_side)
     btype = np.where(ocean, OCEAN, LAND).astype(np.int32)
@@ -401,6 +403,45 @@ def river_basin(q=(2.0, 0.5), ramp_s=600.0, nx=20, ny=10, wet=True, seed=7) -> W
     w.river = River(q=tq, t0=0.0, dt=ramp_s / 4.0)
     w.name = f"river-basin-{m.n_tri}tri-p1"
     return w
+
+
+def inclined_plane(condition="A", duration=10.0, nx=240, ny=2, h0=1e-4, sim_s=86.4) -> Workload:
+    """Rain on an initially dry inclined flume, after the set-up of Sec. 3.2: 24 m long, 19.6 cm
+    wide; condition A: slope sin(theta) = 0.015, rain 0.0833 cm/s; condition B: three 8 m
+    segments (top to bottom) with slopes 0.020, 0.015, 0.010 and rain 0.1080, 0.0638, 0.0800
+    cm/s.  Rain falls for ``duration`` seconds (10, 20 or 30), Manning n = 0.009, dt = 1 ms.
+    The flume walls are land; its downstream end (x = 24 m, bed at the geoid) is an open
+    boundary held at the bed level (free outfall).  Mesh: nx x ny squares, mirrored about the
+    flume axis.  The rain is a gridded field (5 cm cells, records every 0.1 s) so that it stops
+    within one record after ``duration``."""
+    lx, ly = 24.0, 0.196
+    mesh = structured_mesh(lx, ly, nx, ny, mirror=True, ocean_side="x1")
+    x = mesh.xy[:, 0]
+    if condition == "A":
+        slope = lambda xx: np.full_like(xx, 0.015)
+        rate = lambda xx: np.full_like(xx, 0.0833e-2)
+    else:
+        slope = lambda xx: np.where(xx < 8.0, 0.020, np.where(xx < 16.0, 0.015, 0.010))
+        rate = lambda xx: np.where(xx < 8.0, 0.1080e-2, np.where(xx < 16.0, 0.0638e-2, 0.0800e-2))
+    # bed elevation above the outlet: integral of the slope from x to the downstream end
+    xf = np.linspace(0.0, lx, 24001)
+    zf = np.concatenate([[0.0], np.cumsum(0.5 * (slope(xf[1:]) + slope(xf[:-1])) * np.diff(xf))])
+    zf = zf[-1] - zf
+    hb = -np.interp(x, xf, zf)
+    zeta0 = _initial_dry(hb, h0)
+    gdx, gdt = 0.05, 0.1
+    gx = np.arange(0.0, lx + 1e-9, gdx)
+    nt = int(np.ceil(sim_s / gdt)) + 1
+    tr = np.arange(nt) * gdt
+    on = (tr <= duration + 1e-9).astype(np.float64)
+    field = (on[:, None, None] * rate(gx)[None, None, :] * 3.6e6 * np.ones((1, 2, 1))).astype(np.float32)
+    grid = RainGrid(len(gx), 2, nt, 0.0, 0.0, gdx, ly, 0.0, gdt, field)
+    tide = Tide(np.array([0.0]), np.array([3600.0]), np.array([0.0]))
+    return Workload(
+        name=f"plane-{condition}-{int(duration)}s", mesh=mesh, hb=hb, manning=np.full(mesh.n_tri, 0.009),
+        zeta0=zeta0, p=1, steps=int(round(sim_s / 1e-3)), cfl=0.0, rain_grid=grid, tide=tide, h0=h0,
+        meta={"dt": 1e-3, "condition": condition, "duration": duration},
+    )
 
 
 def bathtub(nx=25, ny=4) -> Workload:

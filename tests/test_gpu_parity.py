@@ -271,6 +271,24 @@ def test_river_boundaries_match_oracle(prec, wet):
     assert np.array_equal(dev.dry(), ref.dry())
 
 
+# ---------------------------------------------------------- rain on a flume (Sec. 3.2) --
+@pytest.mark.parametrize("prec", [D.FP64, D.MIXED])
+def test_inclined_plane_runoff_matches_oracle(prec):
+    """Initially dry flume (condition B: three slopes and rain rates, H0 = 0.1 mm), gridded rain
+    stopping after 1 s, free outfall: 1500 steps of 1 ms against the oracle."""
+    w = W.inclined_plane("B", duration=1.0)
+    ref, dev = _pair(w, 1500, prec, dt=1e-3)
+    got, want = dev.state(), ref.state()
+    if prec == D.FP64:
+        assert _fp64_err(got, want) <= FP64_TOL
+    else:
+        ez, eq = _mixed_err(got, want)
+        assert ez <= MIXED_TOL and eq <= MIXED_TOL, (ez, eq)
+    led, rl = dev.ledger(), ref.ledger()
+    assert abs(led["V"] - led["V0"] - led["rain_in"] - led["bdry_in"]) < 1e-12
+    assert abs(led["bdry_in"] - rl["bdry_in"]) <= 1e-6 * abs(rl["rain_in"])
+
+
 # -------------------------------------------------------------------- forcing paths ------
 @pytest.mark.parametrize("prec", [D.FP64, D.MIXED])
 def test_gridded_rain_and_pressure_setup(prec):
