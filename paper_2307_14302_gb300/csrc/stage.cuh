@@ -446,6 +446,69 @@ __device__ __forceinline__ void edge_flux(const Trace<T>& L, const Trace<T>& R, 
   fy = cy - T(0.5) * D2;
 }
 
+#ifndef DG_PACKED_FLUX
+#define DG_PACKED_FLUX 1  // FP32 path, p = 1: both Gauss points of an edge in packed FP32x2 arithmetic
+#endif
+
+// packed FP32x2 arithmetic (two edge points per instruction)
+using f2 = float2;
+__device__ __forceinline__ f2 p2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ f2 add2(f2 a, f2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ f2 neg2(f2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) { return __fadd2_rn(a, neg2(b)); }
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ f2 max2(f2 a, f2 b) { return make_float2(fmaxf(a.x, b.x), fmaxf(a.y, b.y)); }
+__device__ __forceinline__ f2 abs2(f2 a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
+__device__ __forceinline__ f2 rcp2(f2 a) { return make_float2(frcp(a.x), frcp(a.y)); }
+__device__ __forceinline__ f2 sqrt2(f2 a) { return make_float2(fsqrt_pos(a.x), fsqrt_pos(a.y)); }
+struct Trace2 {
+  f2 d, H, qx, qy;  // two edge points
+};
+
+// edge_flux for two points at once (FP32): the same flux, written with packed operations
+template <int FLUX>
+__device__ __forceinline__ void edge_flux_pair(const Trace2& L, const Trace2& R, f2 dcRL, f2 nx, f2 ny, float g,
+                                               float H0, f2& fz, f2& fx, f2& fy) {
+  const f2 half = p2(0.5f), mhalf = p2(-0.5f);
+  const f2 HsL = max2(L.H, p2(H0)), HsR = max2(R.H, p2(H0));
+  const f2 iL = rcp2(HsL), iR = rcp2(HsR);
+  const f2 uL = mul2(L.qx, iL), vL = mul2(L.qy, iL), uR = mul2(R.qx, iR), vR = mul2(R.qy, iR);
+  const f2 unL = fma2(uL, nx, mul2(vL, ny)), unR = fma2(uR, nx, mul2(vR, ny));
+  const f2 mL = fma2(L.qx, nx, mul2(L.qy, ny)), mR = fma2(R.qx, nx, mul2(R.qy, ny));
+  const f2 dz = add2(sub2(R.d, L.d), dcRL);
+  const f2 dqx = sub2(R.qx, L.qx), dqy = sub2(R.qy, L.qy);
+  const f2 cx = mul2(half, fma2(L.qx, unL, mul2(R.qx, unR)));
+  const f2 cy = mul2(half, fma2(L.qy, unL, mul2(R.qy, unR)));
+  const f2 cz = mul2(half, add2(mL, mR));
+  if (FLUX == 1) {  // local Lax-Friedrichs
+    const f2 gg = p2(g);
+    const f2 lam = max2(add2(abs2(unL), sqrt2(mul2(gg, HsL))), add2(abs2(unR), sqrt2(mul2(gg, HsR))));
+    const f2 hl = mul2(mhalf, lam);
+    fz = fma2(hl, dz, cz);
+    fx = fma2(hl, dqx, cx);
+    fy = fma2(hl, dqy, cy);
+    return;
+  }
+  // Roe: averages (arithmetic depth, sqrt-depth-weighted velocity), eigen-decomposition
+  const f2 sL = sqrt2(HsL), sR = sqrt2(HsR);
+  const f2 is = rcp2(add2(sL, sR));
+  const f2 ut = mul2(fma2(sL, uL, mul2(sR, uR)), is), vt = mul2(fma2(sL, vL, mul2(sR, vR)), is);
+  const f2 c = sqrt2(mul2(p2(0.5f * g), add2(HsL, HsR)));
+  const f2 ic = rcp2(c);
+  const f2 utn = fma2(ut, nx, mul2(vt, ny)), utt = fma2(vt, nx, mul2(neg2(ut), ny));
+  const f2 dqn = fma2(dqx, nx, mul2(dqy, ny)), dqt = fma2(dqy, nx, mul2(neg2(dqx), ny));
+  const f2 w = mul2(fma2(neg2(utn), dz, dqn), ic);
+  const f2 a1 = mul2(half, sub2(dz, w)), a3 = mul2(half, add2(dz, w)), a2 = fma2(neg2(utt), dz, dqt);
+  const f2 l1 = mul2(abs2(sub2(utn, c)), a1), l2 = mul2(abs2(utn), a2), l3 = mul2(abs2(add2(utn, c)), a3);
+  const f2 D0 = add2(l1, l3);
+  const f2 D1 = fma2(l1, fma2(neg2(c), nx, ut), fma2(neg2(l2), ny, mul2(l3, fma2(c, nx, ut))));
+  const f2 D2 = fma2(l1, fma2(neg2(c), ny, vt), fma2(l2, nx, mul2(l3, fma2(c, ny, vt))));
+  fz = fma2(mhalf, D0, cz);
+  fx = fma2(mhalf, D1, cx);
+  fy = fma2(mhalf, D2, cy);
+}
+
 // pressure difference P - P_c with P_c the pressure at the reference elevation c:
 // g/2 (zeta - c)(zeta + c + 2 hb) = g/2 d (2 H - d)
 template <class T>
@@ -1232,12 +1295,27 @@ __global__ void DG_STAGE_BOUNDS stage_kernel(const StageArgs<Pol> a) {
       if (!wall) {
         const T sgn = me_L ? T(1) : T(-1);
         T fzc[NG], fxc[NG], fyc[NG];
+        if constexpr (DG_PACKED_FLUX && P == 1 && sizeof(T) == 4) {
+          const Trace<T> a0 = me_L ? tm[0] : to[0], b0 = me_L ? to[0] : tm[0];
+          const Trace<T> a1 = me_L ? tm[1] : to[1], b1 = me_L ? to[1] : tm[1];
+          const Trace2 L2{make_float2(a0.d, a1.d), make_float2(a0.H, a1.H), make_float2(a0.qx, a1.qx),
+                          make_float2(a0.qy, a1.qy)};
+          const Trace2 R2{make_float2(b0.d, b1.d), make_float2(b0.H, b1.H), make_float2(b0.qx, b1.qx),
+                          make_float2(b0.qy, b1.qy)};
+          f2 fz2, fx2, fy2;
+          edge_flux_pair<FLUX>(L2, R2, p2(dcRL), p2(sgn * nx), p2(sgn * ny), g, H0, fz2, fx2, fy2);
+          fzc[0] = fz2.x; fzc[1] = fz2.y;
+          fxc[0] = fx2.x; fxc[1] = fx2.y;
+          fyc[0] = fy2.x; fyc[1] = fy2.y;
+          if (river) fzc[0] = fzc[1] = -qr;
+        } else {
 #pragma unroll
-        for (int k = 0; k < NG; ++k) {
-          const Trace<T> tL = me_L ? tm[k] : to[k];
-          const Trace<T> tR = me_L ? to[k] : tm[k];
-          edge_flux<FLUX, T>(tL, tR, dcRL, sgn * nx, sgn * ny, g, H0, fzc[k], fxc[k], fyc[k]);
-          if (river) fzc[k] = -qr;  // the specified normal flow is the mass flux
+          for (int k = 0; k < NG; ++k) {
+            const Trace<T> tL = me_L ? tm[k] : to[k];
+            const Trace<T> tR = me_L ? to[k] : tm[k];
+            edge_flux<FLUX, T>(tL, tR, dcRL, sgn * nx, sgn * ny, g, H0, fzc[k], fxc[k], fyc[k]);
+            if (river) fzc[k] = -qr;  // the specified normal flow is the mass flux
+          }
         }
         T ecanon = 0;  // in L's point order: identical bits on both sides of the edge
 #pragma unroll
