@@ -51,6 +51,8 @@ def lib():
         L.orc_set_rain_grid.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int] + [C.c_double] * 6 + [_f]
         L.orc_set_tide.argtypes = [C.c_void_p, C.c_int, _d, _d, _d]
         L.orc_set_river.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_double, _d]
+        L.orc_set_limiter.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double]
+        L.orc_apply_limiter.argtypes = [C.c_void_p]
         L.orc_set_pressure.argtypes = [C.c_void_p] + [C.c_double] * 4
         L.orc_set_exact_wave.argtypes = [C.c_void_p] + [C.c_double] * 5
         L.orc_set_exact_linear.argtypes = [C.c_void_p, _d]
@@ -141,6 +143,12 @@ class Oracle:
 
     def set_tide(self, t):
         lib().orc_set_tide(self.h, len(t.amp), _p(_f64(t.amp)), _p(_f64(t.period)), _p(_f64(t.phase)))
+
+    def set_limiter(self, on=True, nu=1.5, M=0.0):
+        lib().orc_set_limiter(self.h, 1 if on else 0, nu, M)
+
+    def apply_limiter(self):
+        lib().orc_apply_limiter(self.h)
 
     def set_river(self, r):
         q = np.ascontiguousarray(np.atleast_2d(np.asarray(r.q, dtype=np.float64)))

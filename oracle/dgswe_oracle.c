@@ -86,6 +86,9 @@ struct orc {
   double gx0, gy0, gdx, gdy, gt0, gdt;
   float* grid;
   int ntide;
+  int lim_on;            /* optional slope limiter (p = 1) */
+  double lim_nu, lim_M;
+  int* nb3;              /* [ne][3] neighbour across local edge j, -1 on the boundary */
   int nriv, rnt;
   double rt0, rdt;
   double* rq; /* [rnt][nriv] */
@@ -272,7 +275,7 @@ void orc_destroy(orc_t* o) {
   void* ptrs[] = {o->x, o->y, o->tri, o->edn, o->ede, o->edj, o->edt, o->eds, o->order, o->det, o->rx, o->ry,
                   o->sx, o->sy, o->area, o->hb, o->man, o->rain_nodal, o->grid, o->tamp, o->tper, o->tpha,
                   o->w, o->wk[0], o->wk[1], o->wk[2], o->wk[3], o->wk[4], o->wk[5], o->Lw, o->rhs, o->rnode,
-                  o->Re, o->dry, o->rq};
+                  o->Re, o->dry, o->rq, o->nb3};
   for (size_t i = 0; i < sizeof ptrs / sizeof ptrs[0]; ++i) freep(ptrs[i]);
   free(o);
 }
@@ -866,6 +869,126 @@ static int element_positivity(int p, const double phv[3][NPMAX], double H0, cons
   return nd > 0;
 }
 
+/* ------------------------------------------- optional slope limiter (Sec. 2.3 mentions one) ---
+ * The paper offers "an optional slope limiter" for shocks without giving its form.  This is the
+ * TVB minmod moment limiter of Cockburn and Shu for P1 on triangles (J. Comput. Phys. 141,
+ * 1998), applied componentwise to zeta, qx, qy: for edge i of element K with midpoint m_i and
+ * barycentre b_0, write m_i - b_0 = a (b_j - b_0) + c (b_k - b_0) with two neighbour barycentres
+ * and a, c >= 0; compare the P1 deviation d_i = w(m_i) - mean_0 with nu (a (mean_j - mean_0) +
+ * c (mean_k - mean_0)) through minmod (kept when |d_i| <= M h^2); if the limited deviations do
+ * not sum to zero, scale the positive and negative parts to balance; rebuild the linear part
+ * from the midpoint deviations.  Means are untouched.  Limited: wet elements with three
+ * neighbours whose edges all have a valid pair; others are left as they are. */
+void orc_set_limiter(orc_t* o, int on, double nu, double M) {
+  o->lim_on = on;
+  o->lim_nu = nu;
+  o->lim_M = M;
+}
+
+static void build_nb3(orc_t* o) {
+  o->nb3 = (int*)malloc(sizeof(int) * 3 * (size_t)o->ne);
+  for (int k = 0; k < 3 * o->ne; ++k) o->nb3[k] = -1;
+  for (int i = 0; i < o->ned; ++i) {
+    int L = o->ede[2 * i], jL = o->edj[2 * i], R = o->ede[2 * i + 1], jR = o->edj[2 * i + 1];
+    if (o->edt[i] != -1 || R < 0) continue;
+    o->nb3[3 * L + jL] = R;
+    o->nb3[3 * R + jR] = L;
+  }
+}
+
+static double minmod2(double a, double b) {
+  if (a > 0.0 && b > 0.0) return a < b ? a : b;
+  if (a < 0.0 && b < 0.0) return a > b ? a : b;
+  return 0.0;
+}
+
+static void limiter(orc_t* o, double* W) {
+  if (!o->lim_on || o->p != 1) return;
+  if (!o->nb3) build_nb3(o);
+  const int np = o->np, ne = o->ne;
+  const double phi0 = 1.0 / sqrt(2.0);
+  double* out = (double*)malloc(sizeof(double) * (size_t)ne * 3 * np);
+  memcpy(out, W, sizeof(double) * (size_t)ne * 3 * np);
+  /* basis at the three edge midpoints of the reference triangle */
+  double phm[3][NPMAX];
+  for (int i = 0; i < 3; ++i) {
+    double l[3] = {0, 0, 0}, r, s2;
+    l[i] = 0.5;
+    l[(i + 1) % 3] = 0.5;
+    bary_to_rs(l, &r, &s2);
+    orc_basis(o->p, r, s2, phm[i], NULL, NULL);
+  }
+  for (int e = 0; e < ne; ++e) {
+    const int* nb = o->nb3 + 3 * e;
+    if (o->dry[e] || nb[0] < 0 || nb[1] < 0 || nb[2] < 0) continue;
+    const int32_t* vt = o->tri + 3 * e;
+    double bx[4], by[4];
+    bx[0] = (o->x[vt[0]] + o->x[vt[1]] + o->x[vt[2]]) / 3.0;
+    by[0] = (o->y[vt[0]] + o->y[vt[1]] + o->y[vt[2]]) / 3.0;
+    for (int j = 0; j < 3; ++j) {
+      const int32_t* vn = o->tri + 3 * nb[j];
+      bx[j + 1] = (o->x[vn[0]] + o->x[vn[1]] + o->x[vn[2]]) / 3.0;
+      by[j + 1] = (o->y[vn[0]] + o->y[vn[1]] + o->y[vn[2]]) / 3.0;
+    }
+    double h = 0.0;
+    for (int j = 0; j < 3; ++j) {
+      double dx = o->x[vt[(j + 1) % 3]] - o->x[vt[j]], dy = o->y[vt[(j + 1) % 3]] - o->y[vt[j]];
+      double len = sqrt(dx * dx + dy * dy);
+      h = len > h ? len : h;
+    }
+    /* barycentric pairs: neighbour i with one of the other two, coefficients >= 0 */
+    int pj[3], pk[3], ok = 1;
+    double pa[3], pc[3];
+    for (int i = 0; i < 3 && ok; ++i) {
+      double mx = 0.5 * (o->x[vt[i]] + o->x[vt[(i + 1) % 3]]) - bx[0];
+      double my = 0.5 * (o->y[vt[i]] + o->y[vt[(i + 1) % 3]]) - by[0];
+      int found = 0;
+      for (int t = 1; t <= 2 && !found; ++t) {
+        int j = i, k = (i + t) % 3;
+        double ax = bx[j + 1] - bx[0], ay = by[j + 1] - by[0], cx = bx[k + 1] - bx[0], cy = by[k + 1] - by[0];
+        double det = ax * cy - ay * cx;
+        if (det == 0.0) continue;
+        double a = (mx * cy - my * cx) / det, c = (ax * my - ay * mx) / det;
+        if (a >= 0.0 && c >= 0.0) { pj[i] = j; pk[i] = k; pa[i] = a; pc[i] = c; found = 1; }
+      }
+      ok = found;
+    }
+    if (!ok) continue;
+    for (int v = 0; v < 3; ++v) {
+      const double* we = W + ((size_t)e * 3 + v) * np;
+      double m0 = we[0] * phi0, mb[3];
+      for (int j = 0; j < 3; ++j) mb[j] = W[((size_t)nb[j] * 3 + v) * np] * phi0;
+      double d[3], lim[3];
+      int changed = 0;
+      for (int i = 0; i < 3; ++i) {
+        d[i] = we[1] * phm[i][1] + we[2] * phm[i][2];
+        double dm = pa[i] * (mb[pj[i]] - m0) + pc[i] * (mb[pk[i]] - m0);
+        lim[i] = (fabs(d[i]) <= o->lim_M * h * h) ? d[i] : minmod2(d[i], o->lim_nu * dm);
+        if (lim[i] != d[i]) changed = 1;
+      }
+      if (!changed) continue;
+      double sum = lim[0] + lim[1] + lim[2];
+      if (sum != 0.0) {
+        double pos = 0.0, neg = 0.0;
+        for (int i = 0; i < 3; ++i) { pos += lim[i] > 0.0 ? lim[i] : 0.0; neg += lim[i] < 0.0 ? -lim[i] : 0.0; }
+        double tp = pos > 0.0 ? (neg / pos < 1.0 ? neg / pos : 1.0) : 0.0;
+        double tn = neg > 0.0 ? (pos / neg < 1.0 ? pos / neg : 1.0) : 0.0;
+        for (int i = 0; i < 3; ++i) lim[i] = tp * (lim[i] > 0.0 ? lim[i] : 0.0) - tn * (lim[i] < 0.0 ? -lim[i] : 0.0);
+      }
+      /* vertex values of the linear function with midpoint deviations lim (edge i joins
+       * vertices i and i+1): f(v_i) = lim_i + lim_{i-1} - lim_{i+1} */
+      double f[3];
+      for (int i = 0; i < 3; ++i) f[i] = m0 + lim[i] + lim[(i + 2) % 3] - lim[(i + 1) % 3];
+      set_linear_part(o->p, out + ((size_t)e * 3 + v) * np, f);
+    }
+  }
+  memcpy(W, out, sizeof(double) * (size_t)ne * 3 * np);
+  free(out);
+}
+
+static void positivity(orc_t* o, double* W);
+void orc_apply_limiter(orc_t* o) { limiter(o, o->w); }
+
 static void positivity(orc_t* o, double* W) {
   for (int e = 0; e < o->ne; ++e) {
     const int32_t* vt = o->tri + 3 * e;
@@ -991,6 +1114,10 @@ void orc_step(orc_t* o, long n) {
         out[k] = s;
       }
       positivity(o, out);
+      if (o->lim_on) {
+        limiter(o, out);
+        positivity(o, out);
+      }
     }
     memcpy(o->w, st[o->nstage], sizeof(double) * nw);
     o->nstep++;

@@ -37,6 +37,12 @@ void orc_set_tide(orc_t*, int nseg, const double* amp, const double* period, con
  * into the domain) per river segment, nt records from t0 every dt (linear in time, held at the
  * ends; nt = 1: constant).  q is [nt][nseg]. */
 void orc_set_river(orc_t* o, int nseg, int nt, double t0, double dt, const double* q);
+/* Optional slope limiter (p = 1): Cockburn-Shu TVB minmod moment limiter after each stage's
+ * positive-depth operator (then the operator again); nu the minmod weight (1.5), M the TVB
+ * constant (0: TVD). */
+void orc_set_limiter(orc_t*, int on, double nu, double M);
+/* the limiter alone on the current state (test hook) */
+void orc_apply_limiter(orc_t*);
 void orc_set_pressure(orc_t*, double x0, double y0, double sigma, double peak);
 void orc_set_exact_wave(orc_t*, double a, double k, double l, double c, double h0);
 void orc_set_exact_linear(orc_t*, const double* coef9);

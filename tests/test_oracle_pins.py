@@ -368,6 +368,58 @@ def test_five_stage_ssp_run_conserves_mass_and_keeps_lake_at_rest():
     assert np.abs(st[:, 0, 0] * O.basis(1, -1 / 3, -1 / 3)[0][0] - 50.0 / 3.6e6 * led["t"]).max() < 1e-12
 
 
+# --------------------------------------------------------------------- slope limiter --
+def _limiter_oracle(w, state_nodal):
+    o = O.from_workload(w)
+    o.set_state_nodal(*state_nodal)
+    o.set_limiter(True, 1.5, 0.0)
+    return o
+
+
+def test_limiter_keeps_linear_fields_and_means():
+    """For linear data the barycentric neighbour differences reproduce the midpoint deviations
+    exactly, so minmod(d, nu d) = d (nu >= 1): a globally linear state is not touched."""
+    w = W.basin_c1(hump=False, rain=False)
+    x, y = w.mesh.xy[:, 0], w.mesh.xy[:, 1]
+    z = 0.3 + 1e-4 * x - 2e-4 * y
+    o = _limiter_oracle(w, (z, 0.2 + 1e-5 * y, -0.1 + 2e-5 * x))
+    before = o.state()
+    o.apply_limiter()
+    assert np.abs(o.state() - before).max() < 1e-13
+
+
+def test_limiter_flattens_an_isolated_slope_and_keeps_means():
+    w = W.basin_c1(hump=False, rain=False)
+    rng = np.random.default_rng(21)
+    o = O.from_workload(w)
+    st = o.state().copy()                    # lake at rest: means 0, slopes 0
+    e = 200                                  # an interior element
+    st[e, 0, 1:] = [0.05, -0.03]             # a slope between equal neighbour means
+    st[:, 1, 0] += rng.normal(scale=1e-3, size=len(st))
+    o.set_state_modal(st)
+    o.set_limiter(True, 1.5, 0.0)
+    o.apply_limiter()
+    out = o.state()
+    assert np.abs(out[e, 0, 1:]).max() < 1e-15
+    assert np.array_equal(out[:, :, 0], st[:, :, 0])
+
+
+def test_limited_dam_break_is_conservative_and_differs_from_unlimited():
+    w = W.basin_c1(hump=True, rain=True)
+    a = O.from_workload(w)
+    b = O.from_workload(w)
+    b.set_limiter(True, 1.5, 0.0)
+    a.step(100)
+    b.step(100)
+    assert b.ledger()["rel_err"] < 1e-14
+    assert np.isfinite(b.state()).all()
+    assert np.abs(a.state() - b.state()).max() > 1e-6          # the limiter acted
+    # TVD limiting clips extrema: the limited hump's element means stay within the unlimited
+    # run's range of means
+    ma, mb = a.state()[:, 0, 0], b.state()[:, 0, 0]
+    assert ma.min() - 1e-12 <= mb.min() and mb.max() <= ma.max() + 1e-12
+
+
 # -------------------------------------------------------------------- hand-made RHS --
 def _two_triangles():
     xy = np.array([[0.0, 0.0], [1000.0, 0.0], [1000.0, 800.0], [0.0, 800.0]])
