@@ -72,7 +72,13 @@ typedef struct dgswe_ctx* dgswe_h;
  *               with lambda_e = max over vertices of |u| + sqrt(g max(H, H0)) of the state
  *               passed to dgswe_set_state (fixed for the run);
  *   friction    DGSWE_MANNING (tau = g n^2 |u| / H^{4/3}), DGSWE_QUADRATIC (tau = cf |u| / H,
- *               Sec. 3.1) or none;  cf quadratic coefficient. */
+ *               Sec. 3.1) or none;  cf quadratic coefficient;
+ *   limiter     1: the optional slope limiter (Sec. 2.3 offers one for shocks without giving its
+ *               form) as the TVB minmod moment limiter of Cockburn and Shu for P1 triangles,
+ *               applied componentwise after each stage's positive-depth operator and followed
+ *               by the operator again; wet elements with three neighbours only; p = 1 only
+ *               (DGSWE_EINVAL otherwise);  lim_nu its minmod weight (1.5 is usual, >= 1 keeps
+ *               linear data), lim_M its TVB constant (0: TVD). */
 typedef struct {
   int32_t p;
   int32_t flux;
@@ -84,6 +90,9 @@ typedef struct {
   double dt;
   int32_t friction;
   double cf;
+  int32_t limiter;
+  double lim_nu;
+  double lim_M;
 } dgswe_params;
 
 /* Moving radially symmetric rain cell (stand-in for the parametric model of Sec. 2.5):

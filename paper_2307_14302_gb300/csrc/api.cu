@@ -112,8 +112,8 @@ struct dgswe_ctx {
   int np = 0, rv = 0, gv = 0;      // modes, record and geometry sizes (16-byte units)
   long long E = 0, N = 0;          // padded element count, node count
   std::vector<long long> eoff, noff;
-  DevBuf rec[3], nbr, geo, nodes, node_xy, xy64, hbn, rain_e, rain_node, node_scen, scen, tile_scen, ledger, ctl, eorig,
-      grids, rivers, scratch,
+  DevBuf rec[3], nbr, geo, nodes, node_xy, xy64, hbn, rain_e, rain_node, node_scen, lim, scen, tile_scen, ledger, ctl,
+      eorig, grids, rivers, scratch,
       gather_buf, edges, slots;
   long long nedges = 0;
   int ntiles = 0;                          // 32-element tiles
@@ -137,7 +137,7 @@ struct dgswe_ctx {
     DeviceGuard dg_(device);
     DevBuf* bufs[] = {&rec[0], &rec[1], &rec[2], &nbr, &geo, &nodes, &node_xy, &xy64, &hbn, &rain_e, &scen,
                       &tile_scen, &ledger, &ctl, &eorig, &grids, &rivers, &scratch, &gather_buf, &edges, &slots,
-                      &rain_node, &node_scen};
+                      &rain_node, &node_scen, &lim};
     for (DevBuf* b : bufs) b->alloc(0);
     if (g1) cudaGraphExecDestroy(g1);
     if (gK) cudaGraphExecDestroy(gK);
@@ -210,6 +210,66 @@ static std::vector<Stage> ssp_table(int s) {
     for (int k = 0; k < n; ++k) c[i + 1][k] = t[i].a_n * c[0][k] + t[i].a_in * c[i][k] + (k == i ? t[i].beta : 0.0);
   for (int k = 0; k < n; ++k) t[k].bw = c[n][k];
   return t;
+}
+
+// slope limiter data per element (new order): for local edge i the coefficients a_i, c_i >= 0
+// of m_i - b_0 = a_i (b_i - b_0) + c_i (b_k - b_0), k = i+1 (bit i clear) or i+2 (bit i set)
+// trying i+1 first; M h^2 with h the longest edge; pair bits, or -1 when the element has a
+// boundary edge or an edge without such a pair (not limited)
+static std::vector<double> limiter_data(dgswe_h h, long long E) {
+  std::vector<double> L(8 * (size_t)E, 0.0);
+  for (long long e = 0; e < E; ++e) L[8 * e + 7] = -1.0;
+  for (size_t s = 0; s < h->sc.size(); ++s) {
+    const HostMesh& M = h->sc[s].m;
+    const long long eo = h->eoff[s];
+    auto bary = [&](int e, double& x, double& y) {
+      const int32_t* v = &M.tri[3 * (size_t)e];
+      x = (M.x[v[0]] + M.x[v[1]] + M.x[v[2]]) / 3.0;
+      y = (M.y[v[0]] + M.y[v[1]] + M.y[v[2]]) / 3.0;
+    };
+    for (int e = 0; e < M.ne; ++e) {
+      int nb[3];
+      bool interior = true;
+      for (int j = 0; j < 3; ++j) {
+        const int32_t c = M.code[3 * (size_t)e + j];
+        interior = interior && c >= 0;
+        nb[j] = c >= 0 ? (c >> 2) : -1;
+      }
+      if (!interior) continue;
+      const int32_t* v = &M.tri[3 * (size_t)e];
+      double bx[4], by[4];
+      bary(e, bx[0], by[0]);
+      for (int j = 0; j < 3; ++j) bary(nb[j], bx[j + 1], by[j + 1]);
+      double hmax = 0.0;
+      for (int j = 0; j < 3; ++j)
+        hmax = std::max(hmax, std::hypot(M.x[v[(j + 1) % 3]] - M.x[v[j]], M.y[v[(j + 1) % 3]] - M.y[v[j]]));
+      double* out = &L[8 * (size_t)(eo + e)];
+      int bits = 0;
+      bool ok = true;
+      for (int i = 0; i < 3 && ok; ++i) {
+        const double mx = 0.5 * (M.x[v[i]] + M.x[v[(i + 1) % 3]]) - bx[0];
+        const double my = 0.5 * (M.y[v[i]] + M.y[v[(i + 1) % 3]]) - by[0];
+        bool found = false;
+        for (int t = 1; t <= 2 && !found; ++t) {
+          const int k = (i + t) % 3;
+          const double ax = bx[i + 1] - bx[0], ay = by[i + 1] - by[0], cx = bx[k + 1] - bx[0], cy = by[k + 1] - by[0];
+          const double det = ax * cy - ay * cx;
+          if (det == 0.0) continue;
+          const double a = (mx * cy - my * cx) / det, c = (ax * my - ay * mx) / det;
+          if (a >= 0.0 && c >= 0.0) {
+            out[2 * i] = a;
+            out[2 * i + 1] = c;
+            if (t == 2) bits |= 1 << i;
+            found = true;
+          }
+        }
+        ok = found;
+      }
+      out[6] = h->prm.lim_M * hmax * hmax;
+      out[7] = ok ? (double)bits : -1.0;
+    }
+  }
+  return L;
 }
 
 static int check_handle(dgswe_h h) {
@@ -415,6 +475,16 @@ static int build_layout(dgswe_h h) {
   if (!rivers.empty()) CU(cudaMemcpy(h->rivers.p, rivers.data(), 8 * rivers.size(), cudaMemcpyHostToDevice));
   CU(cudaMemcpy(h->node_scen.p, nscen.data(), 4 * (size_t)N, cudaMemcpyHostToDevice));
   CU(cudaMemset(h->rain_node.p, 0, (mx ? 4 : 8) * (size_t)N));
+  if (h->prm.limiter) {
+    std::vector<double> limd = limiter_data(h, E);
+    if (h->lim.alloc((mx ? 4 : 8) * limd.size())) return fail(DGSWE_ENOMEM, "device allocation failed");
+    if (mx) {
+      std::vector<float> lf(limd.begin(), limd.end());
+      CU(cudaMemcpy(h->lim.p, lf.data(), 4 * lf.size(), cudaMemcpyHostToDevice));
+    } else {
+      CU(cudaMemcpy(h->lim.p, limd.data(), 8 * limd.size(), cudaMemcpyHostToDevice));
+    }
+  }
   h->nn_total = N;
   h->grid_rain = false;
   for (size_t s = 0; s < ns; ++s) h->grid_rain = h->grid_rain || h->sc[s].rain_kind == 3;
@@ -537,6 +607,8 @@ static StageArgs<Pol> make_args(dgswe_h h, int stage, int tune) {
   a.hb_nodal = h->hbn.as<double>();
   a.rain_e = h->rain_e.as<T>();
   a.rain_node = h->rain_node.as<T>();
+  a.lim = h->lim.as<T>();
+  a.lim_nu = (T)h->prm.lim_nu;
   a.node_scen = h->node_scen.as<int32_t>();
   a.scen = h->scen.as<ScenDev>();
   a.tile_scen = h->tile_scen.as<int32_t>();
@@ -592,10 +664,19 @@ static int launch_stage_once(dgswe_h h, int stage, int tune, cudaStream_t s) {
   else e = launch_stage<Fp64>(h->prm.p, h->prm.flux, make_args<Fp64>(h, stage, tune), grid, h->block, s);
   if (e != cudaSuccess) return fail(DGSWE_ECUDA, "stage launch: %s", cudaGetErrorString(e));
   h->launches++;
+  if (h->prm.limiter && !tune) {  // slope limiter on the stage output, then the positive-depth operator
+    const long long ne = (long long)h->ntiles * TILE;
+    e = mixed(h) ? launch_limiter<Mixed>(make_args<Mixed>(h, stage, tune), ne, s)
+                 : launch_limiter<Fp64>(make_args<Fp64>(h, stage, tune), ne, s);
+    if (e != cudaSuccess) return fail(DGSWE_ECUDA, "limiter launch: %s", cudaGetErrorString(e));
+    h->launches++;
+  }
   return 0;
 }
 
-static int launches_per_stage(dgswe_h h) { return 1 + ((h->split && h->nedges > 0) ? 1 : 0) + (h->grid_rain ? 1 : 0); }
+static int launches_per_stage(dgswe_h h) {
+  return 1 + ((h->split && h->nedges > 0) ? 1 : 0) + (h->grid_rain ? 1 : 0) + (h->prm.limiter ? 1 : 0);
+}
 
 static int occupancy(dgswe_h h, int block) {
   return mixed(h) ? stage_blocks_per_sm<Mixed>(h->prm.p, h->prm.flux, block, h->split)
@@ -788,6 +869,9 @@ int dgswe_set_params(dgswe_h h, const dgswe_params* p) {
   if (p->precision != DGSWE_FP64 && p->precision != DGSWE_MIXED) return fail(DGSWE_EINVAL, "unknown precision");
   if (!(p->g > 0) || !(p->H0 > 0)) return fail(DGSWE_EINVAL, "g and H0 must be positive");
   if (p->friction < 0 || p->friction > 2) return fail(DGSWE_EINVAL, "unknown friction law");
+  if (p->limiter != 0 && p->limiter != 1) return fail(DGSWE_EINVAL, "limiter must be 0 or 1");
+  if (p->limiter && p->p != 1) return fail(DGSWE_EINVAL, "the slope limiter is defined for p = 1");
+  if (p->limiter && !(p->lim_nu >= 0.0 && p->lim_M >= 0.0)) return fail(DGSWE_EINVAL, "limiter constants must be >= 0");
   if (!h->sc.empty() && h->sc[0].level > 0) return fail(DGSWE_ESTATE, "set_params must precede set_mesh");
   h->prm = *p;
   h->has_params = true;
@@ -1183,7 +1267,8 @@ int dgswe_ensemble_create(dgswe_h* out, int32_t n, const dgswe_h* members, int d
     const dgswe_params& a = members[0]->prm;
     const dgswe_params& b = members[i]->prm;
     if (a.p != b.p || a.flux != b.flux || a.ssp_stages != b.ssp_stages || a.precision != b.precision || a.g != b.g ||
-        a.H0 != b.H0 || a.friction != b.friction || a.cf != b.cf)
+        a.H0 != b.H0 || a.friction != b.friction || a.cf != b.cf || a.limiter != b.limiter ||
+        a.lim_nu != b.lim_nu || a.lim_M != b.lim_M)
       return fail(DGSWE_EINVAL, "member %d differs in p, flux, ssp_stages, precision, g, H0 or friction", i);
   }
   dgswe_h h = nullptr;

@@ -36,6 +36,8 @@ struct StageArgs {
   const T* rain_e;         // [elements] constant element rain (rain_kind 1)
   T* rain_node;            // [nodes] gridded rain at the stage time (rain_kind 3), node kernel output
   const int32_t* node_scen;  // [nodes] scenario of each node
+  const T* lim;            // [elements][8] slope limiter data: a_i, c_i (i = 0..2), M h^2, pair bits (-1: off)
+  T lim_nu;                // limiter minmod weight
   const ScenDev* scen;
   const int32_t* tile_scen;  // scenario of each 32-element tile
   double* ledger;          // [scenario][wslots][2]: rain volume, boundary inflow volume per warp
@@ -76,6 +78,9 @@ cudaError_t launch_edges(int p, int flux, const StageArgs<Pol>& a, int grid, int
 // positive-depth operator on records [begin, end) in place (a.in == a.out)
 template <class Pol>
 cudaError_t launch_prepare(int p, const StageArgs<Pol>& a, long long begin, long long end, cudaStream_t s);
+// optional slope limiter (p = 1) on the stage output, in place, then the positive-depth operator
+template <class Pol>
+cudaError_t launch_limiter(const StageArgs<Pol>& a, long long ne, cudaStream_t s);
 // gridded rain (rain_kind 3) interpolated to every node at the stage time: a.rain_node[0, nn)
 template <class Pol>
 cudaError_t launch_node_rain(const StageArgs<Pol>& a, long long nn, cudaStream_t s);

@@ -62,6 +62,7 @@ struct RefTab {
   T el[3][MAXNG][3];               // barycentric coordinates of those points
   T vphi[3][MAXNP];                // basis at the three vertices
   T vinv[2][3];                    // modal coefficients 1,2 of a linear function from vertex values
+  T mphi[3][MAXNP];                // basis at the midpoints of the three edges (slope limiter)
   T phi0;                          // constant mode value 1/sqrt(2)
 };
 

@@ -979,6 +979,96 @@ __global__ void __launch_bounds__(256) node_rain_kernel(const StageArgs<Pol> a, 
   }
 }
 
+// optional slope limiter (Sec. 2.3 offers one without its form): the TVB minmod moment limiter
+// of Cockburn and Shu for P1 triangles, componentwise on zeta, qx, qy of wet elements with three
+// neighbours.  Edge i (vertices i, i+1): deviation d_i = w(m_i) - mean at the edge midpoint,
+// neighbour estimate a_i (mean_i - mean) + c_i (mean_k - mean) with the barycentric pair
+// (i, k) precomputed on the host (a_i, c_i >= 0), limited to minmod(d_i, nu estimate) unless
+// |d_i| <= M h^2; positive and negative parts rebalanced to sum to zero; the slopes rebuilt from
+// the midpoint deviations (vertex deviation i = l_i + l_{i-1} - l_{i+1}).  Means are untouched,
+// so the update runs in place; the positive-depth operator follows.
+template <class T>
+__device__ __forceinline__ T minmod_r(T a, T b) {
+  return (a > T(0) && b > T(0)) ? (a < b ? a : b) : ((a < T(0) && b < T(0)) ? (a > b ? a : b) : T(0));
+}
+
+template <class Pol>
+__device__ __forceinline__ bool limit_var(typename Pol::T* s, const typename Pol::T dm[3], const typename Pol::T* L,
+                                          int bits, typename Pol::T nu, const RefTab<typename Pol::T>& tab) {
+  using T = typename Pol::T;
+  T d[3], l[3];
+  bool changed = false;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    d[i] = s[0] * tab.mphi[i][1] + s[1] * tab.mphi[i][2];
+    const int k = (bits >> i) & 1 ? (i + 2) % 3 : (i + 1) % 3;
+    const T est = L[2 * i] * dm[i] + L[2 * i + 1] * dm[k];
+    l[i] = (abs_r(d[i]) <= L[6]) ? d[i] : minmod_r(d[i], nu * est);
+    changed = changed || (l[i] != d[i]);
+  }
+  if (!changed) return false;
+  const T sum = l[0] + l[1] + l[2];
+  if (sum != T(0)) {
+    T pos = 0, neg = 0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      pos += l[i] > T(0) ? l[i] : T(0);
+      neg += l[i] < T(0) ? -l[i] : T(0);
+    }
+    const T tp = pos > T(0) ? (neg / pos < T(1) ? neg / pos : T(1)) : T(0);
+    const T tn = neg > T(0) ? (pos / neg < T(1) ? pos / neg : T(1)) : T(0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) l[i] = tp * (l[i] > T(0) ? l[i] : T(0)) - tn * (l[i] < T(0) ? -l[i] : T(0));
+  }
+  T f[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) f[i] = l[i] + l[(i + 2) % 3] - l[(i + 1) % 3];
+  s[0] = tab.vinv[0][0] * f[0] + tab.vinv[0][1] * f[1] + tab.vinv[0][2] * f[2];
+  s[1] = tab.vinv[1][0] * f[0] + tab.vinv[1][1] * f[1] + tab.vinv[1][2] * f[2];
+  return true;
+}
+
+template <class Pol>
+__global__ void __launch_bounds__(256) limit_kernel(const StageArgs<Pol> a, long long ne) {
+  using T = typename Pol::T;
+  constexpr int RV = Pol::template RV<1>;
+  const RefTab<T>& tab = ctab<T, 1>();
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += (long long)gridDim.x * blockDim.x) {
+    const int4 nb = __ldg(a.nbr + e);
+    if (nb.x < 0 || nb.y < 0 || nb.z < 0) continue;
+    const T* L = a.lim + 8 * e;
+    const int bits = (int)L[7];
+    if (bits < 0) continue;
+    Raw<RV> r;
+    load_raw<RV>(a.out, e, r);
+    Elem<1, Pol> E;
+    unpack<1>(r, E);
+    if (E.flags & FLAG_DRY) continue;
+    T dz[3], dx[3], dy[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int code = (j == 0) ? nb.x : (j == 1 ? nb.y : nb.z);
+      Raw<RV> rn;
+      load_raw<RV>(a.out, (long long)(code >> 2), rn);
+      Elem<1, Pol> N;
+      unpack<1>(rn, N);
+      dz[j] = acc_diff(N.zb, E.zb);
+      dx[j] = acc_diff(N.xb, E.xb);
+      dy[j] = acc_diff(N.yb, E.yb);
+    }
+    bool ch = limit_var<Pol>(E.zs, dz, L, bits, a.lim_nu, tab);
+    ch = limit_var<Pol>(E.xs, dx, L, bits, a.lim_nu, tab) || ch;
+    ch = limit_var<Pol>(E.ys, dy, L, bits, a.lim_nu, tab) || ch;
+    if (!ch) continue;
+    Geo<Pol> G;
+    load_geo(a.geo, e, nb, G);
+    apply_positivity<1, Pol>(E, G, e, a, &a.ctl->err);
+    Raw<RV> ro;
+    pack<1>(E, ro);
+    store_raw<RV>(a.out, e, ro);
+  }
+}
+
 // ------------------------------------------------------------------------ stage kernel ----
 // Work split: 32-element tiles, warp w of the launch takes tiles w, w + W, w + 2W, ... (W warps
 // in the grid).  No block-wide barrier inside the loop; rain and boundary volumes accumulate per
@@ -1686,6 +1776,11 @@ static inline int grid_for(long long n, int block) {
     int g = grid_for(e - b, 256);                                                                            \
     if (p == 1) prepare_kernel<1, POL><<<g, 256, 0, s>>>(a, b, e);                                           \
     else prepare_kernel<2, POL><<<g, 256, 0, s>>>(a, b, e);                                                  \
+    return cudaGetLastError();                                                                               \
+  }                                                                                                          \
+  template <>                                                                                                \
+  cudaError_t launch_limiter<POL>(const StageArgs<POL>& a, long long ne, cudaStream_t s) {                   \
+    limit_kernel<POL><<<grid_for(ne, 256), 256, 0, s>>>(a, ne);                                              \
     return cudaGetLastError();                                                                               \
   }                                                                                                          \
   template <>                                                                                                \

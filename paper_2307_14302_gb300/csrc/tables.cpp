@@ -161,6 +161,14 @@ void build_tables(int p, RefTab<double>& t) {
     }
   for (int m = 0; m < 2; ++m)
     for (int i = 0; i < 3; ++i) t.vinv[m][i] = inv[m + 1][i];
+  // edge midpoints (edge j joins vertices j and j+1)
+  for (int j = 0; j < 3; ++j) {
+    double l[3] = {0, 0, 0}, r, s;
+    l[j] = 0.5;
+    l[(j + 1) % 3] = 0.5;
+    rs_of(l, r, s);
+    dubiner_eval(p, r, s, t.mphi[j], nullptr, nullptr);
+  }
   t.phi0 = 1.0 / std::sqrt(2.0);
 }
 

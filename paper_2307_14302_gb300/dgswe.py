@@ -35,7 +35,8 @@ class DgsweError(RuntimeError):
 class Params(C.Structure):
     _fields_ = [("p", C.c_int32), ("flux", C.c_int32), ("ssp_stages", C.c_int32), ("precision", C.c_int32),
                 ("g", C.c_double), ("H0", C.c_double), ("cfl", C.c_double), ("dt", C.c_double),
-                ("friction", C.c_int32), ("cf", C.c_double)]
+                ("friction", C.c_int32), ("cf", C.c_double), ("limiter", C.c_int32), ("lim_nu", C.c_double),
+                ("lim_M", C.c_double)]
 
 
 class Storm(C.Structure):
@@ -144,14 +145,15 @@ class Solver:
     """One library context (dgswe_create ... dgswe_destroy)."""
 
     def __init__(self, p=1, flux=FLUX_ROE, ssp_stages=None, precision=MIXED, g=9.81, H0=0.01, cfl=0.3, dt=0.0,
-                 friction=MANNING, cf=0.0, device=0, stream=None):
+                 friction=MANNING, cf=0.0, device=0, stream=None, limiter=False, lim_nu=1.5, lim_M=0.0):
         L = lib()
         h = _h()
         _check(L.dgswe_create(C.byref(h), device, C.c_void_p(stream) if stream else None))
         self.h = h
         self.p = p
         self.np_ = (p + 1) * (p + 2) // 2
-        self.prm = Params(p, flux, ssp_stages if ssp_stages else min(p + 1, 3), precision, g, H0, cfl, dt, friction, cf)
+        self.prm = Params(p, flux, ssp_stages if ssp_stages else min(p + 1, 3), precision, g, H0, cfl, dt, friction, cf,
+                          1 if limiter else 0, lim_nu, lim_M)
         _check(L.dgswe_set_params(self.h, C.byref(self.prm)))
         self.ne = 0
         self._members = []
@@ -332,10 +334,10 @@ class Ensemble:
 
 
 def from_workload(w, precision=MIXED, flux=FLUX_ROE, ssp_stages=None, dt=0.0, friction=MANNING, cf=0.0, device=0,
-                  stream=None, block=0, waves=1, split=1) -> Solver:
+                  stream=None, block=0, waves=1, split=1, limiter=False, lim_nu=1.5, lim_M=0.0) -> Solver:
     """A Solver set up with a workload's mesh, fields, forcing and nodal initial state."""
     s = Solver(p=w.p, flux=flux, ssp_stages=ssp_stages, precision=precision, H0=w.h0, cfl=w.cfl, dt=dt,
-               friction=friction, cf=cf, device=device, stream=stream)
+               friction=friction, cf=cf, device=device, stream=stream, limiter=limiter, lim_nu=lim_nu, lim_M=lim_M)
     s.set_launch(block, waves, split)
     s.set_mesh(w.mesh)
     s.set_fields(w.hb, w.manning if friction == MANNING else None)

@@ -29,13 +29,16 @@ def _built():
     D.lib()
 
 
-def _pair(w, steps, precision, flux=O.ROE, ssp=None, friction=O.MANNING, cf=0.0, block=0, waves=1, dt=None):
+def _pair(w, steps, precision, flux=O.ROE, ssp=None, friction=O.MANNING, cf=0.0, block=0, waves=1, dt=None,
+          limiter=False):
     ref = O.from_workload(w, flux=flux, ssp=ssp, friction=friction, cf=cf, dt=dt)
+    if limiter:
+        ref.set_limiter(True, 1.5, 0.0)
     dt = ref.cfl_dt(w.cfl) if dt is None else dt
     ref.set_dt(dt)
     ref.step(steps)
     dev = D.from_workload(w, precision=precision, flux=flux, ssp_stages=ssp, dt=dt, friction=friction, cf=cf,
-                          block=block, waves=waves)
+                          block=block, waves=waves, limiter=limiter)
     dev.step(steps)
     dev.sync()
     return ref, dev
@@ -229,6 +232,33 @@ def test_hurricane_full_size_two_steps():
     ez, eq = _mixed_err(dev.state(), ref.state())
     assert ez <= MIXED_TOL and eq <= MIXED_TOL, (ez, eq)
     assert dev.ledger()["rel_err"] < 1e-12
+
+
+# ------------------------------------------------------------------ slope limiter ------
+@pytest.mark.parametrize("prec", [D.FP64, D.MIXED])
+@pytest.mark.parametrize("case", ["basin", "coastal"])
+def test_slope_limiter_matches_oracle(prec, case):
+    """The optional Cockburn-Shu TVB minmod limiter (after each stage's positive-depth
+    operator, then the operator again): dam break on the basin, and the coastal wet/dry
+    family; state against the oracle, exact mass."""
+    if case == "basin":
+        w, steps = W.basin_c1(hump=True, rain=True), 200
+    else:
+        w, steps = W.coastal_c2(n_tri=4000, seed=23, steps=100), 100
+    ref, dev = _pair(w, steps, prec, limiter=True)
+    got, want = dev.state(), ref.state()
+    if prec == D.FP64:
+        assert _fp64_err(got, want) <= FP64_TOL
+    else:
+        ez, eq = _mixed_err(got, want)
+        assert ez <= MIXED_TOL and eq <= MIXED_TOL, (ez, eq)
+    assert dev.ledger()["rel_err"] < 1e-12
+    assert np.array_equal(dev.dry(), ref.dry())
+
+
+def test_slope_limiter_rejects_p2():
+    with pytest.raises(D.DgsweError):
+        D.Solver(p=2, limiter=True)
 
 
 # ---------------------------------------------------------------- five-stage SSP ------
