@@ -1126,8 +1126,8 @@ template <int P, int FLUX, class Pol, bool SPLIT>
 #ifdef DG_MAXNREG
 #define DG_STAGE_BOUNDS __maxnreg__(DG_MAXNREG)
 #else
-// register budget per thread: mixed p = 1 at 128 (16 warps per SM), mixed p = 2 at 144 (14 warps
-// per SM; 11-14 % faster than the 166 the compiler picks unbounded), FP64 unbounded
+// register budget per thread: mixed p = 1 at 128 (16 warps per SM), mixed p = 2 at 144 (12 warps
+// per SM as at the 166 the compiler picks unbounded, but 11-14 % faster code), FP64 unbounded
 #define DG_STAGE_BOUNDS __maxnreg__(sizeof(typename Pol::T) == 4 ? (P == 2 ? 144 : 128) : 255)
 #endif
 __global__ void DG_STAGE_BOUNDS stage_kernel(const StageArgs<Pol> a) {
