@@ -453,6 +453,35 @@ def test_ensemble_members_match_solo_runs(prec, split):
         assert _fp64_err(ens.state(0), ref.state()) <= FP64_TOL
 
 
+@pytest.mark.slow
+def test_ensemble_full_size_sampled_members_match_oracle():
+    """The 64-scenario ensemble at the benchmark's size (about 10M triangles in all, members
+    built with the benchmark's launch shape, the ensemble autotuned), 10 mixed-precision steps;
+    the three smallest members are compared element by element with the oracle run alone on the
+    same scenario and dt."""
+    ws = W.ensemble_c4()
+    sample = set(np.argsort([w.mesh.n_tri for w in ws])[:3].tolist())
+    members, refs = [], {}
+    for i, w in enumerate(ws):
+        dt = 0.0
+        if i in sample:
+            ref = O.from_workload(w)
+            dt = ref.cfl_dt(w.cfl)
+            ref.set_dt(dt)
+            refs[i] = ref
+        members.append(D.from_workload(w, precision=D.MIXED, dt=dt, block=64, waves=1, split=0))
+    ens = D.Ensemble(members)
+    for m in members:
+        m.close()
+    ens.step(10)
+    ens.sync()
+    for i, ref in refs.items():
+        ref.step(10)
+        ez, eq = _mixed_err(ens.state(i), ref.state())
+        assert ez <= MIXED_TOL and eq <= MIXED_TOL, (i, ez, eq)
+        assert ens.ledger(i)["rel_err"] < 1e-12 and ens.ledger(i)["steps"] == 10
+
+
 @pytest.mark.parametrize("prec", [D.FP64, D.MIXED])
 def test_load_state_round_trip_and_restart(prec):
     """Checkpoint/restart through the public API (also the e2e benchmark's per-step exchange).
