@@ -436,8 +436,17 @@ def our_arm(args, ws, rank, local):
     s64.sync()
     t64 = timed_steps(s64, k64)
     units64, t64m = whole_job(w.dof * k64, t64, ws, dev)
+    b64, w64, sp64 = s64.launch()
     fp64 = {"value": units64 / t64m, "unit": UNIT, "steps": k64, "ms_per_step": 1e3 * t64 / k64,
-            "mixed_speedup": value / (units64 / t64m)}
+            "mixed_speedup": value / (units64 / t64m), "launch": {"block": b64, "waves": w64, "split": sp64}}
+    # FP64 arithmetic roofline: FP64 FLOPs per element and stage of the launch shape in use (from
+    # the committed ncu summary of the FP64 kernels, hash-checked), over the measured time
+    fpe = profiled_fp64_flops(sp64) if p == 1 else None
+    if fpe is not None:
+        ach = fpe * E * stages * k64 / t64 / 1e12
+        fp64["roofline"] = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                            "frac": ach / FP64_PEAK_TFLOPS, "peak_source": "nominal GB300 FP64 rate",
+                            "flops_per_element_stage": fpe}
     s64.close()
 
     ensemble = None
@@ -634,6 +643,27 @@ def profiled_traffic(summary, n_elem):
     if not m_hash or not m_bpe or m_hash.group(1) != kernel_hash():
         return None
     return float(m_bpe.group(1)) * n_elem
+
+
+FP64_PEAK_TFLOPS = 1.25  # nominal dense FP64 rate of a GB300 (not in the measured peaks)
+
+
+def profiled_fp64_flops(split):
+    """FP64 FLOPs (2 per DFMA, 1 per DADD/DMUL) per element and stage of the FP64 p=1 path in the
+    given launch form (split: edge kernel + element kernel; fused: stage kernel), from the committed
+    ncu summary, or None when it is missing or was taken on a different kernel source."""
+    import re
+
+    path = os.path.join(ROOT, "profiles", "stage_kernel_fp64_p1_coastal.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m_hash = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", txt)
+    key = "fp64_flops_per_element_stage_split" if split else "fp64_flops_per_element_stage_fused"
+    m = re.search(key + r":\s*([0-9.eE+]+)", txt)
+    if not m_hash or not m or m_hash.group(1) != kernel_hash():
+        return None
+    return float(m.group(1))
 
 
 def kernel_hash():
