@@ -240,10 +240,12 @@ int dgswe_ensemble_get_ledger(dgswe_h ens, int32_t member, dgswe_ledger* out);
 
 /* Launch shape of a stage: block size of the element kernel (64, 128, 256, or 0 = autotune on
  * the next step), waves (1 or 2: the grid holds waves x CTAs resident per SM x SMs CTAs whose
- * warps take the 32-element tiles round-robin), and split (1: a separate edge kernel computes
- * every interior edge flux once and the element kernel gathers it; 0: one fused kernel in which
- * both neighbours evaluate the edge).  Fused and split results agree to rounding; for a fixed
- * split value results do not depend on block or waves. */
+ * warps take the 32-element tiles round-robin), and the form, argument split: 0 one fused kernel
+ * in which both neighbours evaluate an interior edge; 1 a separate edge kernel computes every
+ * interior edge flux once and the element kernel gathers it; 2 the tile form, one kernel in which
+ * each warp evaluates every edge touching its 32-element tile once from records staged in shared
+ * memory.  The three forms agree to rounding; for a fixed form results do not depend on block or
+ * waves.  Returns DGSWE_EINVAL for other values. */
 int dgswe_set_launch(dgswe_h, int32_t block, int32_t waves, int32_t split);
 int dgswe_get_launch(dgswe_h, int32_t* block, int32_t* waves, int32_t* split);
 

@@ -112,7 +112,8 @@ struct dgswe_ctx {
   int np = 0, rv = 0, gv = 0;      // modes, record and geometry sizes (16-byte units)
   long long E = 0, N = 0;          // padded element count, node count
   std::vector<long long> eoff, noff;
-  DevBuf rec[3], nbr, geo, nodes, node_xy, xy64, hbn, rain_e, rain_node, node_scen, lim, scen, tile_scen, ledger, ctl,
+  DevBuf rec[3], nbr, geo, nodes, node_xy, xy64, hbn, rain_e, rain_node, node_scen, lim, scen, tile_scen, tile_meta, xy0,
+      ledger, ctl,
       eorig, grids, rivers, scratch,
       gather_buf, edges, slots;
   long long nedges = 0;
@@ -136,7 +137,8 @@ struct dgswe_ctx {
   ~dgswe_ctx() {
     DeviceGuard dg_(device);
     DevBuf* bufs[] = {&rec[0], &rec[1], &rec[2], &nbr, &geo, &nodes, &node_xy, &xy64, &hbn, &rain_e, &scen,
-                      &tile_scen, &ledger, &ctl, &eorig, &grids, &rivers, &scratch, &gather_buf, &edges, &slots,
+                      &tile_scen, &tile_meta, &xy0, &ledger, &ctl, &eorig, &grids, &rivers, &scratch, &gather_buf,
+                      &edges, &slots,
                       &rain_node, &node_scen, &lim};
     for (DevBuf* b : bufs) b->alloc(0);
     if (g1) cudaGraphExecDestroy(g1);
@@ -289,6 +291,8 @@ static int upload_all_tables(int p) {
   }
   CU(upload_tables<Mixed>(p, g_tabf[p], g_tabd[p]));
   CU(upload_tables<Fp64>(p, g_tabf[p], g_tabd[p]));
+  CU(upload_tile_tables<Mixed>(p, g_tabf[p], g_tabd[p]));
+  CU(upload_tile_tables<Fp64>(p, g_tabf[p], g_tabd[p]));
   return 0;
 }
 
@@ -323,6 +327,8 @@ static int build_layout(dgswe_h h) {
   const size_t rw = 4 * (size_t)h->rv, gw = 4 * (size_t)h->gv;  // 32-bit words per element
   std::vector<uint32_t> rec(rw * E, 0u), geo(gw * E, 0u);
   std::vector<int32_t> nbr(4 * E, -1), nodes(4 * E, 0), eorig(E, 0);
+  std::vector<float> xy0f(mx ? 2 * E : 0, 0.f);     // first vertex of each element (tile form)
+  std::vector<double> xy0d(mx ? 0 : 2 * E, 0.0);
   std::vector<double> xy64(2 * N), hbn(N);
   std::vector<int32_t> nscen(N, 0);
   std::vector<float> xyf(mx ? 2 * N : 0), rainf(mx ? E : 0);
@@ -348,6 +354,13 @@ static int build_layout(dgswe_h h) {
       const long long ge = eo + e;
       const int32_t* v = &M.tri[3 * (size_t)e];
       eorig[ge] = M.eorig[e];
+      if (mx) {
+        xy0f[2 * ge] = (float)M.x[v[0]];
+        xy0f[2 * ge + 1] = (float)M.y[v[0]];
+      } else {
+        xy0d[2 * ge] = M.x[v[0]];
+        xy0d[2 * ge + 1] = M.y[v[0]];
+      }
       for (int j = 0; j < 3; ++j) {
         const int32_t c = M.code[3 * (size_t)e + j];
         nbr[4 * ge + j] = c >= 0 ? (int32_t)((((c >> 2) + eo) << 2) | (c & 3)) : c;
@@ -464,6 +477,9 @@ static int build_layout(dgswe_h h) {
   CU(cudaMemcpy(h->xy64.p, xy64.data(), 8 * xy64.size(), cudaMemcpyHostToDevice));
   CU(cudaMemcpy(h->hbn.p, hbn.data(), 8 * hbn.size(), cudaMemcpyHostToDevice));
   CU(cudaMemcpy(h->eorig.p, eorig.data(), 4 * eorig.size(), cudaMemcpyHostToDevice));
+  if (h->xy0.alloc(mx ? 8 * (size_t)E : 16 * (size_t)E)) return fail(DGSWE_ENOMEM, "device allocation failed");
+  if (mx) CU(cudaMemcpy(h->xy0.p, xy0f.data(), 4 * xy0f.size(), cudaMemcpyHostToDevice));
+  else CU(cudaMemcpy(h->xy0.p, xy0d.data(), 8 * xy0d.size(), cudaMemcpyHostToDevice));
   if (mx) {
     CU(cudaMemcpy(h->node_xy.p, xyf.data(), 4 * xyf.size(), cudaMemcpyHostToDevice));
     CU(cudaMemcpy(h->rain_e.p, rainf.data(), 4 * rainf.size(), cudaMemcpyHostToDevice));
@@ -536,9 +552,18 @@ static int build_layout(dgswe_h h) {
   int sms = 0;
   CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
   h->wslots = sms * 64 * 2;
-  if (h->tile_scen.alloc(4 * (size_t)h->ntiles) || h->ledger.alloc(16 * (size_t)h->wslots * ns))
+  std::vector<int32_t> tm(4 * (size_t)h->ntiles, 0);
+  for (long long t = 0; t < h->ntiles; ++t) {
+    const size_t s = (size_t)ts[t];
+    const long long n = h->eoff[s] + h->sc[s].m.ne - t * TILE;
+    tm[4 * t] = ts[t];
+    tm[4 * t + 1] = (int32_t)std::max(0LL, std::min<long long>(TILE, n));
+  }
+  if (h->tile_scen.alloc(4 * (size_t)h->ntiles) || h->tile_meta.alloc(16 * (size_t)h->ntiles) ||
+      h->ledger.alloc(16 * (size_t)h->wslots * ns))
     return fail(DGSWE_ENOMEM, "device allocation failed");
   CU(cudaMemcpy(h->tile_scen.p, ts.data(), 4 * ts.size(), cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(h->tile_meta.p, tm.data(), 4 * tm.size(), cudaMemcpyHostToDevice));
   CU(cudaMemset(h->ledger.p, 0, 16 * (size_t)h->wslots * ns));
   h->wcur = 0;
   CU(cudaMemcpy(h->scen.p, sd.data(), sizeof(ScenDev) * ns, cudaMemcpyHostToDevice));
@@ -600,6 +625,7 @@ static StageArgs<Pol> make_args(dgswe_h h, int stage, int tune) {
   a.in = h->rec[stage == 0 ? 0 : 1 + (stage - 1) % 2].as<uint4>();
   a.wn = h->rec[0].as<uint4>();
   a.out = (stage == S - 1) ? h->rec[0].as<uint4>() : h->rec[1 + stage % 2].as<uint4>();
+  if (tune) a.out = h->rec[1 + stage % 2].as<uint4>();  // timing runs never overwrite w^n
   a.nbr = h->nbr.as<int4>();
   a.geo = h->geo.as<uint4>();
   a.nodes = h->nodes.as<int4>();
@@ -612,6 +638,8 @@ static StageArgs<Pol> make_args(dgswe_h h, int stage, int tune) {
   a.node_scen = h->node_scen.as<int32_t>();
   a.scen = h->scen.as<ScenDev>();
   a.tile_scen = h->tile_scen.as<int32_t>();
+  a.tile_meta = h->tile_meta.as<int4>();
+  a.xy0 = h->xy0.as<uint4>();
   a.ledger = h->ledger.as<double>();
   a.ctl = h->ctl.as<Ctl>();
   a.edges = h->edges.as<uint4>();
@@ -623,6 +651,11 @@ static StageArgs<Pol> make_args(dgswe_h h, int stage, int tune) {
   a.stage = stage;
   a.last = (stage == S - 1) ? 1 : 0;
   a.has_n = st.a_n != 0.0 ? 1 : 0;
+  auto pow2_or_0 = [](double c) {
+    int ex = 0;
+    return c == 0.0 || (c > 0.0 && std::frexp(c, &ex) == 0.5);
+  };
+  a.pow2 = (pow2_or_0(st.a_n) && pow2_or_0(st.a_in)) ? 1 : 0;
   a.cst_f = (float)st.c;
   a.tune = tune;
   a.friction = h->prm.friction;
@@ -644,7 +677,8 @@ static int edge_grid(dgswe_h h) {
   return (int)std::max<long long>(1, std::min<long long>(need, 16LL * sms));
 }
 
-// one Runge-Kutta stage: (edge kernel, when split) then the element kernel
+// one Runge-Kutta stage: (edge kernel, when split = 1) then the element kernel (fused, split or
+// tile form)
 static int launch_stage_once(dgswe_h h, int stage, int tune, cudaStream_t s) {
   const int grid = h->grid;
   cudaError_t e = cudaSuccess;
@@ -654,14 +688,19 @@ static int launch_stage_once(dgswe_h h, int stage, int tune, cudaStream_t s) {
     if (e != cudaSuccess) return fail(DGSWE_ECUDA, "node rain launch: %s", cudaGetErrorString(e));
     h->launches++;
   }
-  if (h->split && h->nedges > 0) {
+  if (h->split == 1 && h->nedges > 0) {
     if (mixed(h)) e = launch_edges<Mixed>(h->prm.p, h->prm.flux, make_args<Mixed>(h, stage, tune), edge_grid(h), 256, s);
     else e = launch_edges<Fp64>(h->prm.p, h->prm.flux, make_args<Fp64>(h, stage, tune), edge_grid(h), 256, s);
     if (e != cudaSuccess) return fail(DGSWE_ECUDA, "edge launch: %s", cudaGetErrorString(e));
     h->launches++;
   }
-  if (mixed(h)) e = launch_stage<Mixed>(h->prm.p, h->prm.flux, make_args<Mixed>(h, stage, tune), grid, h->block, s);
-  else e = launch_stage<Fp64>(h->prm.p, h->prm.flux, make_args<Fp64>(h, stage, tune), grid, h->block, s);
+  if (h->split == 2)
+    e = mixed(h) ? launch_tile<Mixed>(h->prm.p, h->prm.flux, make_args<Mixed>(h, stage, tune), grid, h->block, s)
+                 : launch_tile<Fp64>(h->prm.p, h->prm.flux, make_args<Fp64>(h, stage, tune), grid, h->block, s);
+  else if (mixed(h))
+    e = launch_stage<Mixed>(h->prm.p, h->prm.flux, make_args<Mixed>(h, stage, tune), grid, h->block, s);
+  else
+    e = launch_stage<Fp64>(h->prm.p, h->prm.flux, make_args<Fp64>(h, stage, tune), grid, h->block, s);
   if (e != cudaSuccess) return fail(DGSWE_ECUDA, "stage launch: %s", cudaGetErrorString(e));
   h->launches++;
   if (h->prm.limiter && !tune) {  // slope limiter on the stage output, then the positive-depth operator
@@ -675,10 +714,13 @@ static int launch_stage_once(dgswe_h h, int stage, int tune, cudaStream_t s) {
 }
 
 static int launches_per_stage(dgswe_h h) {
-  return 1 + ((h->split && h->nedges > 0) ? 1 : 0) + (h->grid_rain ? 1 : 0) + (h->prm.limiter ? 1 : 0);
+  return 1 + ((h->split == 1 && h->nedges > 0) ? 1 : 0) + (h->grid_rain ? 1 : 0) + (h->prm.limiter ? 1 : 0);
 }
 
 static int occupancy(dgswe_h h, int block) {
+  if (h->split == 2)
+    return mixed(h) ? tile_blocks_per_sm<Mixed>(h->prm.p, h->prm.flux, block)
+                    : tile_blocks_per_sm<Fp64>(h->prm.p, h->prm.flux, block);
   return mixed(h) ? stage_blocks_per_sm<Mixed>(h->prm.p, h->prm.flux, block, h->split)
                   : stage_blocks_per_sm<Fp64>(h->prm.p, h->prm.flux, block, h->split);
 }
@@ -691,7 +733,9 @@ static int apply_launch(dgswe_h h, int block, int waves, int split) {
   h->block = block;
   h->waves = waves;
   h->split = split;
-  const int want = sms * std::max(1, occupancy(h, block)) * waves;
+  const int occ = occupancy(h, block);
+  if (occ < 1) return fail(DGSWE_EINVAL, "form %d does not fit a block of %d threads on this device", split, block);
+  const int want = sms * occ * waves;
   const int need = (h->ntiles + block / 32 - 1) / (block / 32);  // one tile per warp
   h->grid = std::max(1, std::min(want, need));
   h->wcur = h->grid * (block / 32);
@@ -699,7 +743,8 @@ static int apply_launch(dgswe_h h, int block, int waves, int split) {
   return 0;
 }
 
-// time the first stage (which reads w^n and writes a scratch buffer) for each launch shape
+// time whole steps (every stage; timing runs write only the two scratch records) for each form
+// (fused, edge kernel + element kernel, tile), block size and number of waves
 static int autotune(dgswe_h h) {
   cudaEvent_t e0, e1;
   CU(cudaEventCreate(&e0));
@@ -708,17 +753,20 @@ static int autotune(dgswe_h h) {
   int bb = 128, bp = 0;
   const int blocks[3] = {64, 128, 256};
   int bs = 1;
-  for (int sp = 0; sp <= 1; ++sp)
+  for (int sp = 0; sp <= 2; ++sp)
   for (int pi = 1; pi <= 2; ++pi)
     for (int bi = 0; bi < 3; ++bi) {
       h->split = sp;
       if (occupancy(h, blocks[bi]) < 1) continue;
       if (int rc = apply_launch(h, blocks[bi], pi, sp)) return rc;
+      const int ns = (int)h->stages.size();
       for (int w = 0; w < 2; ++w)
-        if (int rc = launch_stage_once(h, 0, 1, h->stream)) return rc;
+        for (int st = 0; st < ns; ++st)
+          if (int rc = launch_stage_once(h, st, 1, h->stream)) return rc;
       CU(cudaEventRecord(e0, h->stream));
       for (int r = 0; r < 5; ++r)
-        if (int rc = launch_stage_once(h, 0, 1, h->stream)) return rc;
+        for (int st = 0; st < ns; ++st)
+          if (int rc = launch_stage_once(h, st, 1, h->stream)) return rc;
       CU(cudaEventRecord(e1, h->stream));
       CU(cudaEventSynchronize(e1));
       float ms = 0.f;
@@ -1094,6 +1142,7 @@ int dgswe_sync(dgswe_h h) {
   CU(cudaMemcpy(&c, h->ctl.p, sizeof c, cudaMemcpyDeviceToHost));
   if (c.err & ERR_NONFINITE) return fail(DGSWE_ENONFINITE, "a stage produced a non-finite state");
   if (c.err & ERR_NEGDEPTH) return fail(DGSWE_ENEGDEPTH, "an element mean depth fell below zero");
+  if (c.err & ERR_TIMEOUT) return fail(DGSWE_ETIMEOUT, "a bulk copy into shared memory did not complete");
   return 0;
 }
 
@@ -1315,7 +1364,7 @@ int dgswe_set_launch(dgswe_h h, int32_t block, int32_t waves, int32_t split) {
     return 0;
   }
   if (waves < 1 || waves > 2) return fail(DGSWE_EINVAL, "waves must be 1 or 2");
-  if (split != 0 && split != 1) return fail(DGSWE_EINVAL, "split must be 0 or 1");
+  if (split < 0 || split > 2) return fail(DGSWE_EINVAL, "split must be 0, 1 or 2");
   h->autotune = false;
   if (!h->ready) {
     h->block = block;

@@ -40,12 +40,14 @@ struct StageArgs {
   T lim_nu;                // limiter minmod weight
   const ScenDev* scen;
   const int32_t* tile_scen;  // scenario of each 32-element tile
+  const int4* tile_meta;   // tile form: per tile {scenario, elements present (0..32), 0, 0}
+  const uint4* xy0;        // tile form: first vertex of each element, [E] float2 (mixed) / double2 (FP64)
   double* ledger;          // [scenario][wslots][2]: rain volume, boundary inflow volume per warp
   Ctl* ctl;
   const uint4* edges;      // edge-split path: interior edge records
   uint4* slots;            // edge-split path: per (element, local edge) lift slots
   long long nedges;
-  int split;               // 1: interior edges come from the slots written by the edge kernel
+  int split;               // form: 0 fused, 1 edge kernel + slots, 2 tile (each edge of a warp tile once)
   int ntiles;              // 32-element tiles, processed round-robin by the launch's warps
   int wslots;              // ledger slots per scenario (>= warps of the launch)
   int stage;               // Shu-Osher stage index
@@ -54,6 +56,7 @@ struct StageArgs {
   int classify_only;       // prepare pass: derive depth and dry flag, keep the state as given
   int friction;            // 0 Manning, 1 quadratic, 2 none
   int has_n;               // the stage combines with the step-initial state
+  int pow2;                // a_n and a_in are 0 or powers of two (exact float-float scaling)
   float a_n_hi, a_n_lo, a_in_hi, a_in_lo;  // Shu-Osher coefficients as float-float
   double a_n, a_in;
   float cst_f;             // stage time as a fraction of dt
@@ -72,6 +75,14 @@ template <class Pol>
 cudaError_t launch_stage(int p, int flux, const StageArgs<Pol>& a, int grid, int block, cudaStream_t s);
 template <class Pol>
 int stage_blocks_per_sm(int p, int flux, int block, int split);
+// tile form (split = 2): reference tables and shared-memory limits of its translation unit,
+// the launch, and resident CTAs per SM
+template <class Pol>
+cudaError_t upload_tile_tables(int p, const RefTab<float>& tf, const RefTab<double>& td);
+template <class Pol>
+cudaError_t launch_tile(int p, int flux, const StageArgs<Pol>& a, int grid, int block, cudaStream_t s);
+template <class Pol>
+int tile_blocks_per_sm(int p, int flux, int block);
 // edge kernel of the split path: one thread per interior edge, writes both sides' slots
 template <class Pol>
 cudaError_t launch_edges(int p, int flux, const StageArgs<Pol>& a, int grid, int block, cudaStream_t s);

@@ -32,7 +32,7 @@ constexpr int TILE_ALIGN = 256;  // scenario element ranges start on multiples o
 constexpr int TILE = 32;         // elements per warp tile
 
 enum : uint32_t { FLAG_DRY = 1u };
-enum : int { ERR_NONFINITE = 1, ERR_NEGDEPTH = 2 };
+enum : int { ERR_NONFINITE = 1, ERR_NEGDEPTH = 2, ERR_TIMEOUT = 4 };
 
 DG_HD constexpr int np_of(int p) { return (p + 1) * (p + 2) / 2; }
 
@@ -64,6 +64,8 @@ struct RefTab {
   T vinv[2][3];                    // modal coefficients 1,2 of a linear function from vertex values
   T mphi[3][MAXNP];                // basis at the midpoints of the three edges (slope limiter)
   T phi0;                          // constant mode value 1/sqrt(2)
+  T qphiT[MAXNP][MAXNQ];           // qphi transposed: consecutive area points of one mode adjacent
+  T qwphiT[MAXNP][MAXNQ];          // qw[q] * qphi[q][m], same order
 };
 
 // per-scenario forcing constants in the arithmetic type of a path

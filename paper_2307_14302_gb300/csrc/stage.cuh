@@ -93,6 +93,9 @@ __device__ __forceinline__ void acc_set(ff& a, double v) {
   a.hi = (float)v;
   a.lo = (float)(v - (double)a.hi);
 }
+// scaling by a power of two (exact in both words of a float-float)
+__device__ __forceinline__ double acc_scale2(double a, double c) { return a * c; }
+__device__ __forceinline__ ff acc_scale2(ff a, float c) { return {a.hi * c, a.lo * c}; }
 __device__ __forceinline__ double acc_neg(double a) { return -a; }
 __device__ __forceinline__ ff acc_neg(ff a) { return {-a.hi, -a.lo}; }
 template <class Acc>
@@ -122,19 +125,44 @@ __device__ __forceinline__ double cos_r(double x) { return cos(x); }
 __device__ __forceinline__ float pow43_r(float h) { return h * cbrtf(h); }
 __device__ __forceinline__ double pow43_r(double h) { return h * cbrt(h); }
 
-// FP32 path: hardware approximations (MUFU, a few ulp, deterministic); FP64 path: exact
-__device__ __forceinline__ float frcp(float x) { return __fdividef(1.0f, x); }
+// FP32 path: single hardware (MUFU) instructions of the PTX ISA -- approximate to a few ulp,
+// deterministic, flushing subnormals to zero.  Every argument they get is a depth >= H0 > 0, a
+// wave speed, an edge length, a squared speed above 1e-30 or a bounded exponent, far from the
+// subnormal range.  FP64 path: correctly rounded operations.
+__device__ __forceinline__ float mufu_rcp(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float mufu_rsqrt(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float mufu_lg2(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float mufu_ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float frcp(float x) { return mufu_rcp(x); }
 __device__ __forceinline__ double frcp(double x) { return 1.0 / x; }
-__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ float fdiv(float a, float b) { return a * mufu_rcp(b); }
 __device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
-__device__ __forceinline__ float fsqrt_pos(float x) { return x * rsqrtf(x); }  // x > 0
+__device__ __forceinline__ float fsqrt_pos(float x) { return x * mufu_rsqrt(x); }  // x > 0
 __device__ __forceinline__ double fsqrt_pos(double x) { return sqrt(x); }
-__device__ __forceinline__ float fsqrt0(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+// sqrt(x) for x >= 0 (a squared speed): zero below 1e-30, where the friction is negligible
+__device__ __forceinline__ float fsqrt0(float x) { return x > 1e-30f ? x * mufu_rsqrt(x) : 0.f; }
 __device__ __forceinline__ double fsqrt0(double x) { return sqrt(x); }
-// H^{-4/3}
-__device__ __forceinline__ float fpowm43(float h) { return exp2f(-1.3333333f * __log2f(h)); }
+// H^{-4/3} = 2^(-4/3 log2 H)
+__device__ __forceinline__ float fpowm43(float h) { return mufu_ex2(-1.3333333f * mufu_lg2(h)); }
 __device__ __forceinline__ double fpowm43(double h) { return 1.0 / (h * cbrt(h)); }
-__device__ __forceinline__ float fexp(float x) { return __expf(x); }
+// e^x = 2^(x log2 e)
+__device__ __forceinline__ float fexp(float x) { return mufu_ex2(x * 1.4426950408889634f); }
 __device__ __forceinline__ double fexp(double x) { return exp(x); }
 __device__ __forceinline__ float fsin(float x) { return __sinf(x); }
 __device__ __forceinline__ double fsin(double x) { return sin(x); }

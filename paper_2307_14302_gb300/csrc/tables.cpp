@@ -170,6 +170,11 @@ void build_tables(int p, RefTab<double>& t) {
     dubiner_eval(p, r, s, t.mphi[j], nullptr, nullptr);
   }
   t.phi0 = 1.0 / std::sqrt(2.0);
+  for (int m = 0; m < t.np; ++m)
+    for (int q = 0; q < t.nq; ++q) {
+      t.qphiT[m][q] = t.qphi[q][m];
+      t.qwphiT[m][q] = t.qw[q] * t.qphi[q][m];
+    }
 }
 
 void tables_to_float(const RefTab<double>& d, RefTab<float>& f) {

@@ -1,0 +1,126 @@
+"""Parity of each launch form of the stage (fused, edge kernel + element kernel, tile) with the
+FP64 CPU oracle, through the C-ABI.
+
+Same bars as the other parity tests: FP64 device path within 1e-11 of the oracle (relative to
+the larger of the variable's maximum magnitude and 1), mixed path within 1e-4 m in zeta and
+1e-4 m^2/s in q, relative mass balance within 1e-12.  Each case runs the oracle once and all
+three forms on the same seeded inputs and the oracle's dt.
+"""
+import functools
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2307_14302_gb300 import dgswe as D
+from paper_2307_14302_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-11
+MIXED_TOL = 1e-4
+FORMS = (0, 1, 2)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2307_14302_gb300 import build as B
+
+    B.build()
+    D.lib()
+
+
+def _coastal_grid_press():
+    w = W.coastal_c2(n_tri=3000, seed=31, steps=50)
+    w.storm = None
+    rng = np.random.default_rng(3)
+    nx, ny, nt = 12, 9, 3
+    w.rain_grid = W.RainGrid(nx, ny, nt, 0.0, 0.0, 400_000.0 / (nx - 1), 300_000.0 / (ny - 1), 0.0, 60.0,
+                             rng.uniform(0, 80, (nt, ny, nx)).astype(np.float32))
+    w.pressure = (320_000.0, 150_000.0, 50_000.0, 1.0)
+    return w
+
+
+def _coastal_dry():
+    w = W.coastal_c2(n_tri=4000, seed=9, steps=100)
+    w.storm = None
+    return w
+
+
+def _basin_p2():
+    w = W.basin_c1()
+    w.p = 2
+    return w
+
+
+def _ssp5():
+    w = W.coastal_c2(n_tri=4000, seed=19, steps=100)
+    w.cfl = 0.6
+    return w
+
+
+# name: (workload, steps, oracle/device options, dry flags compared on the FP64 path)
+CASES = {
+    "basin": (lambda: W.basin_c1(), 200, {}, False),
+    "basin_p2_ssp3": (_basin_p2, 100, {"ssp": 3}, False),
+    "basin_llf": (lambda: W.basin_c1(), 100, {"flux": O.LLF}, False),
+    "ragged": (lambda: W.basin_c1(nx=13, ny=7), 50, {}, False),
+    "tiny": (lambda: W.basin_c1(nx=1, ny=1), 50, {}, False),
+    "coastal_wet_dry": (lambda: W.coastal_c2(n_tri=6000, seed=21, steps=200), 200, {}, True),
+    "coastal_drying": (_coastal_dry, 100, {}, True),
+    "ssp5_llf": (_ssp5, 100, {"flux": O.LLF, "ssp": 5}, False),
+    "river_onto_dry_land": (lambda: W.river_basin(q=(0.05, 0.0), ramp_s=60.0, wet=False), 200, {}, True),
+    "river_wet": (lambda: W.river_basin(), 200, {}, True),
+    "gridded_rain_pressure": (_coastal_grid_press, 50, {}, False),
+    "graded_p2_20k": (lambda: W.graded_c3(n_tri=20_000, steps=100), 100, {}, False),
+    "hurricane_20k": (lambda: W.hurricane_c5(n_tri=20_000), 100, {}, False),
+    "flume": (lambda: W.inclined_plane("B", duration=1.0), 1500, {"dt": 1e-3}, False),
+}
+
+
+@functools.lru_cache(maxsize=None)
+def _oracle(case):
+    make, steps, opt, _ = CASES[case]
+    w = make()
+    ref = O.from_workload(w, flux=opt.get("flux", O.ROE), ssp=opt.get("ssp"), dt=opt.get("dt"))
+    dt = opt.get("dt") or ref.cfl_dt(w.cfl)
+    ref.set_dt(dt)
+    ref.step(steps)
+    return w, dt, ref.state(), ref.dry(), ref.ledger()
+
+
+@pytest.mark.parametrize("prec", [D.FP64, D.MIXED])
+@pytest.mark.parametrize("case", list(CASES))
+def test_every_form_matches_the_oracle(case, prec):
+    w, dt, want, want_dry, rl = _oracle(case)
+    _, steps, opt, check_dry = CASES[case]
+    states = []
+    for form in FORMS:
+        dev = D.from_workload(w, precision=prec, flux=opt.get("flux", O.ROE), ssp_stages=opt.get("ssp"), dt=dt,
+                              block=128, waves=1, split=form)
+        dev.step(steps)
+        dev.sync()
+        assert dev.launch() == (128, 1, form)
+        got = dev.state()
+        states.append(got)
+        if prec == D.FP64:
+            err = max(np.abs(got[:, v] - want[:, v]).max() / max(1.0, np.abs(want[:, v]).max()) for v in range(3))
+            assert err <= FP64_TOL, (case, form, err)
+            if check_dry:
+                assert np.array_equal(dev.dry(), want_dry), (case, form)
+        else:
+            ez = np.abs(got[:, 0] - want[:, 0]).max()
+            eq = np.abs(got[:, 1:] - want[:, 1:]).max()
+            assert ez <= MIXED_TOL and eq <= MIXED_TOL, (case, form, ez, eq)
+        led = dev.ledger()
+        if case == "flume":  # initially dry: the balance is judged in absolute volume (m^3)
+            assert abs(led["V"] - led["V0"] - led["rain_in"] - led["bdry_in"]) < 1e-12, (case, form, led)
+        else:
+            assert led["rel_err"] < 1e-12, (case, form, led)
+        assert led["steps"] == steps
+        # booked boundary inflow: FP64 against the oracle's; mixed only where it is prescribed
+        # (river edges: the mixed path carries edge lengths in FP32, 6e-8)
+        if rl["bdry_in"] != 0.0 and (prec == D.FP64 or case.startswith("river")):
+            tol = 1e-9 if prec == D.FP64 else 1e-6
+            assert abs(led["bdry_in"] - rl["bdry_in"]) <= tol * max(abs(rl["bdry_in"]), abs(rl["rain_in"])), (case, form)
+        dev.close()

@@ -348,12 +348,15 @@ def test_quadratic_friction_bathtub_short():
 # ----------------------------------------------------------- launch shapes, edge cases ----
 @pytest.mark.parametrize("prec", [D.FP64, D.MIXED])
 def test_launch_shapes_give_identical_bits(prec):
-    """Block size and waves do not change a single bit; fused and split agree to rounding."""
+    """Block size and waves do not change a single bit; the fused, split and tile forms agree to
+    rounding."""
     w = W.coastal_c2(n_tri=5000, seed=5, steps=30)
     both = []
-    for split in (0, 1):
+    for split in (0, 1, 2):
         outs = []
         for block, waves in ((64, 1), (128, 2), (256, 1), (256, 2)):
+            if split == 2 and block == 256 and prec == D.FP64:
+                continue  # the FP64 tile form's shared memory does not fit 8 warps in one block
             dev = D.from_workload(w, precision=prec, block=block, waves=waves, split=split)
             dev.step(30)
             dev.sync()
@@ -363,7 +366,8 @@ def test_launch_shapes_give_identical_bits(prec):
             assert np.array_equal(o, outs[0])
         both.append(outs[0])
     tol = 1e-13 if prec == D.FP64 else 1e-5
-    assert np.abs(both[0] - both[1]).max() <= tol * max(1.0, np.abs(both[0]).max())
+    for other in both[1:]:
+        assert np.abs(both[0] - other).max() <= tol * max(1.0, np.abs(both[0]).max())
 
 
 @pytest.mark.parametrize("prec", [D.FP64, D.MIXED])
@@ -371,8 +375,8 @@ def test_direct_launches_match_graph_replay(prec):
     """Steps replayed from CUDA graphs and steps launched kernel by kernel give identical bits
     (13 steps: one 8-step graph, five 1-step graphs)."""
     w = W.coastal_c2(n_tri=3000, seed=17, steps=13)
-    a = D.from_workload(w, precision=prec, block=128, split=1)
-    b = D.from_workload(w, precision=prec, block=128, split=1)
+    a = D.from_workload(w, precision=prec, block=128, split=2)
+    b = D.from_workload(w, precision=prec, block=128, split=2)
     b.set_graphs(False)
     a.step(13)
     b.step(13)
@@ -423,7 +427,7 @@ def test_negative_mean_depth_is_reported_not_trapped():
 
 # --------------------------------------------------------------------------- ensemble ----
 @pytest.mark.parametrize("prec", [D.FP64, D.MIXED])
-@pytest.mark.parametrize("split", [0, 1])
+@pytest.mark.parametrize("split", [0, 1, 2])
 def test_ensemble_members_match_solo_runs(prec, split):
     """Batching does not change a bit: each member of an ensemble, run with the same kernels
     (launch shape fixed on both sides), ends bit-identical to its solo run."""
