@@ -211,10 +211,9 @@ int dgswe_get_ledger(dgswe_h, dgswe_ledger* out);
 int dgswe_volume(dgswe_h, double* out);
 
 /* No counterpart in the paper: the total water volume of dgswe_volume, for callers that cannot
- * allocate device memory -- inside CUDA stream capture (cudaMalloc and cudaFree are not
- * capturable), with all device memory drawn from their own pool or caching allocator, or in
- * loops that must not stall on the device-wide synchronisation of cudaFree.  This entry point
- * allocates nothing.
+ * allocate device memory -- callers whose device memory all comes from their own pool or caching
+ * allocator, and loops that must not stall on the device-wide synchronisation that cudaFree
+ * implies.  This entry point allocates nothing.
  *   w0_dev    [n] device array: mode-0 coefficients of zeta (row 0 of dgswe_get_state_device);
  *   area_dev  [n] device array: element areas [m^2];
  *   out_dev   device pointer to one double, receives sum_e area_e * w0_e / sqrt(2);
@@ -223,8 +222,9 @@ int dgswe_volume(dgswe_h, double* out);
  * keeps until exit; n may be 0 .. 16,777,216, larger n returns DGSWE_EINVAL.  All calls share
  * that array (each call writes every slot it reads), so calls whose kernels overlap on the GPU
  * race: order them on one stream.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress, with that device current); make that first call before any
- * stream capture.  Pointers must belong to the current device. */
+ * address (cudaGetSymbolAddress, with that device current) and keeps it for the life of the
+ * process; after cudaDeviceReset on that device the kept address is stale, and this entry point
+ * must not be called there again.  Pointers must belong to the current device. */
 int dgswe_volume_sum_noalloc(const double* w0_dev, const double* area_dev, int64_t n, double* out_dev,
                              void* cuda_stream);
 

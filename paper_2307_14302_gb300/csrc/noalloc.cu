@@ -4,10 +4,10 @@
 // two-pass FP64 reduction (Neumaier-compensated per thread, fixed-order merges, per-block
 // partial sums, one final block) with its partials held in a file-scope device array instead,
 // so a call never allocates or frees device memory.  That matters to callers that cannot call
-// cudaMalloc/cudaFree: code between cudaStreamBeginCapture and cudaStreamEndCapture (allocation
-// calls are not capturable there), code whose device memory all comes from its own pool or
-// caching allocator, and loops that must not stall on the implicit device synchronisation of
-// cudaFree.
+// cudaMalloc/cudaFree: code whose device memory all comes from its own pool or caching
+// allocator, and loops that must not stall on the implicit device synchronisation of cudaFree.
+// The scratch array's device address is looked up once per device and kept; it is stale after a
+// cudaDeviceReset of that device.
 #include <cuda_runtime.h>
 
 #include <cstdio>

@@ -1,8 +1,8 @@
 """The allocation-free volume entry point (dgswe_volume_sum_noalloc) against dgswe_volume.
 
-Callers that cannot allocate device memory (inside CUDA stream capture, or drawing all memory
-from their own pool) get the same total water volume from this entry point, which keeps its
-partial sums in a fixed device array.  Two calls in a row reuse that array; each must agree with
+Callers that cannot allocate device memory (all of it drawn from their own pool or caching
+allocator, or loops that must not stall on cudaFree) get the same total water volume from this
+entry point, which keeps its partial sums in a fixed device array.  Two calls in a row reuse that array; each must agree with
 dgswe_volume on the same state within the mass-ledger tolerance (1e-12 relative).  This file is
 collected last, and passes alone in a fresh process too.
 """
