@@ -59,7 +59,8 @@ def parse_args(argv=None):
                          "event pair instead of --steps (the state is several GB, far above L2)")
     ap.add_argument("--ens-scenarios", type=int, default=64, help="ensemble size (0: no ensemble measurement)")
     ap.add_argument("--ens-steps", type=int, default=500)
-    ap.add_argument("--ens-fp64-steps", type=int, default=10, help="FP64 steps timed per scenario")
+    ap.add_argument("--ens-fp64-steps", type=int, default=0,
+                    help="FP64 steps timed per scenario (0: all --ens-steps steps, no scaling)")
     return ap.parse_args(argv)
 
 
@@ -155,24 +156,16 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------ roofline ----
-def stage_bytes_per_element(precision: str, p: int, rain_from_nodes: bool, nodes_per_elem: float,
-                            pressure: bool = False):
-    """Algorithmic DRAM bytes one stage launch moves per element: own record in and out, static
-    geometry and connectivity, the step-initial record on stages > 0, node data (rain, pressure
-    set-up).  Neighbour records are L2 hits (Hilbert-ordered mesh) and are not counted."""
-    np_ = (p + 1) * (p + 2) // 2
-    if precision == "mixed":
-        rec = 16 * (4 if 3 * np_ + 7 <= 16 else 8)
-        static = 16 + 48
-        xy = 8
-    else:
-        rec = 16 * (8 if 3 * np_ + 4 <= 16 else 12)
-        static = 16 + 80
-        xy = 16
-    rain = (16 + xy * nodes_per_elem) if (rain_from_nodes or pressure) else 0.0
-    first = rec + static + rain + rec
-    later = first + rec
-    return first, later
+def step_bytes_per_element(precision: str, p: int) -> float:
+    """Algorithmic bytes per element and SSP-RK step, the count of the hot-path scope table: per
+    step the state is read three times and written twice (5 x 40 B mixed, 5 x 72 B FP64 at p = 1)
+    and the static data is read twice (2 x ~100 B mixed, 2 x ~160 B FP64): 400 B mixed, 680 B
+    FP64 at p = 1; p = 2 moves twice as many.  Neighbour records are L2 hits and not counted."""
+    return (400.0 if precision == "mixed" else 680.0) * (2.0 if p == 2 else 1.0)
+
+
+FORM_KERNEL = {0: "stage_kernel (fused)", 1: "edge_kernel + stage_kernel (split)", 2: "tile_kernel"}
+FORM_PROFILE = {0: "stage_kernel", 1: "stage_kernel", 2: "tile_kernel"}
 
 
 def load_peaks():
@@ -400,15 +393,14 @@ def our_arm(args, ws, rank, local):
     value = units / t_max
     clocks = clk.summary()
 
-    # roofline of the stage kernel: algorithmic bytes per launch / average launch duration
-    nodes_per_elem = w.mesh.n_nodes / E
-    rain_nodes = w.storm is not None or w.rain_grid is not None
-    b0, b1 = stage_bytes_per_element("mixed", p, rain_nodes, nodes_per_elem, w.pressure is not None)
-    bytes_per_launch = E * (b0 + (stages - 1) * b1) / stages
+    # roofline of the stage kernel: algorithmic bytes per launch (scope-table count per element and
+    # step, over the stages) / average stage time measured with the events above
+    bytes_per_launch = E * step_bytes_per_element("mixed", p) / stages
     launch_s = t_mixed / (args.steps * stages)
     peak, peak_kind = load_peaks()
     achieved = bytes_per_launch / launch_s / 1e9
-    traffic = profiled_traffic(WORKLOADS[args.workload][2], E) if WORKLOADS[args.workload][2] else None
+    summary = f"{FORM_PROFILE[split]}_mixed_p{p}_{args.workload}.md"
+    traffic = profiled_traffic(summary, E, split)
 
     # ---- end to end through the public API: state in from pinned host memory, one step,
     # state back to pinned host memory, every step
@@ -476,8 +468,12 @@ def our_arm(args, ws, rank, local):
                        "simulated_s": led["t"], "mass_balance_rel_err": led["rel_err"]},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "peak_source": peak_kind, "kernel": f"stage_kernel<{p},Roe,Mixed>",
-                         "bytes_per_launch": bytes_per_launch, "avg_launch_us": 1e6 * launch_s},
+                         "peak_source": peak_kind, "kernel": f"{FORM_KERNEL[split]}, p={p}, Roe, mixed",
+                         "bytes_per_launch": bytes_per_launch,
+                         "bytes_model": f"{step_bytes_per_element('mixed', p):.0f} B per element and step "
+                                        f"(scope table) over {stages} stages",
+                         "traffic_source": summary if traffic is not None else None,
+                         "avg_launch_us": 1e6 * launch_s},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
@@ -569,14 +565,13 @@ def ensemble_measure(args, ws, rank, dev, stream, flush):
         torch.cuda.synchronize(dev)
         return a.elapsed_time(b) / 1e3
 
-    # members (mixed, fixed launch shape: no per-member autotuning); each also timed solo
+    # members (mixed, each autotuned), each also timed solo over the same k steps
     members, solo = [], 0.0
-    k_solo = 20
     for w in mine:
-        m = D.from_workload(w, precision=D.MIXED, stream=stream.cuda_stream, block=64, waves=1, split=0)
+        m = D.from_workload(w, precision=D.MIXED, stream=stream.cuda_stream)
         m.step(3)
         flush.zero_()
-        solo += timed(lambda: m.step(k_solo)) * k / k_solo
+        solo += timed(lambda: m.step(k))
         members.append(m)
     ens = D.Ensemble(members, device=dev.index, stream=stream.cuda_stream)
     for m in members:
@@ -592,13 +587,14 @@ def ensemble_measure(args, ws, rank, dev, stream, flush):
     block, waves, split = ens.launch()
     ens.close()
 
-    # the same scenarios as sequential plain FP64 GPU runs (k64 steps timed each, scaled to k)
+    # the same scenarios as sequential plain FP64 GPU runs (the FP64 path's launch form, autotuned)
+    k64 = min(k, args.ens_fp64_steps) if args.ens_fp64_steps > 0 else k
     seq64 = 0.0
     for w in mine:
-        s64 = D.from_workload(w, precision=D.FP64, stream=stream.cuda_stream, block=128, waves=1, split=1)
+        s64 = D.from_workload(w, precision=D.FP64, stream=stream.cuda_stream)
         s64.step(2)
         flush.zero_()
-        seq64 += timed(lambda: s64.step(args.ens_fp64_steps)) * k / args.ens_fp64_steps
+        seq64 += timed(lambda: s64.step(k64)) * k / k64
         s64.close()
 
     dof = sum(w.dof for w in mine)
@@ -614,9 +610,10 @@ def ensemble_measure(args, ws, rank, dev, stream, flush):
         "elements_total": int(sum(w.mesh.n_tri for w in all_w)), "elements_rank0": n_tri,
         "ms_per_step": 1e3 * t_max / k,
         "sequential_mixed": {"value": n_all * k / t_solo, "unit": "scenario-steps/s",
-                             "note": f"each scenario alone, {k_solo} steps timed, scaled to {k}"},
+                             "note": f"each scenario alone (autotuned), all {k} steps timed"},
         "sequential_fp64": {"value": n_all * k / t_seq64, "unit": "scenario-steps/s",
-                            "note": f"each scenario alone on the FP64 path, {args.ens_fp64_steps} steps timed, scaled to {k}"},
+                            "note": (f"each scenario alone on the FP64 path, all {k} steps timed" if k64 == k else
+                                     f"each scenario alone on the FP64 path, {k64} steps timed, scaled to {k}")},
         "speedup_vs_sequential_fp64": t_seq64 / t_max,
         "launch": {"block": block, "waves": waves, "split": split},
         "mass_balance_rel_err_max": rel, "mesh_generation_s": t_gen,
@@ -628,7 +625,7 @@ def s_dt(led):
     return led["t"] / max(1, led["steps"])
 
 
-def profiled_traffic(summary, n_elem):
+def profiled_traffic(summary, n_elem, form=0):
     """DRAM bytes per stage launch from a committed ncu summary (dram__bytes_read.sum +
     dram__bytes_write.sum of one capture, scaled to n_elem), or None when the summary is missing
     or was taken on a different kernel source."""
@@ -641,6 +638,9 @@ def profiled_traffic(summary, n_elem):
     m_hash = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", txt)
     m_bpe = re.search(r"dram_bytes_per_element_launch:\s*([0-9.eE+]+)", txt)
     if not m_hash or not m_bpe or m_hash.group(1) != kernel_hash():
+        return None
+    m_form = re.search(r"launch_form:\s*([0-9])", txt)
+    if m_form and int(m_form.group(1)) != form:
         return None
     return float(m_bpe.group(1)) * n_elem
 
@@ -659,7 +659,7 @@ def profiled_fp64_flops(split):
         return None
     txt = open(path).read()
     m_hash = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", txt)
-    key = "fp64_flops_per_element_stage_split" if split else "fp64_flops_per_element_stage_fused"
+    key = "fp64_flops_per_element_stage_" + {0: "fused", 1: "split", 2: "tile"}[split]
     m = re.search(key + r":\s*([0-9.eE+]+)", txt)
     if not m_hash or not m or m_hash.group(1) != kernel_hash():
         return None
@@ -670,7 +670,7 @@ def kernel_hash():
     import hashlib
 
     h = hashlib.sha256()
-    for f in ("stage.cuh", "args.h", "layout.h"):
+    for f in ("stage.cuh", "tile.cuh", "args.h", "layout.h"):
         h.update(open(os.path.join(ROOT, "paper_2307_14302_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

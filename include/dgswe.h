@@ -178,8 +178,11 @@ int dgswe_set_state(dgswe_h, const double* zeta, const double* qx, const double*
  * bit.  The state is kept as given (a state read back from the solver satisfies the positive-
  * depth constraints of Sec. 2.4 already); only the mean depths and wet/dry flags are derived
  * from it.  Mesh, fields, forcing, dt, time and ledger are kept (the ledger then also holds the
- * injected change).  Returns after the stream has consumed the arrays.  For restarts and for
- * couplings that exchange the state every step. */
+ * injected change).  For restarts and for couplings that exchange the state every step.
+ * Page-locked (pinned) host arrays are read by the packing kernel itself, over the host link, in
+ * stream order: the call returns at once, and the arrays must not change until the next call
+ * that synchronises (dgswe_sync, dgswe_get_state, dgswe_get_ledger, ...).  Other host memory is
+ * staged through a device buffer and the call returns after the stream has consumed it. */
 int dgswe_load_state(dgswe_h, const double* zeta, const double* qx, const double* qy);
 
 /* Enqueues n_steps SSP-RK steps on the context's stream (CUDA graph replay) and returns
@@ -192,12 +195,30 @@ int dgswe_sync(dgswe_h);
 /* The fixed time step [s] in *dt. */
 int dgswe_get_dt(dgswe_h, double* dt);
 
-/* Copies the modal state to host arrays [Np][n_tri] (synchronises the stream). */
+/* Copies the modal state to host arrays [Np][n_tri] (synchronises the stream).  Page-locked
+ * (pinned) arrays are written by the unpacking kernel itself over the host link; other host
+ * memory is staged through a device buffer. */
 int dgswe_get_state(dgswe_h, double* zeta, double* qx, double* qy);
 
 /* Copies the modal state into caller-owned device memory: each pointer to Np*n_tri doubles,
  * written on the context's stream (no host round trip). */
 int dgswe_get_state_device(dgswe_h, double* zeta_dev, double* qx_dev, double* qy_dev);
+
+/* Device memory that the element records need (the state w^n and the two Runge-Kutta stage
+ * buffers, each rounded up to 256 bytes), in *bytes.  Valid after dgswe_set_state or
+ * dgswe_ensemble_create. */
+int dgswe_record_bytes(dgswe_h, uint64_t* bytes);
+
+/* Places the element records in caller-owned device memory (for example a framework's tensor
+ * storage), so that the caller's allocator provides the solver's largest arrays: dev must be
+ * device memory of the context's device, 256-byte aligned, at least dgswe_record_bytes long.  The
+ * current state is copied there and every later step reads and writes it in place; the library
+ * never frees it.  The caller keeps it alive and unmodified until it binds other memory, unbinds
+ * (dev = NULL: the library allocates its own records again and copies the state back) or destroys
+ * the context.  A later dgswe_set_state keeps the binding when the memory is still large enough and
+ * drops it otherwise.  Returns DGSWE_EINVAL for memory that is too small, unaligned or not device
+ * memory of the context's device; synchronises the stream. */
+int dgswe_bind_device(dgswe_h, void* dev, uint64_t bytes);
 
 /* Per-element dry flags (Sec. 2.4) [n_tri] as 0/1 bytes. */
 int dgswe_get_dry(dgswe_h, uint8_t* dry);

@@ -76,12 +76,24 @@ struct Stage {
 struct DevBuf {
   void* p = nullptr;
   size_t n = 0;
-  ~DevBuf() { if (p) cudaFree(p); }
+  bool own = true;  // false: memory bound by the caller (dgswe_bind_device), never freed here
+  ~DevBuf() { release(); }
+  void release() {
+    if (p && own) cudaFree(p);
+    p = nullptr;
+    own = true;
+  }
   int alloc(size_t bytes) {
-    if (p) { cudaFree(p); p = nullptr; }
+    release();
     n = bytes;
     if (bytes == 0) return 0;
     return cudaMalloc(&p, bytes) == cudaSuccess ? 0 : -1;
+  }
+  void bind(void* ptr, size_t bytes) {
+    release();
+    p = ptr;
+    n = bytes;
+    own = false;
   }
   template <class T>
   T* as() const { return reinterpret_cast<T*>(p); }
@@ -114,7 +126,7 @@ struct dgswe_ctx {
   std::vector<long long> eoff, noff;
   DevBuf rec[3], nbr, geo, nodes, node_xy, xy64, hbn, rain_e, rain_node, node_scen, lim, scen, tile_scen, tile_meta, xy0,
       ledger, ctl,
-      eorig, grids, rivers, scratch,
+      einv, grids, rivers, scratch,
       gather_buf, edges, slots;
   long long nedges = 0;
   int ntiles = 0;                          // 32-element tiles
@@ -133,11 +145,13 @@ struct dgswe_ctx {
   cudaGraphExec_t g1 = nullptr, gK = nullptr;
   int K = 8;
   long long launches = 0;
+  char* bound = nullptr;           // caller memory holding the three record buffers (dgswe_bind_device)
+  size_t bound_bytes = 0;
 
   ~dgswe_ctx() {
     DeviceGuard dg_(device);
     DevBuf* bufs[] = {&rec[0], &rec[1], &rec[2], &nbr, &geo, &nodes, &node_xy, &xy64, &hbn, &rain_e, &scen,
-                      &tile_scen, &tile_meta, &xy0, &ledger, &ctl, &eorig, &grids, &rivers, &scratch, &gather_buf,
+                      &tile_scen, &tile_meta, &xy0, &ledger, &ctl, &einv, &grids, &rivers, &scratch, &gather_buf,
                       &edges, &slots,
                       &rain_node, &node_scen, &lim};
     for (DevBuf* b : bufs) b->alloc(0);
@@ -296,6 +310,20 @@ static int upload_all_tables(int p) {
   return 0;
 }
 
+// one record buffer's share of bound memory: its size rounded up to 256 bytes
+static size_t record_stride(size_t rbytes) { return (rbytes + 255) / 256 * 256; }
+
+// device-visible address of page-locked host memory (zero-copy), or nullptr when p is pageable
+// memory, device memory or not known to the runtime
+static const void* host_mapped(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return (at.type == cudaMemoryTypeHost && at.devicePointer) ? at.devicePointer : nullptr;
+}
+
 // --------------------------------------------------------------------- device layout -------
 template <class T>
 static void put(std::vector<uint32_t>& w, size_t at, T v) {
@@ -326,7 +354,7 @@ static int build_layout(dgswe_h h) {
   // host images
   const size_t rw = 4 * (size_t)h->rv, gw = 4 * (size_t)h->gv;  // 32-bit words per element
   std::vector<uint32_t> rec(rw * E, 0u), geo(gw * E, 0u);
-  std::vector<int32_t> nbr(4 * E, -1), nodes(4 * E, 0), eorig(E, 0);
+  std::vector<int32_t> nbr(4 * E, -1), nodes(4 * E, 0), einv(E, 0);
   std::vector<float> xy0f(mx ? 2 * E : 0, 0.f);     // first vertex of each element (tile form)
   std::vector<double> xy0d(mx ? 0 : 2 * E, 0.0);
   std::vector<double> xy64(2 * N), hbn(N);
@@ -353,7 +381,7 @@ static int build_layout(dgswe_h h) {
     for (int e = 0; e < M.ne; ++e) {
       const long long ge = eo + e;
       const int32_t* v = &M.tri[3 * (size_t)e];
-      eorig[ge] = M.eorig[e];
+      einv[eo + M.eorig[e]] = e;  // caller element -> position in the library's order
       if (mx) {
         xy0f[2 * ge] = (float)M.x[v[0]];
         xy0f[2 * ge + 1] = (float)M.y[v[0]];
@@ -458,10 +486,16 @@ static int build_layout(dgswe_h h) {
   CU(cudaMemset(h->slots.p, 0, 16 * (size_t)sv * 3 * E));
   // upload
   const size_t rbytes = 16 * (size_t)h->rv * E;
-  for (int b = 0; b < 3; ++b)
-    if (h->rec[b].alloc(rbytes)) return fail(DGSWE_ENOMEM, "device allocation of %zu bytes failed", rbytes);
+  if (h->bound && h->bound_bytes >= 3 * record_stride(rbytes)) {  // keep the caller's binding
+    for (int b = 0; b < 3; ++b) h->rec[b].bind(h->bound + b * record_stride(rbytes), rbytes);
+  } else {
+    h->bound = nullptr;
+    h->bound_bytes = 0;
+    for (int b = 0; b < 3; ++b)
+      if (h->rec[b].alloc(rbytes)) return fail(DGSWE_ENOMEM, "device allocation of %zu bytes failed", rbytes);
+  }
   if (h->geo.alloc(16 * (size_t)h->gv * E) || h->nbr.alloc(16 * (size_t)E) || h->nodes.alloc(16 * (size_t)E) ||
-      h->xy64.alloc(16 * (size_t)N) || h->hbn.alloc(8 * (size_t)N) || h->eorig.alloc(4 * (size_t)E) ||
+      h->xy64.alloc(16 * (size_t)N) || h->hbn.alloc(8 * (size_t)N) || h->einv.alloc(4 * (size_t)E) ||
       h->node_xy.alloc(mx ? 8 * (size_t)N : 16 * (size_t)N) || h->rain_e.alloc(mx ? 4 * (size_t)E : 8 * (size_t)E) ||
       h->ctl.alloc(sizeof(Ctl)) || h->scen.alloc(sizeof(ScenDev) * ns) || h->grids.alloc(4 * grids.size()) ||
       h->rivers.alloc(8 * rivers.size()) || h->node_scen.alloc(4 * (size_t)N) ||
@@ -476,7 +510,7 @@ static int build_layout(dgswe_h h) {
   CU(cudaMemcpy(h->nodes.p, nodes.data(), 4 * nodes.size(), cudaMemcpyHostToDevice));
   CU(cudaMemcpy(h->xy64.p, xy64.data(), 8 * xy64.size(), cudaMemcpyHostToDevice));
   CU(cudaMemcpy(h->hbn.p, hbn.data(), 8 * hbn.size(), cudaMemcpyHostToDevice));
-  CU(cudaMemcpy(h->eorig.p, eorig.data(), 4 * eorig.size(), cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(h->einv.p, einv.data(), 4 * einv.size(), cudaMemcpyHostToDevice));
   if (h->xy0.alloc(mx ? 8 * (size_t)E : 16 * (size_t)E)) return fail(DGSWE_ENOMEM, "device allocation failed");
   if (mx) CU(cudaMemcpy(h->xy0.p, xy0f.data(), 4 * xy0f.size(), cudaMemcpyHostToDevice));
   else CU(cudaMemcpy(h->xy0.p, xy0d.data(), 8 * xy0d.size(), cudaMemcpyHostToDevice));
@@ -1158,18 +1192,31 @@ static int gather_state(dgswe_h h, size_t s, double* z, double* x, double* y, bo
   const long long n = h->sc[s].m.ne, b = h->eoff[s];
   const size_t cnt = (size_t)h->np * n;
   double *dz = z, *dx = x, *dy = y;
+  bool staged = false;
   if (!device_out) {
-    if (h->gather_buf.n < 3 * cnt * sizeof(double))
-      if (h->gather_buf.alloc(3 * cnt * sizeof(double))) return fail(DGSWE_ENOMEM, "gather buffer");
-    dz = h->gather_buf.as<double>();
-    dx = dz + cnt;
-    dy = dx + cnt;
+    // page-locked host arrays are written directly by the gather kernel (coalesced, over the
+    // host link); other host memory goes through a device staging buffer and three copies
+    const void *mz = host_mapped(z), *mx = host_mapped(x), *my = host_mapped(y);
+    if (mz && mx && my) {
+      dz = (double*)mz;
+      dx = (double*)mx;
+      dy = (double*)my;
+    } else {
+      staged = true;
+      if (h->gather_buf.n < 3 * cnt * sizeof(double))
+        if (h->gather_buf.alloc(3 * cnt * sizeof(double))) return fail(DGSWE_ENOMEM, "gather buffer");
+      dz = h->gather_buf.as<double>();
+      dx = dz + cnt;
+      dy = dx + cnt;
+    }
   }
-  cudaError_t ce = mixed(h) ? launch_gather<Mixed>(h->prm.p, h->rec[0].as<uint4>(), b, n, h->eorig.as<int32_t>() + b, dz, dx, dy, h->stream)
-                            : launch_gather<Fp64>(h->prm.p, h->rec[0].as<uint4>(), b, n, h->eorig.as<int32_t>() + b, dz, dx, dy, h->stream);
+  cudaError_t ce = mixed(h) ? launch_gather<Mixed>(h->prm.p, h->rec[0].as<uint4>(), b, n, h->einv.as<int32_t>() + b, dz, dx, dy, h->stream)
+                            : launch_gather<Fp64>(h->prm.p, h->rec[0].as<uint4>(), b, n, h->einv.as<int32_t>() + b, dz, dx, dy, h->stream);
   if (ce != cudaSuccess) return fail(DGSWE_ECUDA, "gather launch: %s", cudaGetErrorString(ce));
   h->launches++;
-  if (!device_out) {
+  if (!device_out && !staged) {
+    CU(cudaStreamSynchronize(h->stream));
+  } else if (!device_out) {
     CU(cudaMemcpyAsync(z, dz, cnt * 8, cudaMemcpyDeviceToHost, h->stream));
     CU(cudaMemcpyAsync(x, dx, cnt * 8, cudaMemcpyDeviceToHost, h->stream));
     CU(cudaMemcpyAsync(y, dy, cnt * 8, cudaMemcpyDeviceToHost, h->stream));
@@ -1202,15 +1249,29 @@ int dgswe_load_state(dgswe_h h, const double* z, const double* x, const double* 
   DeviceGuard dg_(h->device);
   const long long n = h->sc[0].m.ne, b = h->eoff[0];
   const size_t cnt = (size_t)h->np * n;
-  if (h->gather_buf.n < 3 * cnt * sizeof(double))
-    if (h->gather_buf.alloc(3 * cnt * sizeof(double))) return fail(DGSWE_ENOMEM, "staging buffer");
-  double* dz = h->gather_buf.as<double>();
-  CU(cudaMemcpyAsync(dz, z, cnt * 8, cudaMemcpyHostToDevice, h->stream));
-  CU(cudaMemcpyAsync(dz + cnt, x, cnt * 8, cudaMemcpyHostToDevice, h->stream));
-  CU(cudaMemcpyAsync(dz + 2 * cnt, y, cnt * 8, cudaMemcpyHostToDevice, h->stream));
+  // page-locked host arrays are read directly by the scatter kernel (coalesced, over the host
+  // link) and the call returns at once; other memory is staged through three copies first
+  const void *mz = host_mapped(z), *mx = host_mapped(x), *my = host_mapped(y);
+  const bool direct = mz && mx && my;
+  const double *sz, *sx, *sy;
+  if (direct) {
+    sz = (const double*)mz;
+    sx = (const double*)mx;
+    sy = (const double*)my;
+  } else {
+    if (h->gather_buf.n < 3 * cnt * sizeof(double))
+      if (h->gather_buf.alloc(3 * cnt * sizeof(double))) return fail(DGSWE_ENOMEM, "staging buffer");
+    double* dz = h->gather_buf.as<double>();
+    CU(cudaMemcpyAsync(dz, z, cnt * 8, cudaMemcpyHostToDevice, h->stream));
+    CU(cudaMemcpyAsync(dz + cnt, x, cnt * 8, cudaMemcpyHostToDevice, h->stream));
+    CU(cudaMemcpyAsync(dz + 2 * cnt, y, cnt * 8, cudaMemcpyHostToDevice, h->stream));
+    sz = dz;
+    sx = dz + cnt;
+    sy = dz + 2 * cnt;
+  }
   cudaError_t ce;
   if (mixed(h)) {
-    ce = launch_scatter<Mixed>(h->prm.p, h->rec[0].as<uint4>(), b, n, h->eorig.as<int32_t>() + b, dz, dz + cnt, dz + 2 * cnt, h->stream);
+    ce = launch_scatter<Mixed>(h->prm.p, h->rec[0].as<uint4>(), b, n, h->einv.as<int32_t>() + b, sz, sx, sy, h->stream);
     if (ce == cudaSuccess) {
       StageArgs<Mixed> a = make_args<Mixed>(h, 0, 1);
       a.in = a.out = h->rec[0].as<uint4>();
@@ -1218,7 +1279,7 @@ int dgswe_load_state(dgswe_h h, const double* z, const double* x, const double* 
       ce = launch_prepare<Mixed>(h->prm.p, a, b, b + n, h->stream);
     }
   } else {
-    ce = launch_scatter<Fp64>(h->prm.p, h->rec[0].as<uint4>(), b, n, h->eorig.as<int32_t>() + b, dz, dz + cnt, dz + 2 * cnt, h->stream);
+    ce = launch_scatter<Fp64>(h->prm.p, h->rec[0].as<uint4>(), b, n, h->einv.as<int32_t>() + b, sz, sx, sy, h->stream);
     if (ce == cudaSuccess) {
       StageArgs<Fp64> a = make_args<Fp64>(h, 0, 1);
       a.in = a.out = h->rec[0].as<uint4>();
@@ -1228,7 +1289,53 @@ int dgswe_load_state(dgswe_h h, const double* z, const double* x, const double* 
   }
   if (ce != cudaSuccess) return fail(DGSWE_ECUDA, "load_state launch: %s", cudaGetErrorString(ce));
   h->launches += 2;
+  if (!direct) CU(cudaStreamSynchronize(h->stream));
+  return 0;
+}
+
+int dgswe_record_bytes(dgswe_h h, uint64_t* bytes) {
+  if (int rc = check_handle(h)) return rc;
+  if (!h->ready) return fail(DGSWE_ESTATE, "set_state must precede record_bytes");
+  if (!bytes) return fail(DGSWE_EINVAL, "null output");
+  *bytes = 3 * record_stride(16 * (size_t)h->rv * h->E);
+  return 0;
+}
+
+int dgswe_bind_device(dgswe_h h, void* dev, uint64_t bytes) {
+  if (int rc = check_handle(h)) return rc;
+  if (!h->ready) return fail(DGSWE_ESTATE, "set_state must precede bind_device");
+  DeviceGuard dg_(h->device);
+  const size_t rbytes = 16 * (size_t)h->rv * h->E, st = record_stride(rbytes);
+  if (dev) {
+    if (bytes < 3 * st) return fail(DGSWE_EINVAL, "bind_device: %llu bytes given, %zu needed", (unsigned long long)bytes, 3 * st);
+    if ((uintptr_t)dev % 256 != 0) return fail(DGSWE_EINVAL, "bind_device: the memory must be 256-byte aligned");
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, dev) != cudaSuccess || at.type != cudaMemoryTypeDevice || at.device != h->device) {
+      cudaGetLastError();
+      return fail(DGSWE_EINVAL, "bind_device: not device memory of device %d", h->device);
+    }
+  }
   CU(cudaStreamSynchronize(h->stream));
+  if (int rc = fold_ledger(h)) return rc;  // the captured graphs name the old buffers
+  // the state w^n moves to the new home; the two stage buffers need no contents
+  DevBuf keep;
+  keep.bind(h->rec[0].p, h->rec[0].n);
+  keep.own = h->rec[0].own;
+  h->rec[0].own = false;  // handed to keep, freed (if owned) after the copy
+  if (dev) {
+    char* base = static_cast<char*>(dev);
+    for (int b = 0; b < 3; ++b) {
+      if (b > 0) h->rec[b].release();
+      h->rec[b].bind(base + b * st, rbytes);
+    }
+  } else {
+    for (int b = 0; b < 3; ++b)
+      if (h->rec[b].alloc(rbytes)) return fail(DGSWE_ENOMEM, "device allocation of %zu bytes failed", rbytes);
+  }
+  CU(cudaMemcpyAsync(h->rec[0].p, keep.p, rbytes, cudaMemcpyDeviceToDevice, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  h->bound = static_cast<char*>(dev);
+  h->bound_bytes = dev ? bytes : 0;
   return 0;
 }
 

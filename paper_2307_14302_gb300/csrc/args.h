@@ -104,14 +104,16 @@ template <class Pol>
 cudaError_t launch_dt(int p, const uint4* rec, const int4* nodes, const double* xy64, const double* hb_nodal,
                       long long begin, long long end, double cfl, double g, double H0, double* partials, int nblk,
                       cudaStream_t s);
-// modal state [Np][n] of scenario elements [begin, begin + n) in caller order (orig index)
+// modal state [Np][n] of scenario elements [begin, begin + n) in caller order; inv[c] is the
+// position of caller element c relative to begin.  The arrays may be device memory or
+// device-accessible page-locked host memory (coalesced in caller order).
 template <class Pol>
-cudaError_t launch_gather(int p, const uint4* rec, long long begin, long long n, const int32_t* orig, double* z,
+cudaError_t launch_gather(int p, const uint4* rec, long long begin, long long n, const int32_t* inv, double* z,
                           double* x, double* y, cudaStream_t s);
 
-// modal state [Np][n] (caller order) into the records of [begin, begin + n)
+// modal state [Np][n] (caller order) into the records of [begin, begin + n), same conventions
 template <class Pol>
-cudaError_t launch_scatter(int p, uint4* rec, long long begin, long long n, const int32_t* orig, const double* z,
+cudaError_t launch_scatter(int p, uint4* rec, long long begin, long long n, const int32_t* inv, const double* z,
                            const double* x, const double* y, cudaStream_t s);
 
 // Neumaier-compensated reduction of per-block partial pairs (shared by all precisions)

@@ -1753,53 +1753,57 @@ __global__ void __launch_bounds__(256) dt_kernel(const uint4* rec, const int4* n
   }
 }
 
+// modal state [Np][n] in caller order from the records of elements [begin, begin + n): thread c
+// writes caller element c (consecutive threads write consecutive addresses, which keeps the
+// stores coalesced when the arrays are page-locked host memory read over the C2C link) and reads
+// the record of inv[c], its position in the library's order
 template <int P, class Pol>
 __global__ void __launch_bounds__(256) gather_kernel(const uint4* rec, long long begin, long long n,
-                                                     const int32_t* orig, double* z, double* x, double* y) {
+                                                     const int32_t* inv, double* z, double* x, double* y) {
   constexpr int RV = Pol::template RV<P>, NS = np_of(P) - 1;
   const double s2 = 1.4142135623730951;  // mode-0 coefficient = sqrt(2) * mean
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
     Raw<RV> r;
-    load_raw<RV>(rec, begin + i, r);
+    load_raw<RV>(rec, begin + inv[c], r);
     Elem<P, Pol> E;
     unpack<P>(r, E);
-    const long long o = orig[i];
-    z[o] = s2 * acc_d(E.zb);
-    x[o] = s2 * acc_d(E.xb);
-    y[o] = s2 * acc_d(E.yb);
+    z[c] = s2 * acc_d(E.zb);
+    x[c] = s2 * acc_d(E.xb);
+    y[c] = s2 * acc_d(E.yb);
 #pragma unroll
     for (int m = 0; m < NS; ++m) {
-      z[(m + 1) * n + o] = (double)E.zs[m];
-      x[(m + 1) * n + o] = (double)E.xs[m];
-      y[(m + 1) * n + o] = (double)E.ys[m];
+      z[(m + 1) * n + c] = (double)E.zs[m];
+      x[(m + 1) * n + c] = (double)E.xs[m];
+      y[(m + 1) * n + c] = (double)E.ys[m];
     }
   }
 }
 
-// modal state [Np][n] in caller order -> records of elements [begin, begin + n); bathymetry
-// modes are kept, depth and flags are recomputed by the positive-depth pass that follows
+// modal state [Np][n] in caller order -> records of elements [begin, begin + n) (thread c reads
+// caller element c, coalesced); bathymetry modes are kept, depth and flags are recomputed by the
+// positive-depth pass that follows
 template <int P, class Pol>
-__global__ void __launch_bounds__(256) scatter_kernel(uint4* rec, long long begin, long long n, const int32_t* orig,
+__global__ void __launch_bounds__(256) scatter_kernel(uint4* rec, long long begin, long long n, const int32_t* inv,
                                                       const double* z, const double* x, const double* y) {
   constexpr int RV = Pol::template RV<P>, NS = np_of(P) - 1;
   const double is2 = 0.7071067811865476;  // mean = mode-0 coefficient / sqrt(2)
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+    const long long e = begin + inv[c];
     Raw<RV> r;
-    load_raw<RV>(rec, begin + i, r);
+    load_raw<RV>(rec, e, r);
     Elem<P, Pol> E;
     unpack<P>(r, E);
-    const long long o = orig[i];
-    acc_set(E.zb, is2 * z[o]);
-    acc_set(E.xb, is2 * x[o]);
-    acc_set(E.yb, is2 * y[o]);
+    acc_set(E.zb, is2 * z[c]);
+    acc_set(E.xb, is2 * x[c]);
+    acc_set(E.yb, is2 * y[c]);
 #pragma unroll
     for (int m = 0; m < NS; ++m) {
-      E.zs[m] = (typename Pol::T)z[(m + 1) * n + o];
-      E.xs[m] = (typename Pol::T)x[(m + 1) * n + o];
-      E.ys[m] = (typename Pol::T)y[(m + 1) * n + o];
+      E.zs[m] = (typename Pol::T)z[(m + 1) * n + c];
+      E.xs[m] = (typename Pol::T)x[(m + 1) * n + c];
+      E.ys[m] = (typename Pol::T)y[(m + 1) * n + c];
     }
     pack<P>(E, r);
-    store_raw<RV>(rec, begin + i, r);
+    store_raw<RV>(rec, e, r);
   }
 }
 
@@ -1899,19 +1903,19 @@ static inline int grid_for(long long n, int block) {
     return cudaGetLastError();                                                                               \
   }                                                                                                          \
   template <>                                                                                                \
-  cudaError_t launch_gather<POL>(int p, const uint4* rec, long long b, long long n, const int32_t* orig,      \
+  cudaError_t launch_gather<POL>(int p, const uint4* rec, long long b, long long n, const int32_t* inv,       \
                                  double* z, double* x, double* y, cudaStream_t s) {                          \
     int g = grid_for(n, 256);                                                                                \
-    if (p == 1) gather_kernel<1, POL><<<g, 256, 0, s>>>(rec, b, n, orig, z, x, y);                           \
-    else gather_kernel<2, POL><<<g, 256, 0, s>>>(rec, b, n, orig, z, x, y);                                  \
+    if (p == 1) gather_kernel<1, POL><<<g, 256, 0, s>>>(rec, b, n, inv, z, x, y);                            \
+    else gather_kernel<2, POL><<<g, 256, 0, s>>>(rec, b, n, inv, z, x, y);                                   \
     return cudaGetLastError();                                                                               \
   }                                                                                                          \
   template <>                                                                                                \
-  cudaError_t launch_scatter<POL>(int p, uint4* rec, long long b, long long n, const int32_t* orig,          \
+  cudaError_t launch_scatter<POL>(int p, uint4* rec, long long b, long long n, const int32_t* inv,           \
                                   const double* z, const double* x, const double* y, cudaStream_t s) {       \
     int g = grid_for(n, 256);                                                                                \
-    if (p == 1) scatter_kernel<1, POL><<<g, 256, 0, s>>>(rec, b, n, orig, z, x, y);                          \
-    else scatter_kernel<2, POL><<<g, 256, 0, s>>>(rec, b, n, orig, z, x, y);                                 \
+    if (p == 1) scatter_kernel<1, POL><<<g, 256, 0, s>>>(rec, b, n, inv, z, x, y);                           \
+    else scatter_kernel<2, POL><<<g, 256, 0, s>>>(rec, b, n, inv, z, x, y);                                  \
     return cudaGetLastError();                                                                               \
   }
 

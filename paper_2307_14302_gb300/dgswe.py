@@ -60,7 +60,7 @@ EXPORTS = [
     "dgswe_create", "dgswe_set_params", "dgswe_set_mesh", "dgswe_set_fields", "dgswe_set_rain_nodal",
     "dgswe_set_rain_parametric", "dgswe_set_rain_grid", "dgswe_set_tide", "dgswe_set_river", "dgswe_set_pressure_setup",
     "dgswe_set_state", "dgswe_load_state", "dgswe_step", "dgswe_sync", "dgswe_get_dt", "dgswe_get_state", "dgswe_get_state_device",
-    "dgswe_get_dry", "dgswe_get_ledger", "dgswe_volume", "dgswe_volume_sum_noalloc", "dgswe_ensemble_create", "dgswe_ensemble_step",
+    "dgswe_get_dry", "dgswe_get_ledger", "dgswe_volume", "dgswe_record_bytes", "dgswe_bind_device", "dgswe_volume_sum_noalloc", "dgswe_ensemble_create", "dgswe_ensemble_step",
     "dgswe_ensemble_get_state", "dgswe_ensemble_get_ledger", "dgswe_set_launch", "dgswe_get_launch",
     "dgswe_set_graphs", "dgswe_launch_count", "dgswe_destroy", "dgswe_last_error",
 ]
@@ -104,6 +104,8 @@ def lib():
         "dgswe_get_dry": ([_h, _u8], C.c_int),
         "dgswe_get_ledger": ([_h, C.POINTER(Ledger)], C.c_int),
         "dgswe_volume": ([_h, _d], C.c_int),
+        "dgswe_record_bytes": ([_h, C.POINTER(C.c_uint64)], C.c_int),
+        "dgswe_bind_device": ([_h, C.c_void_p, C.c_uint64], C.c_int),
         "dgswe_volume_sum_noalloc": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p], C.c_int),
         "dgswe_ensemble_create": ([C.POINTER(_h), C.c_int32, C.POINTER(_h), C.c_int, C.c_void_p], C.c_int),
         "dgswe_ensemble_step": ([_h, C.c_int64], C.c_int),
@@ -256,6 +258,15 @@ class Solver:
         v = C.c_double()
         _check(lib().dgswe_volume(self.h, C.byref(v)))
         return v.value
+
+    def record_bytes(self) -> int:
+        v = C.c_uint64()
+        _check(lib().dgswe_record_bytes(self.h, C.byref(v)))
+        return v.value
+
+    def bind_device(self, ptr, nbytes):
+        """Element records in caller-owned device memory (e.g. a torch tensor's storage); ptr 0 unbinds."""
+        _check(lib().dgswe_bind_device(self.h, C.c_void_p(ptr) if ptr else None, int(nbytes)))
 
     def set_launch(self, block, waves=1, split=1):
         _check(lib().dgswe_set_launch(self.h, block, waves, split))
