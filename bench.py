@@ -526,14 +526,10 @@ def graded_subsample_error(args, stream):
 
 
 def deal_scenarios(sizes, ws):
-    """Owner rank of each scenario: largest first, each to the least-loaded rank (ties: lowest)."""
-    load = [0] * ws
-    owner = [0] * len(sizes)
-    for i in sorted(range(len(sizes)), key=lambda i: (-sizes[i], i)):
-        r = min(range(ws), key=lambda k: (load[k], k))
-        load[r] += sizes[i]
-        owner[i] = r
-    return owner
+    """Owner rank of each scenario (the library's dealing: largest first to the least-loaded rank)."""
+    from paper_2307_14302_gb300.ensemble import deal_scenarios as deal
+
+    return deal(sizes, ws)
 
 
 def ensemble_measure(args, ws, rank, dev, stream, flush):
@@ -553,7 +549,8 @@ def ensemble_measure(args, ws, rank, dev, stream, flush):
     all_w = W.ensemble_c4(n_scen=args.ens_scenarios, steps=args.ens_steps)
     t_gen = time.perf_counter() - t_gen
     owner = deal_scenarios([x.mesh.n_tri for x in all_w], ws)
-    mine = [x for x, r in zip(all_w, owner) if r == rank]
+    mine_idx = [i for i, r in enumerate(owner) if r == rank]
+    mine = [all_w[i] for i in mine_idx]
     k = args.ens_steps
 
     def timed(fn):
@@ -583,7 +580,11 @@ def ensemble_measure(args, ws, rank, dev, stream, flush):
     t_ens = timed(lambda: ens.step(k))
     barrier(ws)
     ens.sync()
-    rel = max(abs(ens.ledger(i)["rel_err"]) for i in range(len(mine)))
+    # every scenario's ledger gathered on rank 0 (host objects over the process group)
+    from paper_2307_14302_gb300.ensemble import gather_results
+
+    gathered = gather_results({i: (None, ens.ledger(j)) for j, i in enumerate(mine_idx)}, ws, rank)
+    rel = max(abs(led["rel_err"]) for _, led in gathered) if gathered is not None else None
     block, waves, split = ens.launch()
     ens.close()
 
