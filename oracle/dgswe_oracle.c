@@ -28,7 +28,11 @@
  *   - ghost states: land mirrors q.n and carries zero mass flux; ocean takes zeta = tide(t)
  *     with the interior q; river edges (Eq. river_bc) carry exactly the prescribed normal
  *     discharge as the mass component of the flux, and the momentum components of the
- *     numerical flux between the interior trace and the ghost (zeta, -q_river n); "exact" boundaries (verification only) take a prescribed field;
+ *     numerical flux between the interior trace and the ghost (zeta, -q_river n); an interior
+ *     edge listed as a river edge is an internal river boundary (Sec. 2.3): the river enters the
+ *     element to the left of the listed direction a -> b and the element on the other side sees
+ *     a wall (an interior land edge is a wall on both sides); "exact" boundaries (verification
+ *     only) take a prescribed field;
  *   - bathymetry is continuous and piecewise linear from nodal values;
  *   - area rule exact to degree 2p+1 (p=1: 7-point degree 3; p=2: 7-point degree 5), edge
  *     rule Gauss-Legendre with p+1 points;
@@ -350,6 +354,33 @@ int orc_set_mesh(orc_t* o, int nn, const double* xy, int ne, const int32_t* tri,
     if (i + 1 < 3 * ne && he[i + 1].key == he[i].key) {
       o->ede[2 * ned + 1] = he[i + 1].e; o->edj[2 * ned + 1] = he[i + 1].j;
       o->edt[ned] = -1;
+      /* an interior edge listed as a boundary: a river edge (Sec. 2.3, internal river boundaries)
+       * lets the river enter the element to the left of its listed direction a -> b, and that
+       * element's neighbour sees a wall; a land edge is a wall on both sides */
+      int lo = 0, hi = nb - 1, bi = -1;
+      while (lo <= hi) {
+        int mid = (lo + hi) / 2;
+        if (bk[mid].key == he[i].key) { bi = bk[mid].e; break; }
+        if (bk[mid].key < he[i].key) lo = mid + 1; else hi = mid - 1;
+      }
+      if (bi >= 0) {
+        if (btype[bi] != ORC_BT_RIVER && btype[bi] != ORC_BT_LAND) { free(he); free(bk); return -3; }
+        int h0 = i, h1 = i + 1;  /* h0: the receiving half-edge (traversed a -> b) */
+        if (o->tri[3 * he[h0].e + he[h0].j] != bedge[2 * bi]) { h0 = i + 1; h1 = i; }
+        o->ede[2 * ned] = he[h0].e; o->edj[2 * ned] = he[h0].j;
+        o->edn[2 * ned] = o->tri[3 * he[h0].e + he[h0].j];
+        o->edn[2 * ned + 1] = o->tri[3 * he[h0].e + (he[h0].j + 1) % 3];
+        o->ede[2 * ned + 1] = -1; o->edj[2 * ned + 1] = -1;
+        o->edt[ned] = btype[bi];
+        o->eds[ned] = bseg ? bseg[bi] : 0;
+        ++ned;
+        o->ede[2 * ned] = he[h1].e; o->edj[2 * ned] = he[h1].j;
+        o->edn[2 * ned] = o->tri[3 * he[h1].e + he[h1].j];
+        o->edn[2 * ned + 1] = o->tri[3 * he[h1].e + (he[h1].j + 1) % 3];
+        o->ede[2 * ned + 1] = -1; o->edj[2 * ned + 1] = -1;
+        o->edt[ned] = ORC_BT_LAND;
+        o->eds[ned] = 0;
+      }
       i += 2;
     } else {
       o->ede[2 * ned + 1] = -1; o->edj[2 * ned + 1] = -1;

@@ -7,7 +7,9 @@
 // 4. edges are paired by their node pair; each local edge j (vertex j -> j+1) gets a code:
 //    (neighbour << 2 | neighbour's local edge), -1 for land, -2 - segment for ocean edges,
 //    -2 - MAXSEG - segment for river edges (Sec. 2.1: ocean = specified elevation, land = zero
-//    normal flow, river = specified normal flow);
+//    normal flow, river = specified normal flow).  An interior edge listed as a river edge is an
+//    internal river boundary (Sec. 2.3): the river enters the triangle to the left of the listed
+//    direction, whose neighbour sees a wall there; an interior land edge is a wall on both sides;
 // 5. scaled outward normals ln_j = (dy, -dx) of each local edge are computed in FP64 from node
 //    differences, so the two sides of an interior edge hold exactly opposite values.
 #include <algorithm>
@@ -154,6 +156,28 @@ int build_mesh(int nn, const double* xy, int ne, const int32_t* tri_in, int nb, 
       }
       M.code[3 * (size_t)p.e + p.j] = (q.e << 2) | q.j;
       M.code[3 * (size_t)q.e + q.j] = (p.e << 2) | p.j;
+      // an interior edge listed as a boundary: a river edge (internal river boundary) lets the
+      // river enter the triangle to the left of its listed direction a -> b, whose neighbour sees
+      // a wall; a land edge is a wall on both sides
+      auto it = std::lower_bound(bsorted.begin(), bsorted.end(), p.k);
+      if (it != bsorted.end() && *it == p.k) {
+        const int32_t b = bid[it - bsorted.begin()];
+        if (btype[b] == DGSWE_BT_OCEAN) {
+          snprintf(buf, sizeof buf, "set_mesh: boundary edge %d is interior; only river and land edges may be", b);
+          err = buf;
+          return DGSWE_EINVAL;
+        }
+        const bool p_in = M.tri[3 * (size_t)p.e + p.j] == (int32_t)nnew[bedge[2 * b]];
+        const HE& in = p_in ? p : q;
+        const HE& wall = p_in ? q : p;
+        if (btype[b] == DGSWE_BT_RIVER) {
+          M.code[3 * (size_t)in.e + in.j] = -2 - MAXSEG - bseg[b];
+          M.nriv = std::max(M.nriv, bseg[b] + 1);
+        } else {
+          M.code[3 * (size_t)in.e + in.j] = -1;
+        }
+        M.code[3 * (size_t)wall.e + wall.j] = -1;
+      }
     } else {
       const HE& p = he[i];
       int32_t c = -1;

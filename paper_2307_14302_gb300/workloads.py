@@ -376,10 +376,13 @@ def basin_c1(seed=1, hump=True, rain=True, mirror=False, nx=20, ny=10) -> Worklo
     )
 
 
-def river_basin(q=(2.0, 0.5), ramp_s=600.0, nx=20, ny=10, wet=True, seed=7) -> Workload:
+def river_basin(q=(2.0, 0.5), ramp_s=600.0, nx=20, ny=10, wet=True, seed=7, internal=False) -> Workload:
     """The basin of ``basin_c1`` (no hump, no rain) with two river inflow segments on its walls:
     segment 0 on the x = 0 wall for 1 km <= y <= 3 km, segment 1 on the y = 5 km wall for
-    6 km <= x <= 8 km.  Discharge per unit width ramps linearly from 0 to q over ramp_s seconds
+    6 km <= x <= 8 km.  With ``internal`` a third segment (q gives its discharge as a third value)
+    lies inside the basin, on the interior edges of the line y = 2.5 km for 4 km <= x <= 6 km,
+    listed west to east so that the river enters the triangles north of the line (an internal
+    river boundary).  Discharge per unit width ramps linearly from 0 to q over ramp_s seconds
     (records every ramp_s / 4 s).  With wet=False the bathymetry rises above the geoid near the
     x = 0 river so that the river first flows onto dry land; the CFL number is then 0.04, since
     explicit Manning friction on films of about H0 (tau ~ 3/s) needs dt * tau < 1."""
@@ -393,7 +396,17 @@ def river_basin(q=(2.0, 0.5), ramp_s=600.0, nx=20, ny=10, wet=True, seed=7) -> W
     btype[r0 | r1] = RIVER
     bseg[r0] = 0
     bseg[r1] = 1
-    w.mesh = Mesh(m.xy, m.tri, m.bedge, btype, bseg)
+    bedge = m.bedge
+    if internal:
+        lx, ly = 10_000.0, 5_000.0
+        dx = lx / nx
+        j = int(round(0.5 * ly / (ly / ny)))
+        inner = np.array([(j * (nx + 1) + i, j * (nx + 1) + i + 1) for i in range(nx + 1)
+                          if 4000.0 - 1e-6 <= i * dx and (i + 1) * dx <= 6000.0 + 1e-6], np.int32)
+        bedge = np.concatenate([bedge, inner])
+        btype = np.concatenate([btype, np.full(len(inner), RIVER, np.int32)])
+        bseg = np.concatenate([bseg, np.full(len(inner), 2, np.int32)])
+    w.mesh = Mesh(m.xy, m.tri, bedge, btype, bseg)
     if not wet:
         x = m.xy[:, 0]
         w.hb = w.hb - 8.0 * np.clip(1.0 - x / 2500.0, 0.0, None)

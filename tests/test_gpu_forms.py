@@ -71,6 +71,7 @@ CASES = {
     "ssp5_llf": (_ssp5, 100, {"flux": O.LLF, "ssp": 5}, False),
     "river_onto_dry_land": (lambda: W.river_basin(q=(0.05, 0.0), ramp_s=60.0, wet=False), 200, {}, True),
     "river_wet": (lambda: W.river_basin(), 200, {}, True),
+    "river_internal": (lambda: W.river_basin(q=(2.0, 0.5, 1.5), internal=True), 200, {}, True),
     "gridded_rain_pressure": (_coastal_grid_press, 50, {}, False),
     "graded_p2_20k": (lambda: W.graded_c3(n_tri=20_000, steps=100), 100, {}, False),
     "hurricane_20k": (lambda: W.hurricane_c5(n_tri=20_000), 100, {}, False),

@@ -301,6 +301,26 @@ def test_river_boundaries_match_oracle(prec, wet):
     assert np.array_equal(dev.dry(), ref.dry())
 
 
+@pytest.mark.parametrize("prec", [D.FP64, D.MIXED])
+def test_internal_river_boundary_matches_oracle(prec):
+    """Sec. 2.3 internal river boundaries: two wall rivers and one river on interior edges of the
+    basin (entering the triangles north of its line); state, dry flags and the booked inflow
+    against the oracle."""
+    w = W.river_basin(q=(2.0, 0.5, 1.5), ramp_s=600.0, internal=True)
+    ref, dev = _pair(w, 200, prec)
+    got, want = dev.state(), ref.state()
+    if prec == D.FP64:
+        assert _fp64_err(got, want) <= FP64_TOL
+    else:
+        ez, eq = _mixed_err(got, want)
+        assert ez <= MIXED_TOL and eq <= MIXED_TOL, (ez, eq)
+    led, rl = dev.ledger(), ref.ledger()
+    assert led["rel_err"] < 1e-12
+    tol = 1e-9 if prec == D.FP64 else 1e-6
+    assert abs(led["bdry_in"] - rl["bdry_in"]) <= tol * abs(rl["bdry_in"])
+    assert np.array_equal(dev.dry(), ref.dry())
+
+
 # ---------------------------------------------------------- rain on a flume (Sec. 3.2) --
 @pytest.mark.parametrize("prec", [D.FP64, D.MIXED])
 def test_inclined_plane_runoff_matches_oracle(prec):

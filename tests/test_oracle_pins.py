@@ -312,6 +312,36 @@ def test_river_with_zero_discharge_keeps_the_lake_at_rest():
     assert np.abs(st[:, 0]).max() < 1e-12 and np.abs(st[:, 1:]).max() < 1e-11
 
 
+def test_internal_river_inflow_is_the_prescribed_discharge_and_enters_one_side():
+    """Sec. 2.3: river boundaries may lie on interior edges.  An interior river segment (listed
+    west to east along y = 2.5 km) admits exactly its prescribed discharge -- the volume gained is
+    q L T^2 / (2 T_ramp), the same closed form as on the walls -- into the triangles north of the
+    line; the triangles south of it see a wall, so at first only the northern side rises."""
+    w = W.river_basin(q=(0.0, 0.0, 1.5), ramp_s=600.0, internal=True)
+    o = O.from_workload(w)
+    c = w.mesh.xy[w.mesh.tri].mean(axis=1)
+    north = (c[:, 1] > 2500.0) & (c[:, 1] < 2750.0) & (c[:, 0] > 4000.0) & (c[:, 0] < 6000.0)
+    south = (c[:, 1] < 2500.0) & (c[:, 1] > 2250.0) & (c[:, 0] > 4000.0) & (c[:, 0] < 6000.0)
+    assert north.sum() == 4 and south.sum() == 4
+    o.step(5)
+    z = o.state()[:, 0, 0]
+    assert z[north].min() > 0.0 and z[north].min() > 10.0 * np.abs(z[south]).max()
+    o.step(195)
+    led = o.ledger()
+    T = led["t"]
+    expect = 1.5 * 2000.0 * T * T / 1200.0
+    assert abs((led["V"] - led["V0"]) - expect) <= 1e-9 * expect
+    assert abs(led["bdry_in"] - expect) <= 1e-9 * expect
+    assert led["rel_err"] < 1e-14
+    # with zero discharge the internal river edge keeps the lake at rest
+    w0 = W.river_basin(q=(0.0, 0.0, 0.0), internal=True)
+    o0 = O.from_workload(w0)
+    assert np.abs(o0.rhs()).max() < 1e-12
+    o0.step(100)
+    st = o0.state()
+    assert np.abs(st[:, 0]).max() < 1e-12 and np.abs(st[:, 1:]).max() < 1e-11
+
+
 def test_river_onto_dry_land_wets_it_and_conserves_mass():
     w = W.river_basin(q=(0.05, 0.0), ramp_s=60.0, wet=False)
     o = O.from_workload(w)
