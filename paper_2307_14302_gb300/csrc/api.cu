@@ -690,7 +690,6 @@ static StageArgs<Pol> make_args(dgswe_h h, int stage, int tune) {
     return c == 0.0 || (c > 0.0 && std::frexp(c, &ex) == 0.5);
   };
   a.pow2 = (pow2_or_0(st.a_n) && pow2_or_0(st.a_in)) ? 1 : 0;
-  a.cst_f = (float)st.c;
   a.tune = tune;
   a.friction = h->prm.friction;
   split_ff(st.a_n, a.a_n_hi, a.a_n_lo);

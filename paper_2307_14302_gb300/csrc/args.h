@@ -59,7 +59,6 @@ struct StageArgs {
   int pow2;                // a_n and a_in are 0 or powers of two (exact float-float scaling)
   float a_n_hi, a_n_lo, a_in_hi, a_in_lo;  // Shu-Osher coefficients as float-float
   double a_n, a_in;
-  float cst_f;             // stage time as a fraction of dt
   double cst;
   T g, H0, cf;
 };

@@ -997,12 +997,12 @@ __device__ __forceinline__ T grid_rain(const ScenDev& S, const ForcingT<T>& F, T
 template <class Pol>
 __global__ void __launch_bounds__(256) node_rain_kernel(const StageArgs<Pol> a, long long nn) {
   using T = typename Pol::T;
-  const T stepc = (T)a.ctl->step + (sizeof(T) == 4 ? (T)a.cst_f : (T)a.cst);
+  const double stepd = (double)a.ctl->step + a.cst;
   for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < nn; n += (long long)gridDim.x * blockDim.x) {
     const ScenDev& S = a.scen[a.node_scen[n]];
     if (S.rain_kind != 3) continue;
     const ForcingT<T>& F = forcing<T>(S);
-    const T t = F.t0 + stepc * F.dt;
+    const T t = (T)(S.d.t0 + stepd * S.d.dt);  // stage time, formed in FP64
     a.rain_node[n] = grid_rain<T>(S, F, a.node_xy[2 * n], a.node_xy[2 * n + 1], t);
   }
 }
@@ -1180,7 +1180,7 @@ __global__ void DG_STAGE_BOUNDS stage_kernel(const StageArgs<Pol> a) {
   const int lane = tid & 31;
   const long long gw = (long long)blockIdx.x * (B >> 5) + (tid >> 5);
   const long long W = (long long)gridDim.x * (B >> 5);
-  const T stepc = (T)a.ctl->step + (sizeof(T) == 4 ? (T)a.cst_f : (T)a.cst);
+  const double stepd = (double)a.ctl->step + a.cst;
   const T g = a.g, H0 = a.H0;
   Acc rain_acc = acc_make<Acc>(0.f, 0.f, 0.0), bdry_acc = acc_make<Acc>(0.f, 0.f, 0.0);
   int cur = -1;
@@ -1195,7 +1195,7 @@ __global__ void DG_STAGE_BOUNDS stage_kernel(const StageArgs<Pol> a) {
     const ForcingT<T>& F = forcing<T>(S);
     const long long e = tile * TILE + lane;
     if (e >= S.elem_end) continue;
-    const T t = F.t0 + stepc * F.dt;
+    const T t = (T)(S.d.t0 + stepd * S.d.dt);  // stage time, formed in FP64
 
     const int4 nb = __ldg(a.nbr + e);
     // stage what the edge loop and the combination need, asynchronously
