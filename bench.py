@@ -54,6 +54,8 @@ def parse_args(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--launch", default="", help="block,waves,split of the stage kernels (default: autotuned)")
+    ap.add_argument("--fp64-launch", default="", help="block,waves,split of the FP64 leg (default: autotuned)")
+    ap.add_argument("--limiter", action="store_true", help="apply the optional slope limiter after every stage")
     ap.add_argument("--sim-hours", type=float, default=0.0,
                     help="hurricane: time the whole run of this many simulated hours (steps from dt) in one "
                          "event pair instead of --steps (the state is several GB, far above L2)")
@@ -252,12 +254,15 @@ WORKLOADS = {
 }
 
 
-def fixed_launch(args):
-    """Solver keyword arguments for --launch block,waves,split (empty: autotune)."""
-    if not args.launch:
-        return {}
-    block, waves, split = (int(v) for v in args.launch.split(","))
-    return {"block": block, "waves": waves, "split": split}
+def fixed_launch(args, spec=None):
+    """Solver keyword arguments for --launch block,waves,split (empty: autotune) and --limiter."""
+    spec = args.launch if spec is None else spec
+    kw = {"limiter": True} if args.limiter else {}
+    if not spec:
+        return kw
+    block, waves, split = (int(v) for v in spec.split(","))
+    kw.update(block=block, waves=waves, split=split)
+    return kw
 
 
 def make_workload(args):
@@ -423,7 +428,7 @@ def our_arm(args, ws, rank, local):
 
     # ---- FP64 path on the same workload
     k64 = args.fp64_steps or max(10, min(50, args.steps // 100))
-    s64 = D.from_workload(w, precision=D.FP64, stream=stream.cuda_stream)
+    s64 = D.from_workload(w, precision=D.FP64, stream=stream.cuda_stream, **fixed_launch(args, args.fp64_launch))
     s64.step(3)
     s64.sync()
     t64 = timed_steps(s64, k64)
