@@ -442,7 +442,7 @@ def our_arm(args, ws, rank, local):
     if fpe is not None:
         ach = fpe * E * stages * k64 / t64 / 1e12
         fp64["roofline"] = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                            "frac": ach / FP64_PEAK_TFLOPS, "peak_source": "nominal GB300 FP64 rate",
+                            "frac": ach / FP64_PEAK_TFLOPS, "peak_source": "nominal GB300 FP64 rate (recipe table)",
                             "flops_per_element_stage": fpe}
     s64.close()
 
@@ -660,7 +660,7 @@ def profiled_fp64_flops(split):
     ncu summary, or None when it is missing or was taken on a different kernel source."""
     import re
 
-    path = os.path.join(ROOT, "profiles", "stage_kernel_fp64_p1_coastal.md")
+    path = os.path.join(ROOT, "profiles", "fp64_kernels_p1_coastal.md")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
