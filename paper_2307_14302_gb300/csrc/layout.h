@@ -27,6 +27,7 @@ constexpr int MAXRIV = 8;   // river segments: river edge code -2 - MAXSEG - seg
 constexpr int MAXSTAGE = 5; // Runge-Kutta stages
 constexpr int MAXNP = 6;
 constexpr int MAXNQ = 7;
+constexpr int MAXNQP = 8;  // MAXNQ rounded up to an even number
 constexpr int MAXNG = 3;
 constexpr int TILE_ALIGN = 256;  // scenario element ranges start on multiples of this
 constexpr int TILE = 32;         // elements per warp tile
@@ -62,10 +63,14 @@ struct RefTab {
   T el[3][MAXNG][3];               // barycentric coordinates of those points
   T vphi[3][MAXNP];                // basis at the three vertices
   T vinv[2][3];                    // modal coefficients 1,2 of a linear function from vertex values
+  T vabs[MAXNP];                   // largest |basis| over the three vertices, per mode
   T mphi[3][MAXNP];                // basis at the midpoints of the three edges (slope limiter)
   T phi0;                          // constant mode value 1/sqrt(2)
-  T qphiT[MAXNP][MAXNQ];           // qphi transposed: consecutive area points of one mode adjacent
-  T qwphiT[MAXNP][MAXNQ];          // qw[q] * qphi[q][m], same order
+  // transposed copies for evaluating the area points two at a time: consecutive points of one
+  // mode adjacent, padded with zeros to an even number of points
+  T qwT[MAXNQP];                   // qw, padded
+  T qphiT[MAXNP][MAXNQP];          // qphi transposed
+  T qwphiT[MAXNP][MAXNQP];         // qw[q] * qphi[q][m], same order
 };
 
 // per-scenario forcing constants in the arithmetic type of a path

@@ -82,6 +82,17 @@ __device__ __forceinline__ double acc_diff(double a, double b) { return a - b; }
 __device__ __forceinline__ float acc_diff(ff a, ff b) { return ff_diff(a, b); }
 __device__ __forceinline__ double acc_add(double a, double b) { return a + b; }
 __device__ __forceinline__ ff acc_add(ff a, ff b) { return ff_add(a, b); }
+// a + b with one two-sum: the error is within a few ulps of the low word of the larger operand
+// (no cancellation between the low words is recovered); for sums of like-signed terms and small
+// increments, as in the stage combination and the ledgers
+__device__ __forceinline__ double acc_addf(double a, double b) { return a + b; }
+__device__ __forceinline__ ff acc_addf(ff a, ff b) {
+  ff s = two_sum(a.hi, b.hi);
+  return quick_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+// a + b rounded to the working precision (float: within an ulp, without the float-float sum)
+__device__ __forceinline__ double acc_sum_r(double a, double b) { return a + b; }
+__device__ __forceinline__ float acc_sum_r(ff a, ff b) { return __fadd_rn(__fadd_rn(a.hi, b.hi), __fadd_rn(a.lo, b.lo)); }
 __device__ __forceinline__ double acc_addr(double a, double b) { return a + b; }
 __device__ __forceinline__ ff acc_addr(ff a, float b) { return ff_add_f(a, b); }
 __device__ __forceinline__ double acc_mul(double a, double b) { return a * b; }
@@ -438,6 +449,39 @@ __device__ __forceinline__ Trace<typename Pol::T> trace_at(const Elem<P, Pol>& E
 template <int FLUX, class T>
 __device__ __forceinline__ void edge_flux(const Trace<T>& L, const Trace<T>& R, T dcRL, T nx, T ny, T g, T H0, T& fz,
                                           T& fx, T& fy) {
+  if constexpr (sizeof(T) == 4) {  // FP32: one reciprocal square root per side (as edge_flux_pair)
+    const float HsL = fmaxf(L.H, H0), HsR = fmaxf(R.H, H0);
+    const float rL = mufu_rsqrt(HsL), rR = mufu_rsqrt(HsR);
+    const float mL = L.qx * nx + L.qy * ny, mR = R.qx * nx + R.qy * ny;
+    const float unL = mL * (rL * rL), unR = mR * (rR * rR);
+    const float dz = (R.d - L.d) + dcRL;
+    const float dqx = R.qx - L.qx, dqy = R.qy - L.qy;
+    const float cx = 0.5f * (L.qx * unL + R.qx * unR);
+    const float cy = 0.5f * (L.qy * unL + R.qy * unR);
+    const float cz = 0.5f * (mL + mR);
+    const float sL = HsL * rL, sR = HsR * rR;
+    if (FLUX == 1) {
+      const float sg = fsqrt_pos(g);
+      const float lam = fmaxf(fabsf(unL) + sg * sL, fabsf(unR) + sg * sR);
+      fz = cz - 0.5f * lam * dz;
+      fx = cx - 0.5f * lam * dqx;
+      fy = cy - 0.5f * lam * dqy;
+      return;
+    }
+    const float is = frcp(sL + sR);
+    const float ut = (L.qx * rL + R.qx * rR) * is, vt = (L.qy * rL + R.qy * rR) * is;
+    const float c2 = 0.5f * g * (HsL + HsR);
+    const float ic = mufu_rsqrt(c2), c = c2 * ic;
+    const float utn = ut * nx + vt * ny, utt = vt * nx - ut * ny;
+    const float dqn = mR - mL, dqt = dqy * nx - dqx * ny;
+    const float w = (dqn - utn * dz) * ic;
+    const float a1 = 0.5f * (dz - w), a3 = 0.5f * (dz + w), a2 = dqt - utt * dz;
+    const float l1 = fabsf(utn - c) * a1, l2 = fabsf(utn) * a2, l3 = fabsf(utn + c) * a3;
+    fz = cz - 0.5f * (l1 + l3);
+    fx = cx - 0.5f * (l1 * (ut - c * nx) - l2 * ny + l3 * (ut + c * nx));
+    fy = cy - 0.5f * (l1 * (vt - c * ny) + l2 * nx + l3 * (vt + c * ny));
+    return;
+  }
   T HsL = max_r(L.H, H0), HsR = max_r(R.H, H0);
   T iL = frcp(HsL), iR = frcp(HsR);
   T uL = L.qx * iL, vL = L.qy * iL, uR = R.qx * iR, vR = R.qy * iR;
@@ -490,28 +534,33 @@ __device__ __forceinline__ f2 max2(f2 a, f2 b) { return make_float2(fmaxf(a.x, b
 __device__ __forceinline__ f2 abs2(f2 a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
 __device__ __forceinline__ f2 rcp2(f2 a) { return make_float2(frcp(a.x), frcp(a.y)); }
 __device__ __forceinline__ f2 sqrt2(f2 a) { return make_float2(fsqrt_pos(a.x), fsqrt_pos(a.y)); }
+__device__ __forceinline__ f2 rsqrt2(f2 a) { return make_float2(mufu_rsqrt(a.x), mufu_rsqrt(a.y)); }  // a > 0
 struct Trace2 {
   f2 d, H, qx, qy;  // two edge points
 };
 
-// edge_flux for two points at once (FP32): the same flux, written with packed operations
+// edge_flux for two points at once (FP32), written with packed operations and one reciprocal
+// square root per side: with r = 1/sqrt(Hs), 1/Hs = r^2, sqrt(Hs) = Hs r, the Roe velocity is
+// (q_L r_L + q_R r_R) / (sqrt(Hs_L) + sqrt(Hs_R)), u.n = (q.n)/Hs, and the jump of q.n is the
+// difference of the sides' q.n (the same quantities as edge_flux, fewer operations)
 template <int FLUX>
 __device__ __forceinline__ void edge_flux_pair(const Trace2& L, const Trace2& R, f2 dcRL, f2 nx, f2 ny, float g,
                                                float H0, f2& fz, f2& fx, f2& fy) {
   const f2 half = p2(0.5f), mhalf = p2(-0.5f);
   const f2 HsL = max2(L.H, p2(H0)), HsR = max2(R.H, p2(H0));
-  const f2 iL = rcp2(HsL), iR = rcp2(HsR);
-  const f2 uL = mul2(L.qx, iL), vL = mul2(L.qy, iL), uR = mul2(R.qx, iR), vR = mul2(R.qy, iR);
-  const f2 unL = fma2(uL, nx, mul2(vL, ny)), unR = fma2(uR, nx, mul2(vR, ny));
+  const f2 rL = rsqrt2(HsL), rR = rsqrt2(HsR);
+  const f2 iL = mul2(rL, rL), iR = mul2(rR, rR);
   const f2 mL = fma2(L.qx, nx, mul2(L.qy, ny)), mR = fma2(R.qx, nx, mul2(R.qy, ny));
+  const f2 unL = mul2(mL, iL), unR = mul2(mR, iR);
   const f2 dz = add2(sub2(R.d, L.d), dcRL);
   const f2 dqx = sub2(R.qx, L.qx), dqy = sub2(R.qy, L.qy);
   const f2 cx = mul2(half, fma2(L.qx, unL, mul2(R.qx, unR)));
   const f2 cy = mul2(half, fma2(L.qy, unL, mul2(R.qy, unR)));
   const f2 cz = mul2(half, add2(mL, mR));
-  if (FLUX == 1) {  // local Lax-Friedrichs
-    const f2 gg = p2(g);
-    const f2 lam = max2(add2(abs2(unL), sqrt2(mul2(gg, HsL))), add2(abs2(unR), sqrt2(mul2(gg, HsR))));
+  const f2 sL = mul2(HsL, rL), sR = mul2(HsR, rR);
+  if (FLUX == 1) {  // local Lax-Friedrichs: sqrt(g Hs) = sqrt(g) sqrt(Hs)
+    const f2 sg = p2(fsqrt_pos(g));
+    const f2 lam = max2(fma2(sg, sL, abs2(unL)), fma2(sg, sR, abs2(unR)));
     const f2 hl = mul2(mhalf, lam);
     fz = fma2(hl, dz, cz);
     fx = fma2(hl, dqx, cx);
@@ -519,13 +568,12 @@ __device__ __forceinline__ void edge_flux_pair(const Trace2& L, const Trace2& R,
     return;
   }
   // Roe: averages (arithmetic depth, sqrt-depth-weighted velocity), eigen-decomposition
-  const f2 sL = sqrt2(HsL), sR = sqrt2(HsR);
   const f2 is = rcp2(add2(sL, sR));
-  const f2 ut = mul2(fma2(sL, uL, mul2(sR, uR)), is), vt = mul2(fma2(sL, vL, mul2(sR, vR)), is);
-  const f2 c = sqrt2(mul2(p2(0.5f * g), add2(HsL, HsR)));
-  const f2 ic = rcp2(c);
+  const f2 ut = mul2(fma2(L.qx, rL, mul2(R.qx, rR)), is), vt = mul2(fma2(L.qy, rL, mul2(R.qy, rR)), is);
+  const f2 c2 = mul2(p2(0.5f * g), add2(HsL, HsR));
+  const f2 ic = rsqrt2(c2), c = mul2(c2, ic);
   const f2 utn = fma2(ut, nx, mul2(vt, ny)), utt = fma2(vt, nx, mul2(neg2(ut), ny));
-  const f2 dqn = fma2(dqx, nx, mul2(dqy, ny)), dqt = fma2(dqy, nx, mul2(neg2(dqx), ny));
+  const f2 dqn = sub2(mR, mL), dqt = fma2(dqy, nx, mul2(neg2(dqx), ny));
   const f2 w = mul2(fma2(neg2(utn), dz, dqn), ic);
   const f2 a1 = mul2(half, sub2(dz, w)), a3 = mul2(half, add2(dz, w)), a2 = fma2(neg2(utt), dz, dqt);
   const f2 l1 = mul2(abs2(sub2(utn, c)), a1), l2 = mul2(abs2(utn), a2), l3 = mul2(abs2(add2(utn, c)), a3);
@@ -639,8 +687,10 @@ __device__ bool positivity_fp64(double zbar, double& xbar, double& ybar, double*
 // above H0 at every vertex is case 1 (unchanged, wet; at p = 2 its quadratic modes are scaled
 // by the continuous blend factor when the shallowest vertex is below 2 H0), one whose mean
 // depth is clearly below H0 with a vertex clearly below H0 is case 2 (flat depth, dry, no
-// momentum: the zeta slopes become minus the bathymetry slopes).  Only elements near the
-// threshold take the FP64 operator.
+// momentum: the zeta slopes become minus the bathymetry slopes), and one with a vertex clearly
+// below H0 but a mean depth clearly above it is case 3 (depth moved to the lowest vertex, wet).
+// Every depth test is thereby decided as in FP64: FP32 decides only outside a band wider than
+// the FP32 evaluation error; elements inside it (and near ties of case 3) take the FP64 operator.
 template <int P, class Pol>
 __device__ __forceinline__ void apply_positivity(Elem<P, Pol>& E, const Geo<Pol>& G, long long e,
                                                  const StageArgs<Pol>& a, int* err) {
@@ -648,26 +698,23 @@ __device__ __forceinline__ void apply_positivity(Elem<P, Pol>& E, const Geo<Pol>
   constexpr int NS = np_of(P) - 1;
   const RefTab<T>& tab = ctab<T, P>();
   const T H0 = a.H0;
-  const typename Pol::Acc Hbar = acc_add(E.zb, G.hbm);
-  const T Hb = acc_r(Hbar);
+  const T Hb = acc_sum_r(E.zb, G.hbm);  // mean depth
   constexpr int NL = NS < 2 ? NS : 2;  // linear modes among zs
   bool need64 = true, dry = false;
   if (sizeof(T) == 4) {
-    T hmin = T(3.0e38), bound = abs_r(Hb);
+    T hv[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      T v = Hb, b = 0;
+      T v = Hb;
 #pragma unroll
-      for (int m = 0; m < NL; ++m) {
-        v = fma(E.zs[m], tab.vphi[i][m + 1], v);
-        b += abs_r(E.zs[m] * tab.vphi[i][m + 1]);
-      }
+      for (int m = 0; m < NL; ++m) v = fma(E.zs[m], tab.vphi[i][m + 1], v);
       v = fma(E.hb1, tab.vphi[i][1], v);
-      v = fma(E.hb2, tab.vphi[i][2], v);
-      b += abs_r(E.hb1 * tab.vphi[i][1]) + abs_r(E.hb2 * tab.vphi[i][2]);
-      hmin = fminf(hmin, v);
-      bound = fmaxf(bound, b);
+      hv[i] = fma(E.hb2, tab.vphi[i][2], v);
     }
+    // bound on the magnitudes summed at any vertex: |Hb| + sum_m (|zs_m| + |hb_m|) max_i |phi_m(x_i)|
+    T bound = (abs_r(E.hb1) + abs_r(E.zs[0])) * tab.vabs[1];
+    if (NL > 1) bound = fma(abs_r(E.hb2) + abs_r(E.zs[NL > 1 ? 1 : 0]), tab.vabs[2], bound);
+    const T hmin = fminf(hv[0], fminf(hv[1], hv[2]));
     const T tol = T(4.0e-6) * (abs_r(Hb) + bound);
     if (hmin - tol > H0) {
       need64 = false;  // case 1
@@ -691,6 +738,34 @@ __device__ __forceinline__ void apply_positivity(Elem<P, Pol>& E, const Geo<Pol>
       for (int m = 0; m < NS; ++m) E.xs[m] = E.ys[m] = T(0);
       E.xb = acc_make<typename Pol::Acc>(0.f, 0.f, 0.0);
       E.yb = acc_make<typename Pol::Acc>(0.f, 0.f, 0.0);
+    } else if (hmin + tol < H0 && Hb > H0 * T(1.00001)) {
+      // case 3, partially wet: the lowest vertex is raised to H0 and the deficit taken from the
+      // others (M Pi^d); no vertex ends dry, so the momentum is unchanged (M Pi^f) and the element
+      // is wet.  Formed as vertex changes dH_i (summing to zero: the mean is kept) and added to the
+      // slope modes through the vertex-to-mode map, so the bathymetry cancels and FP32 keeps the
+      // precision of the small depths.  A near tie of the two upper vertices (where the operator
+      // depends on their order) is left to the FP64 operator.
+      const T h0 = hmin, h2 = fmaxf(hv[0], fmaxf(hv[1], hv[2]));
+      const T h1 = fmaxf(fminf(hv[0], hv[1]), fminf(fmaxf(hv[0], hv[1]), hv[2]));  // median
+      const T d = H0 - h0;
+      const bool split = h1 - T(0.5) * d >= H0;  // the other two vertices share the deficit
+      if (split || h2 - h1 > tol) {
+        need64 = false;
+        const T e = H0 - h1;
+        T dh[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+          dh[i] = (hv[i] == h0) ? d : (split ? T(-0.5) * d : (hv[i] == h2 ? -(d + e) : e));
+#pragma unroll
+        for (int m = 0; m < NL; ++m)
+          E.zs[m] += tab.vinv[m][0] * dh[0] + tab.vinv[m][1] * dh[1] + tab.vinv[m][2] * dh[2];
+#pragma unroll
+        for (int m = 2; m < NS; ++m) {  // p = 2: the blend factor is zero below H0
+          E.zs[m] = T(0);
+          E.xs[m] = T(0);
+          E.ys[m] = T(0);
+        }
+      }
     }
   }
   if (need64) {
@@ -718,7 +793,7 @@ __device__ __forceinline__ void apply_positivity(Elem<P, Pol>& E, const Geo<Pol>
         acc_set(E.yb, yb);
       }
     }
-    if (acc_d(Hbar) < 0.0) atomicOr(err, ERR_NEGDEPTH);
+    if (acc_d(E.zb) + acc_d(G.hbm) < 0.0) atomicOr(err, ERR_NEGDEPTH);
   }
   E.Hb = Hb;
   E.flags = dry ? FLAG_DRY : 0u;
@@ -1570,18 +1645,32 @@ __global__ void DG_STAGE_BOUNDS stage_kernel(const StageArgs<Pol> a) {
       for (int i = 0; i < RV; ++i) rn.v[i] = *sv(3 * St::PER_EDGE + i);
       unpack<P>(rn, Wn);
     }
+    const T an_r = (sizeof(T) == 4) ? (T)a.a_n_hi : (T)a.a_n, ain_r = (sizeof(T) == 4) ? (T)a.a_in_hi : (T)a.a_in;
     {
-      Acc z = acc_mul(ain, E.zb), x = acc_mul(ain, E.xb), y = acc_mul(ain, E.yb);
-      if (a.has_n) {
-        z = acc_add(z, acc_mul(an, Wn.zb));
-        x = acc_add(x, acc_mul(an, Wn.xb));
-        y = acc_add(y, acc_mul(an, Wn.yb));
+      Acc z, x, y;
+      if (sizeof(T) == 4 && a.pow2) {  // exact scaling of both words by a power of two
+        z = acc_scale2(E.zb, ain_r);
+        x = acc_scale2(E.xb, ain_r);
+        y = acc_scale2(E.yb, ain_r);
+        if (a.has_n) {
+          z = acc_addf(z, acc_scale2(Wn.zb, an_r));
+          x = acc_addf(x, acc_scale2(Wn.xb, an_r));
+          y = acc_addf(y, acc_scale2(Wn.yb, an_r));
+        }
+      } else {
+        z = acc_mul(ain, E.zb);
+        x = acc_mul(ain, E.xb);
+        y = acc_mul(ain, E.yb);
+        if (a.has_n) {
+          z = acc_add(z, acc_mul(an, Wn.zb));
+          x = acc_add(x, acc_mul(an, Wn.xb));
+          y = acc_add(y, acc_mul(an, Wn.yb));
+        }
       }
-      O.zb = acc_add(z, acc_mul(bdt, zrate));
+      O.zb = acc_addf(z, acc_mul(bdt, zrate));
       O.xb = acc_addr(x, acc_r(bdt) * xrate);
       O.yb = acc_addr(y, acc_r(bdt) * yrate);
     }
-    const T an_r = (sizeof(T) == 4) ? (T)a.a_n_hi : (T)a.a_n, ain_r = (sizeof(T) == 4) ? (T)a.a_in_hi : (T)a.a_in;
     const T bdt_r = acc_r(bdt);
 #pragma unroll
     for (int m = 0; m < NS; ++m) {
@@ -1605,7 +1694,7 @@ __global__ void DG_STAGE_BOUNDS stage_kernel(const StageArgs<Pol> a) {
     store_raw<RV>(a.out, e, ro);
 
     // ---- ledger: rain volume rate of the element
-    rain_acc = acc_add(rain_acc, acc_mulr(G.A, Re));
+    rain_acc = acc_addf(rain_acc, acc_mulr(G.A, Re));
   }
   if (cur >= 0 && !a.tune) flush_ledger<P, Pol>(a, cur, gw, rain_acc, bdry_acc);
 

@@ -170,6 +170,9 @@ void build_tables(int p, RefTab<double>& t) {
     dubiner_eval(p, r, s, t.mphi[j], nullptr, nullptr);
   }
   t.phi0 = 1.0 / std::sqrt(2.0);
+  for (int q = 0; q < t.nq; ++q) t.qwT[q] = t.qw[q];
+  for (int m = 0; m < t.np; ++m)
+    for (int i = 0; i < 3; ++i) t.vabs[m] = std::max(t.vabs[m], std::fabs(t.vphi[i][m]));
   for (int m = 0; m < t.np; ++m)
     for (int q = 0; q < t.nq; ++q) {
       t.qphiT[m][q] = t.qphi[q][m];

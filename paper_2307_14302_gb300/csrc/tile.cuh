@@ -39,6 +39,46 @@ namespace dg {
 constexpr int HALO = 32;    // staged out-of-tile neighbour records per tile
 constexpr int TE_MAX = 96;  // edges touching a 32-element tile (3 per element at most)
 
+// edge descriptor: left side, right side (or boundary code), and the left side's scaled outward
+// normal (written by the lane that owns the edge, from its own geometry)
+template <class T>
+struct EdgeDesc;
+template <>
+struct alignas(16) EdgeDesc<float> {
+  int sL, sR;
+  float lnx, lny;
+};
+template <>
+struct alignas(16) EdgeDesc<double> {
+  int sL, sR, pad0, pad1;
+  double lnx, lny;
+};
+__device__ __forceinline__ void put_desc(EdgeDesc<float>* d, int i, int sL, int sR, float lnx, float lny) {
+  reinterpret_cast<int4*>(d)[i] = make_int4(sL, sR, __float_as_int(lnx), __float_as_int(lny));
+}
+__device__ __forceinline__ void put_desc(EdgeDesc<double>* d, int i, int sL, int sR, double lnx, double lny) {
+  int4* p = reinterpret_cast<int4*>(d) + 2 * i;
+  p[0] = make_int4(sL, sR, 0, 0);
+  reinterpret_cast<double2*>(p)[1] = make_double2(lnx, lny);
+}
+__device__ __forceinline__ void get_desc(const EdgeDesc<float>* d, int i, int& sL, int& sR, float& lnx, float& lny) {
+  const int4 v = reinterpret_cast<const int4*>(d)[i];
+  sL = v.x;
+  sR = v.y;
+  lnx = __int_as_float(v.z);
+  lny = __int_as_float(v.w);
+}
+__device__ __forceinline__ void get_desc(const EdgeDesc<double>* d, int i, int& sL, int& sR, double& lnx,
+                                         double& lny) {
+  const int4* p = reinterpret_cast<const int4*>(d) + 2 * i;
+  const int4 v = p[0];
+  const double2 n = reinterpret_cast<const double2*>(p)[1];
+  sL = v.x;
+  sR = v.y;
+  lnx = n.x;
+  lny = n.y;
+}
+
 template <int P, class Pol>
 struct TileLayout {
   using T = typename Pol::T;
@@ -53,20 +93,25 @@ struct TileLayout {
   static constexpr int NPR = (NV + 1) / 2;
   static constexpr int XV = sizeof(T) == 4 ? 16 : 32;          // first vertices of a tile, 16-byte units
   // one buffer: records [32][RV], geometry [32][GV], neighbour codes [32], first vertices, the
-  // tile's metadata {scenario, elements present}
+  // tile's metadata {scenario, elements present}, all filled by the TMA batch
   static constexpr int O_GEO = TILE * RV;
   static constexpr int O_NBR = O_GEO + TILE * GV;
   static constexpr int O_XY = O_NBR + TILE;
   static constexpr int O_META = O_XY + XV;
-  static constexpr int BUF = O_META + 1;
+  static constexpr int COPIED = O_META + 1;
+  // the edge slots [3][NPR][32] (pairs of T) overlay the geometry, codes, vertices and metadata,
+  // which every lane has read into registers (or into the edge descriptors) before the edge phase
+  static constexpr int O_FLX = O_GEO;
+  static constexpr int FLXV = 3 * NPR * 32 * 2 * (int)sizeof(T) / 16;
+  static constexpr int BUF = (O_FLX + FLXV > COPIED) ? O_FLX + FLXV : COPIED;
   static constexpr int BUF0 = 0;
   static constexpr int BUF1 = BUF;
   static constexpr int HAL = 2 * BUF;                          // [HALO][RV]
-  static constexpr int DESC = HAL + HALO * RV;                 // [96] int2 {left side, right side}
-  static constexpr int FLX = DESC + TE_MAX / 2;                // [3][NPR][32] pairs of T
-  static constexpr int BAR = FLX + 3 * NPR * 32 * 2 * (int)sizeof(T) / 16;  // two 8-byte mbarriers
+  static constexpr int DESC = HAL + HALO * RV;                 // [96] EdgeDesc<T>
+  static constexpr int DV = (int)sizeof(EdgeDesc<T>) / 16;
+  static constexpr int BAR = DESC + TE_MAX * DV;               // two 8-byte mbarriers
   static constexpr int VEC = BAR + 1;                          // 16-byte units per warp
-  static constexpr unsigned TILE_BYTES = 16u * BUF;            // bytes of one buffer's copies
+  static constexpr unsigned TILE_BYTES = 16u * COPIED;         // bytes of one buffer's copies
 };
 template <int P, class Pol>
 __host__ __device__ constexpr int tile_smem_bytes(int block) {
@@ -87,6 +132,12 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                "l"(src), "r"(bytes), "r"(bar)
                : "memory");
+}
+// 16-byte load from a shared-memory address
+__device__ __forceinline__ uint4 lds128(uint32_t addr) {
+  uint4 v;
+  asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr));
+  return v;
 }
 // bulk prefetch of global memory into L2 (16-byte aligned, size a multiple of 16)
 __device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
@@ -215,7 +266,7 @@ __device__ __forceinline__ void area_points_p1(AreaP1<V>& A, const RefTab<T>& ta
   }
   const V sx = vfma(ghbx, d, vfma(vneg(tau), qx, Fxs));
   const V sy = vfma(ghby, d, vfma(vneg(tau), qy, Fys));
-  const V w = vtab<V, T>(tab.qw, q);
+  const V w = vtab<V, T>(tab.qwT, q);
   A.SF[0] = vfma(w, qx, A.SF[0]);
   A.SF[1] = vfma(w, vfma(qx, u, pp), A.SF[1]);
   A.SF[2] = vfma(w, vmul(qy, u), A.SF[2]);
@@ -377,9 +428,14 @@ __device__ __forceinline__ void tile_area(const Elem<P, Pol>& E, const Geo<Pol>&
 template <int RV>
 __device__ __forceinline__ void fetch_side(const uint4* own, const uint4* halo, const uint4* __restrict__ gin, int src,
                                            Raw<RV>& r) {
-  const uint4* p = src < 32 ? own + src * RV : (src < 64 ? halo + (src - 32) * RV : gin + (size_t)(src - 64) * RV);
+  if (src < 64) {  // shared memory, read as such (not through a generic address)
+    const uint32_t p = smem_u32(src < 32 ? own + src * RV : halo + (src - 32) * RV);
 #pragma unroll
-  for (int v = 0; v < RV; ++v) r.v[v] = p[v];
+    for (int v = 0; v < RV; ++v) r.v[v] = lds128(p + 16 * v);
+  } else {
+#pragma unroll
+    for (int v = 0; v < RV; ++v) r.v[v] = __ldg(gin + (size_t)(src - 64) * RV + v);
+  }
 }
 
 // one side's edge slot at flx[(j NPR + i) 32 + lane], pairs of T: Gz[NG], Gx[NG], Gy[NG] (, mass)
@@ -428,17 +484,6 @@ __device__ __forceinline__ T side_mass(const T* vals) {
     return m;
   }
 }
-// scaled outward normal of local edge j from a staged geometry record
-__device__ __forceinline__ void geo_normal(const uint4* g, int j, float& lnx, float& lny) {
-  const float* f = reinterpret_cast<const float*>(g);
-  lnx = f[2 * j];
-  lny = f[2 * j + 1];
-}
-__device__ __forceinline__ void geo_normal(const uint4* g, int j, double& lnx, double& lny) {
-  const double* f = reinterpret_cast<const double*>(g);
-  lnx = f[2 * j];
-  lny = f[2 * j + 1];
-}
 
 // reflective wall seen from a trace, along the unit outward normal n: the numerical flux between
 // the trace and its mirror image in closed form (Roe: q.n (q.n / Hs + c) n; LLF adds |q.n| q.n / Hs
@@ -455,27 +500,19 @@ __device__ __forceinline__ T wall_coef(const Trace<T>& t, T nx, T ny, T g, T H0)
 
 template <int P, int FLUX, class Pol>
 __device__ __forceinline__ void tile_edge(const StageArgs<Pol>& a, const ScenDev& S, const uint4* own,
-                                          const uint4* geoS, const uint4* halo, const int2* desc, void* flx, int i,
+                                          const uint4* halo, const EdgeDesc<typename Pol::T>* desc, void* flx, int i,
                                           const typename Pol::T (*ephi)[P + 1][np_of(P)], double t64,
                                           typename Pol::Acc& bdry_acc) {
   using T = typename Pol::T;
   using L = TileLayout<P, Pol>;
-  constexpr int NG = P + 1, RV = L::RV, GV = L::GV, NPR = L::NPR, NV = L::NV;
+  constexpr int NG = P + 1, RV = L::RV, NPR = L::NPR, NV = L::NV;
   constexpr bool MASSV = L::MASSV;
   const RefTab<T>& tab = ctab<T, P>();
   const T g = a.g, H0 = a.H0;
-  const int2 d = desc[i];
-  const int sL = d.x, sR = d.y;
+  int sL, sR;
+  T lnx, lny;  // L's scaled outward normal
+  get_desc(desc, i, sL, sR, lnx, lny);
   const int jL = sL & 3, srcL = sL >> 2;
-  // L's scaled outward normal, from the staged geometry of a side that lies in the tile
-  T lnx, lny;
-  if (srcL < TILE) {
-    geo_normal(geoS + srcL * GV, jL, lnx, lny);
-  } else {  // L is a halo element, R belongs to the tile: its normal, reversed
-    geo_normal(geoS + (sR >> 2) * GV, sR & 3, lnx, lny);
-    lnx = -lnx;
-    lny = -lny;
-  }
   Raw<RV> rl;
   fetch_side<RV>(own, halo, a.in, srcL, rl);
   Elem<P, Pol> EL;
@@ -553,15 +590,28 @@ __device__ __forceinline__ void tile_edge(const StageArgs<Pol>& a, const ScenDev
   }
   const T hl = T(0.5) * len;
   T vals[NV + 1];
+  constexpr bool PK = DG_PACKED_FLUX && P == 1 && sizeof(T) == 4;  // both points in packed FP32x2
   if (srcL < TILE) {  // L's slot, in L's point order
     if (!closed) {
+      if constexpr (PK) {
+        const f2 hq = p2(0.25f * g), dc = p2(dcRL);  // the mean of the sides' g/2 d (2H - d)
+        const f2 Ld = make_float2(tl[0].d, tl[1].d), LH = make_float2(tl[0].H, tl[1].H);
+        const f2 Rd = add2(make_float2(tr[0].d, tr[1].d), dc), RH = make_float2(tr[0].H, tr[1].H);
+        const f2 pp = mul2(hq, fma2(Ld, fma2(p2(2.f), LH, neg2(Ld)), mul2(Rd, fma2(p2(2.f), RH, neg2(Rd)))));
+        const f2 wk = mul2(make_float2(tab.gw[0], tab.gw[1]), p2(hl));
+        const f2 vz = mul2(wk, make_float2(fz[0], fz[1]));
+        const f2 vx = mul2(wk, fma2(pp, p2(nx), make_float2(fx[0], fx[1])));
+        const f2 vy = mul2(wk, fma2(pp, p2(ny), make_float2(fy[0], fy[1])));
+        vals[0] = vz.x; vals[1] = vz.y; vals[2] = vx.x; vals[3] = vx.y; vals[4] = vy.x; vals[5] = vy.y;
+      } else {
 #pragma unroll
-      for (int k = 0; k < NG; ++k) {
-        const T p = T(0.5) * (pdev(tl[k].d, tl[k].H, g) + pdev(tr[k].d + dcRL, tr[k].H, g));
-        const T wk = tab.gw[k] * hl;
-        vals[k] = wk * fz[k];
-        vals[NG + k] = wk * (fx[k] + p * nx);
-        vals[2 * NG + k] = wk * (fy[k] + p * ny);
+        for (int k = 0; k < NG; ++k) {
+          const T p = T(0.5) * (pdev(tl[k].d, tl[k].H, g) + pdev(tr[k].d + dcRL, tr[k].H, g));
+          const T wk = tab.gw[k] * hl;
+          vals[k] = wk * fz[k];
+          vals[NG + k] = wk * (fx[k] + p * nx);
+          vals[2 * NG + k] = wk * (fy[k] + p * ny);
+        }
       }
       if (MASSV) vals[3 * NG] = ec;
     } else {
@@ -579,14 +629,26 @@ __device__ __forceinline__ void tile_edge(const StageArgs<Pol>& a, const ScenDev
   }
   if (interior && srcR < TILE) {  // R's slot, in R's point order (its point k is L's NG-1-k)
     if (!closed) {
+      if constexpr (PK) {  // R's point kr is L's point 1 - kr
+        const f2 hq = p2(0.25f * g), dc = p2(dcRL);  // the mean of the sides' g/2 d (2H - d)
+        const f2 Rd = make_float2(tr[1].d, tr[0].d), RH = make_float2(tr[1].H, tr[0].H);
+        const f2 Ld = sub2(make_float2(tl[1].d, tl[0].d), dc), LH = make_float2(tl[1].H, tl[0].H);
+        const f2 pp = mul2(hq, fma2(Rd, fma2(p2(2.f), RH, neg2(Rd)), mul2(Ld, fma2(p2(2.f), LH, neg2(Ld)))));
+        const f2 wk = mul2(make_float2(tab.gw[0], tab.gw[1]), p2(-hl));
+        const f2 vz = mul2(wk, make_float2(fz[1], fz[0]));
+        const f2 vx = mul2(wk, fma2(pp, p2(nx), make_float2(fx[1], fx[0])));
+        const f2 vy = mul2(wk, fma2(pp, p2(ny), make_float2(fy[1], fy[0])));
+        vals[0] = vz.x; vals[1] = vz.y; vals[2] = vx.x; vals[3] = vx.y; vals[4] = vy.x; vals[5] = vy.y;
+      } else {
 #pragma unroll
-      for (int kr = 0; kr < NG; ++kr) {
-        const int k = NG - 1 - kr;
-        const T p = T(0.5) * (pdev(tr[k].d, tr[k].H, g) + pdev(tl[k].d - dcRL, tl[k].H, g));
-        const T wk = tab.gw[kr] * hl;
-        vals[kr] = -(wk * fz[k]);
-        vals[NG + kr] = -(wk * (fx[k] + p * nx));
-        vals[2 * NG + kr] = -(wk * (fy[k] + p * ny));
+        for (int kr = 0; kr < NG; ++kr) {
+          const int k = NG - 1 - kr;
+          const T p = T(0.5) * (pdev(tr[k].d, tr[k].H, g) + pdev(tl[k].d - dcRL, tl[k].H, g));
+          const T wk = tab.gw[kr] * hl;
+          vals[kr] = -(wk * fz[k]);
+          vals[NG + kr] = -(wk * (fx[k] + p * nx));
+          vals[2 * NG + kr] = -(wk * (fy[k] + p * ny));
+        }
       }
       if (MASSV) vals[3 * NG] = -ec;
     } else {
@@ -631,9 +693,8 @@ __global__ void DG_TILE_BOUNDS tile_kernel(const StageArgs<Pol> a) {
   __syncthreads();
   const int lane = tid & 31;
   uint4* Wm = tsm + (size_t)(tid >> 5) * L::VEC;
-  uint4* halo = Wm + L::HAL;                        // [HALO][RV]
-  int2* desc = reinterpret_cast<int2*>(Wm + L::DESC);  // [96]
-  void* flx = Wm + L::FLX;                           // [3][NPR][32] pairs
+  uint4* halo = Wm + L::HAL;                                       // [HALO][RV]
+  EdgeDesc<T>* desc = reinterpret_cast<EdgeDesc<T>*>(Wm + L::DESC);  // [96]
   const uint32_t bar0 = smem_u32(Wm + L::BAR), bar1 = bar0 + 8;
   if (lane == 0) {
     mbar_init(bar0, 1);
@@ -677,8 +738,10 @@ __global__ void DG_TILE_BOUNDS tile_kernel(const StageArgs<Pol> a) {
       return;
     }
     ph ^= 1u << b;
-    const uint4* own = Wm + (b ? L::BUF1 : L::BUF0);  // [32][RV] records
+    uint4* const buf = Wm + (b ? L::BUF1 : L::BUF0);
+    const uint4* own = buf;                           // [32][RV] records
     const uint4* geoS = own + L::O_GEO;               // [32][GV]
+    void* flx = buf + L::O_FLX;                       // [3][NPR][32] pairs, over geoS .. meta
     const int4* nbrS = reinterpret_cast<const int4*>(own + L::O_NBR);
     const int4 meta = reinterpret_cast<const int4*>(own + L::O_META)[0];
     const int sc = meta.x, present = meta.y;
@@ -750,6 +813,7 @@ __global__ void DG_TILE_BOUNDS tile_kernel(const StageArgs<Pol> a) {
       const int c = code[j];
       const int me = (lane << 2) | j;
       int sL = me, sR = c;
+      T lnx = G.lnx[j], lny = G.lny[j];
       if (c >= 0) {
         const int n = c >> 2, jn = c & 3;
         if (!out[j]) {
@@ -761,10 +825,12 @@ __global__ void DG_TILE_BOUNDS tile_kernel(const StageArgs<Pol> a) {
           } else {  // the neighbour has the lower index: it is the left side
             sL = other;
             sR = me;
+            lnx = -lnx;
+            lny = -lny;
           }
         }
       }
-      desc[eidx[j]] = make_int2(sL, sR);
+      put_desc(desc, eidx[j], sL, sR, lnx, lny);
     }
 
     // ---- element phase A: area integrals and rain, while the halo copies are in flight
@@ -818,8 +884,9 @@ __global__ void DG_TILE_BOUNDS tile_kernel(const StageArgs<Pol> a) {
     // ---- edge phase: each edge touching the tile once, one per lane and round
     for (int r = 0; r * 32 < nedge; ++r) {
       const int i = r * 32 + lane;
-      if (i < nedge) tile_edge<P, FLUX, Pol>(a, S, own, geoS, halo, desc, flx, i, s_ephi, t64, bdry_acc);
+      if (i < nedge) tile_edge<P, FLUX, Pol>(a, S, own, halo, desc, flx, i, s_ephi, t64, bdry_acc);
     }
+    fence_proxy_async();  // the slots' generic writes before the TMA batch that later refills the buffer
     __syncwarp();
 
     // ---- element phase B: lift, inverse mass, stage combination, positive-depth operator
@@ -831,7 +898,7 @@ __global__ void DG_TILE_BOUNDS tile_kernel(const StageArgs<Pol> a) {
         for (int v = 0; v < RV; ++v) r.v[v] = own[lane * RV + v];
         unpack<P>(r, E);
       }
-      Acc massout = acc_make<Acc>(0.f, 0.f, 0.0);  // edge mass outflow (volume per second)
+      Acc massout;  // edge mass outflow (volume per second), summed exactly over the three sides
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
         T vals[NV + 1];
@@ -846,7 +913,8 @@ __global__ void DG_TILE_BOUNDS tile_kernel(const StageArgs<Pol> a) {
             Ry[m] = fma(-ph_, vals[2 * NG + k], Ry[m]);
           }
         }
-        massout = acc_addr(massout, side_mass<T, NG, L::MASSV>(vals));
+        const T ms = side_mass<T, NG, L::MASSV>(vals);
+        massout = (j == 0) ? acc_make<Acc>(ms, T(0), ms) : acc_addr(massout, ms);
       }
       if (E.flags & FLAG_DRY) {  // the momentum equations are not advanced on dry elements
 #pragma unroll
@@ -876,9 +944,9 @@ __global__ void DG_TILE_BOUNDS tile_kernel(const StageArgs<Pol> a) {
           x = acc_scale2(E.xb, ain_r);
           y = acc_scale2(E.yb, ain_r);
           if (a.has_n) {
-            z = acc_add(z, acc_scale2(Wn.zb, an_r));
-            x = acc_add(x, acc_scale2(Wn.xb, an_r));
-            y = acc_add(y, acc_scale2(Wn.yb, an_r));
+            z = acc_addf(z, acc_scale2(Wn.zb, an_r));
+            x = acc_addf(x, acc_scale2(Wn.xb, an_r));
+            y = acc_addf(y, acc_scale2(Wn.yb, an_r));
           }
         } else {
           z = acc_mul(ain, E.zb);
@@ -890,7 +958,7 @@ __global__ void DG_TILE_BOUNDS tile_kernel(const StageArgs<Pol> a) {
             y = acc_add(y, acc_mul(an, Wn.yb));
           }
         }
-        O.zb = acc_add(z, acc_mul(bdt, zrate));
+        O.zb = acc_addf(z, acc_mul(bdt, zrate));
         O.xb = acc_addr(x, acc_r(bdt) * xrate);
         O.yb = acc_addr(y, acc_r(bdt) * yrate);
       }
@@ -913,7 +981,7 @@ __global__ void DG_TILE_BOUNDS tile_kernel(const StageArgs<Pol> a) {
       Raw<RV> ro;
       pack<P>(O, ro);
       store_raw<RV>(a.out, e, ro);
-      rain_acc = acc_add(rain_acc, acc_mulr(G.A, Re));
+      rain_acc = acc_addf(rain_acc, acc_mulr(G.A, Re));
     }
     __syncwarp();  // this tile's shared data is consumed: its buffers may be refilled
   }
