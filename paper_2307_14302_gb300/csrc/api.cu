@@ -313,6 +313,22 @@ static int upload_all_tables(int p) {
 // one record buffer's share of bound memory: its size rounded up to 256 bytes
 static size_t record_stride(size_t rbytes) { return (rbytes + 255) / 256 * 256; }
 
+// Element records on the device are tile-blocked (the layout the kernels read): the 16-byte
+// vector v of element e is vector ((e / 32) rv + v) 32 + e % 32 of the array.
+static size_t rec_vec(size_t e, size_t v, size_t rv) { return ((e >> 5) * rv + v) * 32 + (e & 31); }
+// 32-bit word w of element e's record in a tile-blocked array (e counted from the array's start,
+// which is tile-aligned)
+static uint32_t rec_word(const std::vector<uint32_t>& blk, size_t e, size_t w, size_t rv) {
+  return blk[4 * rec_vec(e, w / 4, rv) + w % 4];
+}
+// element-major records (rw = 4 rv words each) -> tile-blocked, E a multiple of 32
+static std::vector<uint32_t> to_blocked(const std::vector<uint32_t>& rec, size_t E, size_t rv) {
+  std::vector<uint32_t> blk(rec.size());
+  for (size_t e = 0; e < E; ++e)
+    for (size_t v = 0; v < rv; ++v) std::memcpy(&blk[4 * rec_vec(e, v, rv)], &rec[4 * (rv * e + v)], 16);
+  return blk;
+}
+
 // device-visible address of page-locked host memory (zero-copy), or nullptr when p is pageable
 // memory, device memory or not known to the runtime
 static const void* host_mapped(const void* p) {
@@ -502,7 +518,8 @@ static int build_layout(dgswe_h h) {
       h->rain_node.alloc((mx ? 4 : 8) * (size_t)N) ||
       h->scratch.alloc(sizeof(double) * 4 * 4096))
     return fail(DGSWE_ENOMEM, "device allocation failed");
-  CU(cudaMemcpy(h->rec[0].p, rec.data(), rbytes, cudaMemcpyHostToDevice));
+  const std::vector<uint32_t> blk = to_blocked(rec, (size_t)E, (size_t)h->rv);
+  CU(cudaMemcpy(h->rec[0].p, blk.data(), rbytes, cudaMemcpyHostToDevice));
   CU(cudaMemset(h->rec[1].p, 0, rbytes));
   CU(cudaMemset(h->rec[2].p, 0, rbytes));
   CU(cudaMemcpy(h->geo.p, geo.data(), 4 * geo.size(), cudaMemcpyHostToDevice));
@@ -1345,12 +1362,12 @@ int dgswe_get_dry(dgswe_h h, uint8_t* dry) {
   DeviceGuard dg_(h->device);
   const HostMesh& M = h->sc[0].m;
   const size_t rw = 4 * (size_t)h->rv;
-  std::vector<uint32_t> rec(rw * M.ne);
+  std::vector<uint32_t> rec(rw * ((size_t)(M.ne + TILE - 1) / TILE * TILE));  // whole tiles
   CU(cudaStreamSynchronize(h->stream));
   CU(cudaMemcpy(rec.data(), h->rec[0].p, 4 * rec.size(), cudaMemcpyDeviceToHost));
   const int NS = h->np - 1;
   const size_t off = mixed(h) ? (size_t)(6 + 3 * NS + 1) : (size_t)2 * (3 + 3 * NS + 1);
-  for (int e = 0; e < M.ne; ++e) dry[M.eorig[e]] = (rec[rw * e + off] & FLAG_DRY) ? 1 : 0;
+  for (int e = 0; e < M.ne; ++e) dry[M.eorig[e]] = (rec_word(rec, e, off, h->rv) & FLAG_DRY) ? 1 : 0;
   return 0;
 }
 
@@ -1386,12 +1403,12 @@ static int ledger_of(dgswe_h h, size_t s, dgswe_ledger* out) {
   // wet fraction from the dry flags
   const HostMesh& M = h->sc[s].m;
   const size_t rw = 4 * (size_t)h->rv;
-  std::vector<uint32_t> rec(rw * M.ne);
+  std::vector<uint32_t> rec(rw * ((size_t)(M.ne + TILE - 1) / TILE * TILE));  // whole tiles
   CU(cudaMemcpy(rec.data(), h->rec[0].as<uint32_t>() + rw * h->eoff[s], 4 * rec.size(), cudaMemcpyDeviceToHost));
   const int NS = h->np - 1;
   const size_t off = mixed(h) ? (size_t)(6 + 3 * NS + 1) : (size_t)2 * (3 + 3 * NS + 1);
   long long wet = 0;
-  for (int e = 0; e < M.ne; ++e) wet += (rec[rw * e + off] & FLAG_DRY) ? 0 : 1;
+  for (int e = 0; e < M.ne; ++e) wet += (rec_word(rec, e, off, h->rv) & FLAG_DRY) ? 0 : 1;
   out->wet_frac = (double)wet / M.ne;
   return 0;
 }

@@ -249,17 +249,23 @@ struct Raw {
   uint4 v[NV];
 };
 
+// Element records in device memory are tile-blocked: the 16-byte vector v of element e sits at
+// index ((e / 32) NV + v) 32 + e % 32.  The 32 elements of a tile read vector v as 512 contiguous
+// bytes, a tile's records form one contiguous block of NV x 32 vectors, and that block copied to
+// shared memory keeps the vector-major order, in which a warp's 16-byte reads spread over the banks.
+template <int NV>
+__host__ __device__ __forceinline__ long long rec_at(long long e, int v) {
+  return ((e >> 5) * NV + v) * 32 + (e & 31);
+}
 template <int NV>
 __device__ __forceinline__ void load_raw(const uint4* __restrict__ base, long long e, Raw<NV>& r) {
-  const uint4* p = base + e * NV;
 #pragma unroll
-  for (int i = 0; i < NV; ++i) r.v[i] = __ldg(p + i);
+  for (int i = 0; i < NV; ++i) r.v[i] = __ldg(base + rec_at<NV>(e, i));
 }
 template <int NV>
 __device__ __forceinline__ void store_raw(uint4* __restrict__ base, long long e, const Raw<NV>& r) {
-  uint4* p = base + e * NV;
 #pragma unroll
-  for (int i = 0; i < NV; ++i) p[i] = r.v[i];
+  for (int i = 0; i < NV; ++i) base[rec_at<NV>(e, i)] = r.v[i];
 }
 
 template <int P>
@@ -1282,15 +1288,13 @@ __global__ void DG_STAGE_BOUNDS stage_kernel(const StageArgs<Pol> a) {
 #pragma unroll
         for (int i = 0; i < St::SV; ++i) cp_async16(sv(j * St::PER_EDGE + i), src + i);
       } else if (code >= 0) {
-        const uint4* src = a.in + (long long)(code >> 2) * RV;
 #pragma unroll
-        for (int i = 0; i < RV; ++i) cp_async16(sv(j * St::PER_EDGE + i), src + i);
+        for (int i = 0; i < RV; ++i) cp_async16(sv(j * St::PER_EDGE + i), a.in + rec_at<RV>(code >> 2, i));
       }
     }
     if (a.has_n) {
-      const uint4* src = a.wn + e * RV;
 #pragma unroll
-      for (int i = 0; i < RV; ++i) cp_async16(sv(3 * St::PER_EDGE + i), src + i);
+      for (int i = 0; i < RV; ++i) cp_async16(sv(3 * St::PER_EDGE + i), a.wn + rec_at<RV>(e, i));
     }
     cp_async_commit();
 

@@ -27,9 +27,11 @@
 // out-of-tile neighbour records are gathered with 16-byte cp.async.  Every mbarrier wait is
 // bounded: a wait that runs out sets ERR_TIMEOUT in the device error word and the kernel returns.
 //
-// Shared memory per warp: the two buffers, the halo records [32][RV], the edge descriptors
-// [96] {left side, right side} and the edge slots [3][pairs][32] (about 13.5 KB in the mixed
-// p = 1 path, so 16 warps fit on an SM).  Neighbours beyond 32 halo slots (none on Hilbert-ordered
+// Records are vector-major in shared memory ([RV][32], as in the tile-blocked device array), so
+// the 16-byte reads of a warp, at its own slots or at any mix of neighbour slots, spread over
+// the banks.  Shared memory per warp: the two buffers, the halo records [RV][32], the edge
+// descriptors [96] {left side, right side, left normal} and the edge slots [3][pairs][32], which
+// overlay the consumed static part of the current buffer (about 12 KB in the mixed p = 1 path).  Neighbours beyond 32 halo slots (none on Hilbert-ordered
 // meshes; kept for generality) are read from global memory.
 #pragma once
 #include "stage.cuh"
@@ -37,6 +39,7 @@
 namespace dg {
 
 constexpr int HALO = 32;    // staged out-of-tile neighbour records per tile
+static_assert(HALO == TILE, "own and halo records share one vector stride in shared memory");
 constexpr int TE_MAX = 96;  // edges touching a 32-element tile (3 per element at most)
 
 // edge descriptor: left side, right side (or boundary code), and the left side's scaled outward
@@ -92,8 +95,9 @@ struct TileLayout {
   static constexpr int NV = 3 * NG + (MASSV ? 1 : 0);
   static constexpr int NPR = (NV + 1) / 2;
   static constexpr int XV = sizeof(T) == 4 ? 16 : 32;          // first vertices of a tile, 16-byte units
-  // one buffer: records [32][RV], geometry [32][GV], neighbour codes [32], first vertices, the
-  // tile's metadata {scenario, elements present}, all filled by the TMA batch
+  // one buffer: records [RV][32] (the tile's block of the tile-blocked record array), geometry
+  // [32][GV], neighbour codes [32], first vertices, the tile's metadata {scenario, elements
+  // present}, all filled by the TMA batch
   static constexpr int O_GEO = TILE * RV;
   static constexpr int O_NBR = O_GEO + TILE * GV;
   static constexpr int O_XY = O_NBR + TILE;
@@ -106,7 +110,7 @@ struct TileLayout {
   static constexpr int BUF = (O_FLX + FLXV > COPIED) ? O_FLX + FLXV : COPIED;
   static constexpr int BUF0 = 0;
   static constexpr int BUF1 = BUF;
-  static constexpr int HAL = 2 * BUF;                          // [HALO][RV]
+  static constexpr int HAL = 2 * BUF;                          // [RV][HALO]
   static constexpr int DESC = HAL + HALO * RV;                 // [96] EdgeDesc<T>
   static constexpr int DV = (int)sizeof(EdgeDesc<T>) / 16;
   static constexpr int BAR = DESC + TE_MAX * DV;               // two 8-byte mbarriers
@@ -423,18 +427,19 @@ __device__ __forceinline__ void tile_area(const Elem<P, Pol>& E, const Geo<Pol>&
 }
 
 // ---------------------------------------------------------------------- edge phase ------
-// record of a side: own (src < 32) or staged halo (src < 64) records in shared memory, else the
-// global record of element src - 64 (all contiguous [RV])
+// record of a side: own (src < 32: [RV][32]) or staged halo (src < 64: [RV][HALO]) records in
+// shared memory, vector-major, else the global record of element src - 64
 template <int RV>
 __device__ __forceinline__ void fetch_side(const uint4* own, const uint4* halo, const uint4* __restrict__ gin, int src,
                                            Raw<RV>& r) {
   if (src < 64) {  // shared memory, read as such (not through a generic address)
-    const uint32_t p = smem_u32(src < 32 ? own + src * RV : halo + (src - 32) * RV);
+    const uint32_t p = smem_u32(src < 32 ? own + src : halo + (src - 32));
+    constexpr uint32_t stride = 16u * TILE;  // HALO == TILE: one stride for both
 #pragma unroll
-    for (int v = 0; v < RV; ++v) r.v[v] = lds128(p + 16 * v);
+    for (int v = 0; v < RV; ++v) r.v[v] = lds128(p + stride * v);
   } else {
 #pragma unroll
-    for (int v = 0; v < RV; ++v) r.v[v] = __ldg(gin + (size_t)(src - 64) * RV + v);
+    for (int v = 0; v < RV; ++v) r.v[v] = __ldg(gin + rec_at<RV>(src - 64, v));
   }
 }
 
@@ -739,7 +744,7 @@ __global__ void DG_TILE_BOUNDS tile_kernel(const StageArgs<Pol> a) {
     }
     ph ^= 1u << b;
     uint4* const buf = Wm + (b ? L::BUF1 : L::BUF0);
-    const uint4* own = buf;                           // [32][RV] records
+    const uint4* own = buf;                           // [RV][32] records
     const uint4* geoS = own + L::O_GEO;               // [32][GV]
     void* flx = buf + L::O_FLX;                       // [3][NPR][32] pairs, over geoS .. meta
     const int4* nbrS = reinterpret_cast<const int4*>(own + L::O_NBR);
@@ -799,9 +804,8 @@ __global__ void DG_TILE_BOUNDS tile_kernel(const StageArgs<Pol> a) {
 #pragma unroll
     for (int j = 0; j < 3; ++j)
       if (out[j] && hslot[j] < HALO) {
-        const uint4* src = a.in + (size_t)(code[j] >> 2) * RV;
 #pragma unroll
-        for (int v = 0; v < RV; ++v) cp_async16(halo + hslot[j] * RV + v, src + v);
+        for (int v = 0; v < RV; ++v) cp_async16(halo + v * HALO + hslot[j], a.in + rec_at<RV>(code[j] >> 2, v));
       }
     cp_async_commit();
     Geo<Pol> G;
@@ -843,7 +847,7 @@ __global__ void DG_TILE_BOUNDS tile_kernel(const StageArgs<Pol> a) {
       {
         Raw<RV> r;
 #pragma unroll
-        for (int v = 0; v < RV; ++v) r.v[v] = own[lane * RV + v];
+        for (int v = 0; v < RV; ++v) r.v[v] = own[v * TILE + lane];
         unpack<P>(r, E);
       }
       // vertex coordinates: the first vertex, then along the edge vectors t_j = (-ln_j.y, ln_j.x)
@@ -895,7 +899,7 @@ __global__ void DG_TILE_BOUNDS tile_kernel(const StageArgs<Pol> a) {
       {
         Raw<RV> r;
 #pragma unroll
-        for (int v = 0; v < RV; ++v) r.v[v] = own[lane * RV + v];
+        for (int v = 0; v < RV; ++v) r.v[v] = own[v * TILE + lane];
         unpack<P>(r, E);
       }
       Acc massout;  // edge mass outflow (volume per second), summed exactly over the three sides
@@ -933,7 +937,7 @@ __global__ void DG_TILE_BOUNDS tile_kernel(const StageArgs<Pol> a) {
       if (a.has_n) {
         Raw<RV> rn;
 #pragma unroll
-        for (int v = 0; v < RV; ++v) rn.v[v] = __ldg(a.wn + (size_t)e * RV + v);
+        for (int v = 0; v < RV; ++v) rn.v[v] = __ldg(a.wn + rec_at<RV>(e, v));
         unpack<P>(rn, Wn);
       }
       const T an_r = (sizeof(T) == 4) ? (T)a.a_n_hi : (T)a.a_n, ain_r = (sizeof(T) == 4) ? (T)a.a_in_hi : (T)a.a_in;
