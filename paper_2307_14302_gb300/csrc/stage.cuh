@@ -640,23 +640,31 @@ __device__ bool positivity_fp64(double zbar, double& xbar, double& ybar, double*
     Ho[0] = Ho[1] = Ho[2] = Hbar;
     dry[0] = dry[1] = dry[2] = true;
   } else {
-    int i0 = 0, i1 = 1, i2 = 2, t;
-    // stable sort of the three depths (ties by vertex index)
-    if (H[i1] < H[i0]) { t = i0; i0 = i1; i1 = t; }
-    if (H[i2] < H[i1]) { t = i1; i1 = i2; i2 = t; }
-    if (H[i1] < H[i0] || (H[i1] == H[i0] && i1 < i0)) { t = i0; i0 = i1; i1 = t; }
-    if (H[i2] == H[i1] && i2 < i1) { t = i1; i1 = i2; i2 = t; }
-    double d = H0 - H[i0];
-    Ho[i0] = H0;
-    if (H[i1] - 0.5 * d >= H0) {
-      Ho[i1] = H[i1] - 0.5 * d;
-      Ho[i2] = H[i2] - 0.5 * d;
-    } else {
-      Ho[i1] = H0;
-      Ho[i2] = H[i2] - (H0 - H[i0]) - (H0 - H[i1]);
-    }
+    // rank of each vertex in the stable order of the three depths (ties by vertex index): lowest
+    // 0, middle 1, highest 2; formed by comparisons, so no array is indexed at run time
+    int rk[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) dry[i] = Ho[i] < H0;
+    for (int i = 0; i < 3; ++i) {
+      rk[i] = 0;
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        if (j != i && (H[j] < H[i] || (H[j] == H[i] && j < i))) ++rk[i];
+    }
+    double hl = H[0], hm = H[0];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      if (rk[i] == 0) hl = H[i];
+      if (rk[i] == 1) hm = H[i];
+    }
+    const double d = H0 - hl;
+    const bool share = hm - 0.5 * d >= H0;  // the other two vertices give up d/2 each
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      if (rk[i] == 0) Ho[i] = H0;
+      else if (share) Ho[i] = H[i] - 0.5 * d;
+      else Ho[i] = (rk[i] == 1) ? H0 : H[i] - (H0 - hl) - (H0 - hm);
+      dry[i] = Ho[i] < H0;
+    }
   }
   // rebuild the linear part of zeta from the redistributed vertex values; the mean is kept
   double zv[3] = {Ho[0] - hbv[0], Ho[1] - hbv[1], Ho[2] - hbv[2]};
@@ -677,9 +685,10 @@ __device__ bool positivity_fp64(double zbar, double& xbar, double& ybar, double*
       qy[i] = ybar + ys[0] * tb.vphi[i][1] + ys[1] * tb.vphi[i][2];
       if (dry[i]) { sx += qx[i]; sy += qy[i]; qx[i] = qy[i] = 0.0; }
     }
+    const double share = (nd == 1) ? 0.5 : 1.0;  // 1 / (3 - nd), exact
 #pragma unroll
     for (int i = 0; i < 3; ++i)
-      if (!dry[i]) { qx[i] += sx / (3 - nd); qy[i] += sy / (3 - nd); }
+      if (!dry[i]) { qx[i] += sx * share; qy[i] += sy * share; }
     xs[0] = tb.vinv[0][0] * qx[0] + tb.vinv[0][1] * qx[1] + tb.vinv[0][2] * qx[2];
     xs[1] = tb.vinv[1][0] * qx[0] + tb.vinv[1][1] * qx[1] + tb.vinv[1][2] * qx[2];
     ys[0] = tb.vinv[0][0] * qy[0] + tb.vinv[0][1] * qy[1] + tb.vinv[0][2] * qy[2];
