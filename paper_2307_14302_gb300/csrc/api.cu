@@ -140,6 +140,7 @@ struct dgswe_ctx {
   bool autotune = true;
   bool graphs = true;  // replay steps from CUDA graphs (else direct launches)
   bool grid_rain = false;  // some scenario has gridded rain: a node kernel runs before each stage
+  int feat = FT_ALL;       // features of the run (Feature bits): selects the tile-kernel instantiation
   long long nn_total = 0;
   int grid = 0;
   cudaGraphExec_t g1 = nullptr, gK = nullptr;
@@ -306,6 +307,7 @@ static int upload_all_tables(int p) {
   CU(upload_tables<Mixed>(p, g_tabf[p], g_tabd[p]));
   CU(upload_tables<Fp64>(p, g_tabf[p], g_tabd[p]));
   CU(upload_tile_tables<Mixed>(p, g_tabf[p], g_tabd[p]));
+  CU(upload_tile_spec_tables(p, g_tabf[p], g_tabd[p]));
   CU(upload_tile_tables<Fp64>(p, g_tabf[p], g_tabd[p]));
   return 0;
 }
@@ -344,6 +346,34 @@ static const void* host_mapped(const void* p) {
 template <class T>
 static void put(std::vector<uint32_t>& w, size_t at, T v) {
   std::memcpy(&w[at], &v, sizeof(T));
+}
+
+// a Shu-Osher weight that scales a float-float value exactly: zero or a positive power of two
+static bool pow2_or_0(double c) {
+  int ex = 0;
+  return c == 0.0 || (c > 0.0 && std::frexp(c, &ex) == 0.5);
+}
+
+// the Feature bits of the run: boundary kinds present in the neighbour codes, forcing kinds of
+// every scenario, the friction law and the kinds of Runge-Kutta stage weights
+static int run_features(dgswe_h h, const std::vector<int32_t>& nbr) {
+  int f = 0;
+  for (size_t i = 0; i < nbr.size(); i += 4)
+    for (int j = 0; j < 3; ++j) {
+      const int32_t c = nbr[i + j];
+      if (c <= -2 - MAXSEG) f |= FT_RIVER;
+      else if (c <= -2) f |= FT_OCEAN;
+    }
+  for (const Scenario& S : h->sc) {
+    if (S.rain_kind == 0) f |= FT_RAIN0;
+    if (S.rain_kind == 1) f |= FT_RAIN1;
+    if (S.rain_kind == 2) f |= FT_RAIN2;
+    if (S.rain_kind == 3) f |= FT_RAIN3;
+    if (S.press) f |= FT_PRESS;
+  }
+  f |= h->prm.friction == DGSWE_MANNING ? FT_MANNING : h->prm.friction == DGSWE_QUADRATIC ? FT_QUAD : FT_NOFRIC;
+  for (const Stage& st : h->stages) f |= (pow2_or_0(st.a_n) && pow2_or_0(st.a_in)) ? FT_POW2 : FT_GENSSP;
+  return f;
 }
 
 static int build_layout(dgswe_h h) {
@@ -623,6 +653,7 @@ static int build_layout(dgswe_h h) {
   h->V0.assign(ns, 0.0);
   h->VH0.assign(ns, 0.0);
   h->stages = ssp_table(h->prm.ssp_stages);
+  h->feat = run_features(h, nbr);
   return 0;
 }
 
@@ -702,10 +733,6 @@ static StageArgs<Pol> make_args(dgswe_h h, int stage, int tune) {
   a.stage = stage;
   a.last = (stage == S - 1) ? 1 : 0;
   a.has_n = st.a_n != 0.0 ? 1 : 0;
-  auto pow2_or_0 = [](double c) {
-    int ex = 0;
-    return c == 0.0 || (c > 0.0 && std::frexp(c, &ex) == 0.5);
-  };
   a.pow2 = (pow2_or_0(st.a_n) && pow2_or_0(st.a_in)) ? 1 : 0;
   a.tune = tune;
   a.friction = h->prm.friction;
@@ -745,8 +772,8 @@ static int launch_stage_once(dgswe_h h, int stage, int tune, cudaStream_t s) {
     h->launches++;
   }
   if (h->split == 2)
-    e = mixed(h) ? launch_tile<Mixed>(h->prm.p, h->prm.flux, make_args<Mixed>(h, stage, tune), grid, h->block, s)
-                 : launch_tile<Fp64>(h->prm.p, h->prm.flux, make_args<Fp64>(h, stage, tune), grid, h->block, s);
+    e = mixed(h) ? launch_tile<Mixed>(h->prm.p, h->prm.flux, h->feat, make_args<Mixed>(h, stage, tune), grid, h->block, s)
+                 : launch_tile<Fp64>(h->prm.p, h->prm.flux, h->feat, make_args<Fp64>(h, stage, tune), grid, h->block, s);
   else if (mixed(h))
     e = launch_stage<Mixed>(h->prm.p, h->prm.flux, make_args<Mixed>(h, stage, tune), grid, h->block, s);
   else
@@ -769,8 +796,8 @@ static int launches_per_stage(dgswe_h h) {
 
 static int occupancy(dgswe_h h, int block) {
   if (h->split == 2)
-    return mixed(h) ? tile_blocks_per_sm<Mixed>(h->prm.p, h->prm.flux, block)
-                    : tile_blocks_per_sm<Fp64>(h->prm.p, h->prm.flux, block);
+    return mixed(h) ? tile_blocks_per_sm<Mixed>(h->prm.p, h->prm.flux, h->feat, block)
+                    : tile_blocks_per_sm<Fp64>(h->prm.p, h->prm.flux, h->feat, block);
   return mixed(h) ? stage_blocks_per_sm<Mixed>(h->prm.p, h->prm.flux, block, h->split)
                   : stage_blocks_per_sm<Fp64>(h->prm.p, h->prm.flux, block, h->split);
 }

@@ -74,14 +74,60 @@ template <class Pol>
 cudaError_t launch_stage(int p, int flux, const StageArgs<Pol>& a, int grid, int block, cudaStream_t s);
 template <class Pol>
 int stage_blocks_per_sm(int p, int flux, int block, int split);
-// tile form (split = 2): reference tables and shared-memory limits of its translation unit,
-// the launch, and resident CTAs per SM
+// Features of a run that a tile-kernel instantiation compiles in.  The generic instantiation has
+// all of them; a specialised one leaves out the code, and the run-time tests, of the others and
+// serves any run whose features it covers (ft_covers).
+enum Feature : int {
+  FT_RIVER = 1 << 0,     // river boundary edges
+  FT_OCEAN = 1 << 1,     // tidal (open) boundary edges
+  FT_PRESS = 1 << 2,     // pressure set-up forcing
+  FT_RAIN1 = 1 << 3,     // rain: constant nodal rates
+  FT_RAIN2 = 1 << 4,     // rain: parametric storm
+  FT_RAIN3 = 1 << 5,     // rain: gridded, nodal rates from the node kernel
+  FT_MANNING = 1 << 6,   // Manning friction
+  FT_QUAD = 1 << 7,      // quadratic friction
+  FT_NOFRIC = 1 << 8,    // no friction
+  FT_POW2 = 1 << 9,      // stages whose Shu-Osher weights are powers of two
+  FT_GENSSP = 1 << 10,   // stages with other weights
+  FT_RAIN0 = 1 << 11,    // no rain
+  FT_ALL = (1 << 12) - 1
+};
+// a run has one or more rain kinds (one per scenario), exactly one friction law, and one or both
+// stage-weight kinds; an instantiation with exactly one of a group fixes it at compile time
+constexpr int FT_RAIN = FT_RAIN0 | FT_RAIN1 | FT_RAIN2 | FT_RAIN3;
+constexpr int FT_FRIC = FT_MANNING | FT_QUAD | FT_NOFRIC;
+// what an instantiation fixes at compile time (-1: decided at run time)
+DG_HD constexpr int ft_rain(int ft) {
+  return (ft & FT_RAIN) == FT_RAIN0 ? 0
+         : (ft & FT_RAIN) == FT_RAIN1 ? 1
+         : (ft & FT_RAIN) == FT_RAIN2 ? 2
+         : (ft & FT_RAIN) == FT_RAIN3 ? 3
+                                      : -1;
+}
+DG_HD constexpr int ft_friction(int ft) {
+  return (ft & FT_FRIC) == FT_MANNING ? 0 : (ft & FT_FRIC) == FT_QUAD ? 1 : (ft & FT_FRIC) == FT_NOFRIC ? 2 : -1;
+}
+DG_HD constexpr int ft_pow2(int ft) {
+  return (ft & (FT_POW2 | FT_GENSSP)) == FT_POW2 ? 1 : (ft & (FT_POW2 | FT_GENSSP)) == FT_GENSSP ? 0 : -1;
+}
+DG_HD constexpr bool ft_covers(int ft, int need) { return (need & ~ft) == 0; }
+
+// tile form (split = 2): reference tables and shared-memory limits of its translation units,
+// the launch (the specialised instantiation that covers the run's features, else the generic
+// one), and resident CTAs per SM of the instantiation the launch would use
 template <class Pol>
 cudaError_t upload_tile_tables(int p, const RefTab<float>& tf, const RefTab<double>& td);
 template <class Pol>
-cudaError_t launch_tile(int p, int flux, const StageArgs<Pol>& a, int grid, int block, cudaStream_t s);
+cudaError_t launch_tile(int p, int flux, int feat, const StageArgs<Pol>& a, int grid, int block, cudaStream_t s);
 template <class Pol>
-int tile_blocks_per_sm(int p, int flux, int block);
+int tile_blocks_per_sm(int p, int flux, int feat, int block);
+// specialised mixed-precision tile kernels (tile_spec.cu): launch or occupancy of the one that
+// covers feat; cudaErrorNotSupported (launch) or -1 (occupancy) when none does
+cudaError_t launch_tile_spec(int p, int flux, int feat, const StageArgs<Mixed>& a, int grid, int block,
+                             cudaStream_t s);
+int tile_spec_blocks_per_sm(int p, int flux, int feat, int block);
+// reference tables and shared-memory limits of the specialised instantiations' translation unit
+cudaError_t upload_tile_spec_tables(int p, const RefTab<float>& tf, const RefTab<double>& td);
 // edge kernel of the split path: one thread per interior edge, writes both sides' slots
 template <class Pol>
 cudaError_t launch_edges(int p, int flux, const StageArgs<Pol>& a, int grid, int block, cudaStream_t s);

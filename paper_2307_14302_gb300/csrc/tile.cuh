@@ -295,7 +295,7 @@ __device__ __forceinline__ void setup_force(const ForcingT<T>& F, T px, T py, T 
 }
 
 // area integrals (grad v, F) + (s, v) of one element into Rz, Rx, Ry (weak-form moments)
-template <int P, class Pol>
+template <int P, class Pol, int FT>
 __device__ __forceinline__ void tile_area(const Elem<P, Pol>& E, const Geo<Pol>& G, const ScenDev& S,
                                           const StageArgs<Pol>& a, int press, const typename Pol::T vx[3],
                                           const typename Pol::T vy[3], typename Pol::T (&Rz)[np_of(P)],
@@ -316,8 +316,8 @@ __device__ __forceinline__ void tile_area(const Elem<P, Pol>& E, const Geo<Pol>&
   const T g1x = tab.qdr[0][1] * rx + tab.qds[0][1] * sx, g1y = tab.qdr[0][1] * ry + tab.qds[0][1] * sy;
   const T g2x = tab.qdr[0][2] * rx + tab.qds[0][2] * sx, g2y = tab.qdr[0][2] * ry + tab.qds[0][2] * sy;
   const T hbx = E.hb1 * g1x + E.hb2 * g2x, hby = E.hb1 * g1y + E.hb2 * g2y;  // constant grad(hb)
-  const T cfm = (a.friction == 0) ? g * G.man * G.man : a.cf;
-  const int friction = a.friction;
+  const int friction = ft_friction(FT) >= 0 ? ft_friction(FT) : a.friction;
+  const T cfm = (friction == 0) ? g * G.man * G.man : a.cf;
   if constexpr (P == 1) {
     const T xb = acc_r(E.xb), yb = acc_r(E.yb);
     T Fx[NQ], Fy[NQ];
@@ -503,7 +503,7 @@ __device__ __forceinline__ T wall_coef(const Trace<T>& t, T nx, T ny, T g, T H0)
   return qn * (un + c) + pdev(t.d, t.H, g);
 }
 
-template <int P, int FLUX, class Pol>
+template <int P, int FLUX, class Pol, int FT>
 __device__ __forceinline__ void tile_edge(const StageArgs<Pol>& a, const ScenDev& S, const uint4* own,
                                           const uint4* halo, const EdgeDesc<typename Pol::T>* desc, void* flx, int i,
                                           const typename Pol::T (*ephi)[P + 1][np_of(P)], double t64,
@@ -528,7 +528,12 @@ __device__ __forceinline__ void tile_edge(const StageArgs<Pol>& a, const ScenDev
   Trace<T> tl[NG], tr[NG];
 #pragma unroll
   for (int k = 0; k < NG; ++k) tl[k] = trace_at<P, Pol>(EL, ephi[jL][k]);
-  const bool interior = sR >= 0, land = sR == -1;
+  // boundary kind (an instantiation without a kind treats such an edge as a wall; the host never
+  // selects it for a run that has one)
+  const bool interior = sR >= 0;
+  const bool river_e = (FT & FT_RIVER) && sR <= -2 - MAXSEG;
+  const bool ocean_e = (FT & FT_OCEAN) && sR <= -2 && sR > -2 - MAXSEG;
+  const bool land = !interior && !river_e && !ocean_e;
   const bool dryL = (EL.flags & FLAG_DRY) != 0;
   bool dryR = false, river = false;
   int jR = 0, srcR = 64;
@@ -544,7 +549,7 @@ __device__ __forceinline__ void tile_edge(const StageArgs<Pol>& a, const ScenDev
     dryR = (ER.flags & FLAG_DRY) != 0;
 #pragma unroll
     for (int k = 0; k < NG; ++k) tr[k] = trace_at<P, Pol>(ER, ephi[jR][NG - 1 - k]);  // the same points
-  } else if (sR <= -2 - MAXSEG) {  // river: interior elevation, prescribed normal discharge
+  } else if (river_e) {  // river: interior elevation, prescribed normal discharge
     const int rs = min(-2 - MAXSEG - sR, MAXRIV - 1);
     qr = river_at<T>(S, rs, t64);
     river = true;
@@ -554,7 +559,7 @@ __device__ __forceinline__ void tile_edge(const StageArgs<Pol>& a, const ScenDev
       tr[k].qx = -qr * nx;
       tr[k].qy = -qr * ny;
     }
-  } else if (!land) {  // ocean: tidal elevation, interior discharge
+  } else if (ocean_e) {  // ocean: tidal elevation, interior discharge
     const int seg = min(-2 - sR, MAXSEG - 1);
     const T zbc = tide_at<T>(S, seg, t64);
     const T dgh = acc_r(acc_addr(acc_neg(EL.zb), zbc));  // ghost zeta - mean of L
@@ -680,7 +685,7 @@ __device__ __forceinline__ void tile_edge(const StageArgs<Pol>& a, const ScenDev
 #define DG_TILE_BOUNDS __maxnreg__(DG_TILE_MAXNREG)
 #endif
 
-template <int P, int FLUX, class Pol>
+template <int P, int FLUX, class Pol, int FT = FT_ALL>
 __global__ void DG_TILE_BOUNDS tile_kernel(const StageArgs<Pol> a) {
   using T = typename Pol::T;
   using Acc = typename Pol::Acc;
@@ -759,8 +764,8 @@ __global__ void DG_TILE_BOUNDS tile_kernel(const StageArgs<Pol> a) {
       cur = sc;
       Sp = a.scen + sc;
       t64 = Sp->d.t0 + stepd * Sp->d.dt;  // stage time, formed in FP64
-      rain_kind = Sp->rain_kind;
-      press = Sp->press;
+      rain_kind = ft_rain(FT) >= 0 ? ft_rain(FT) : Sp->rain_kind;
+      press = (FT & FT_PRESS) ? Sp->press : 0;
     }
     const ScenDev& S = *Sp;
     const int e0 = tile * TILE, e = e0 + lane;
@@ -861,7 +866,7 @@ __global__ void DG_TILE_BOUNDS tile_kernel(const StageArgs<Pol> a) {
         vx[2] = vx[0] + G.lny[2];
         vy[2] = vy[0] - G.lnx[2];
       }
-      tile_area<P, Pol>(E, G, S, a, press, vx, vy, Rz, Rx, Ry);
+      tile_area<P, Pol, FT>(E, G, S, a, press, vx, vy, Rz, Rx, Ry);
       // forcing: element rain = mean of the three nodal rates (Eq. rain)
       if (rain_kind == 1) {
         Re = a.rain_e[e];
@@ -888,7 +893,7 @@ __global__ void DG_TILE_BOUNDS tile_kernel(const StageArgs<Pol> a) {
     // ---- edge phase: each edge touching the tile once, one per lane and round
     for (int r = 0; r * 32 < nedge; ++r) {
       const int i = r * 32 + lane;
-      if (i < nedge) tile_edge<P, FLUX, Pol>(a, S, own, halo, desc, flx, i, s_ephi, t64, bdry_acc);
+      if (i < nedge) tile_edge<P, FLUX, Pol, FT>(a, S, own, halo, desc, flx, i, s_ephi, t64, bdry_acc);
     }
     fence_proxy_async();  // the slots' generic writes before the TMA batch that later refills the buffer
     __syncwarp();
@@ -943,7 +948,8 @@ __global__ void DG_TILE_BOUNDS tile_kernel(const StageArgs<Pol> a) {
       const T an_r = (sizeof(T) == 4) ? (T)a.a_n_hi : (T)a.a_n, ain_r = (sizeof(T) == 4) ? (T)a.a_in_hi : (T)a.a_in;
       {
         Acc z, x, y;
-        if (sizeof(T) == 4 && a.pow2) {  // exact scaling of both words by a power of two
+        constexpr int PW = ft_pow2(FT);
+        if (sizeof(T) == 4 && (PW == 1 || (PW == -1 && a.pow2))) {  // exact scaling of both words by a power of two
           z = acc_scale2(E.zb, ain_r);
           x = acc_scale2(E.xb, ain_r);
           y = acc_scale2(E.yb, ain_r);

@@ -14,6 +14,22 @@ static cudaError_t tile_smem_limit(K kernel, int optin, int need) {
   const int room = optin - (int)fa.sharedSizeBytes;
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, need < room ? need : room);
 }
+// the specialised instantiations exist for the mixed path only
+template <class Pol>
+inline cudaError_t tile_try_spec(int, int, int, const StageArgs<Pol>&, int, int, cudaStream_t) {
+  return cudaErrorNotSupported;
+}
+template <>
+inline cudaError_t tile_try_spec<Mixed>(int p, int flux, int feat, const StageArgs<Mixed>& a, int grid, int block,
+                                        cudaStream_t s) {
+  return launch_tile_spec(p, flux, feat, a, grid, block, s);
+}
+template <class Pol>
+inline int tile_try_spec_occ(int, int, int, int) { return -1; }
+template <>
+inline int tile_try_spec_occ<Mixed>(int p, int flux, int feat, int block) {
+  return tile_spec_blocks_per_sm(p, flux, feat, block);
+}
 }  // namespace dg
 
 #define DG_DEFINE_TILE_LAUNCHERS(POL)                                                                        \
@@ -36,7 +52,10 @@ static cudaError_t tile_smem_limit(K kernel, int optin, int need) {
     return tile_smem_limit(tile_kernel<2, 1, POL>, optin, tile_smem_bytes<2, POL>(256));                     \
   }                                                                                                          \
   template <>                                                                                                \
-  cudaError_t launch_tile<POL>(int p, int flux, const StageArgs<POL>& a, int grid, int block, cudaStream_t s) { \
+  cudaError_t launch_tile<POL>(int p, int flux, int feat, const StageArgs<POL>& a, int grid, int block,      \
+                               cudaStream_t s) {                                                            \
+    const cudaError_t es = tile_try_spec<POL>(p, flux, feat, a, grid, block, s);                             \
+    if (es != cudaErrorNotSupported) return es;                                                              \
     const int k = (p == 1 ? 0 : 2) + (flux ? 1 : 0);                                                         \
     switch (k) {                                                                                             \
       case 0: tile_kernel<1, 0, POL><<<grid, block, tile_smem_bytes<1, POL>(block), s>>>(a); break;          \
@@ -47,7 +66,9 @@ static cudaError_t tile_smem_limit(K kernel, int optin, int need) {
     return cudaGetLastError();                                                                               \
   }                                                                                                          \
   template <>                                                                                                \
-  int tile_blocks_per_sm<POL>(int p, int flux, int block) {                                                  \
+  int tile_blocks_per_sm<POL>(int p, int flux, int feat, int block) {                                        \
+    const int ns = tile_try_spec_occ<POL>(p, flux, feat, block);                                             \
+    if (ns >= 0) return ns;                                                                                  \
     int n = 0;                                                                                               \
     cudaError_t e = cudaSuccess;                                                                             \
     const int k = (p == 1 ? 0 : 2) + (flux ? 1 : 0);                                                         \
