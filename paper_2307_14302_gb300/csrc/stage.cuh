@@ -702,10 +702,12 @@ __device__ bool positivity_fp64(double zbar, double& xbar, double& ybar, double*
 // above H0 at every vertex is case 1 (unchanged, wet; at p = 2 its quadratic modes are scaled
 // by the continuous blend factor when the shallowest vertex is below 2 H0), one whose mean
 // depth is clearly below H0 with a vertex clearly below H0 is case 2 (flat depth, dry, no
-// momentum: the zeta slopes become minus the bathymetry slopes), and one with a vertex clearly
-// below H0 but a mean depth clearly above it is case 3 (depth moved to the lowest vertex, wet).
-// Every depth test is thereby decided as in FP64: FP32 decides only outside a band wider than
-// the FP32 evaluation error; elements inside it (and near ties of case 3) take the FP64 operator.
+// momentum: the zeta slopes become minus the bathymetry slopes), and one with a vertex below H0
+// but a mean depth clearly above it is case 3 (depth moved to the lowest vertex, wet).  The wet /
+// dry decision is thereby the FP64 one: FP32 decides only outside a band wider than the FP32
+// evaluation error, and elements inside it (and near ties of case 3) take the FP64 operator; for
+// a wet mean, a vertex within that band of H0 only decides a redistribution below the FP32
+// resolution of the vertex depths, which FP32 makes.
 template <int P, class Pol>
 __device__ __forceinline__ void apply_positivity(Elem<P, Pol>& E, const Geo<Pol>& G, long long e,
                                                  const StageArgs<Pol>& a, int* err) {
@@ -731,7 +733,11 @@ __device__ __forceinline__ void apply_positivity(Elem<P, Pol>& E, const Geo<Pol>
     if (NL > 1) bound = fma(abs_r(E.hb2) + abs_r(E.zs[NL > 1 ? 1 : 0]), tab.vabs[2], bound);
     const T hmin = fminf(hv[0], fminf(hv[1], hv[2]));
     const T tol = T(4.0e-6) * (abs_r(Hb) + bound);
-    if (hmin - tol > H0) {
+    // mean depth clearly above H0: the element is wet whatever its vertices; a vertex depth within
+    // tol of H0 then decides only whether a redistribution smaller than tol (below the FP32
+    // resolution of the vertex depths) is made, and FP32 decides it
+    const bool wet_mean = Hb > H0 * T(1.00001);
+    if (hmin - tol > H0 || (wet_mean && hmin >= H0)) {
       need64 = false;  // case 1
       if (P >= 2 && hmin < T(2) * H0) {  // quadratic modes blended out, continuous in hmin
         const T th = (hmin - H0) * frcp(H0);
@@ -753,7 +759,7 @@ __device__ __forceinline__ void apply_positivity(Elem<P, Pol>& E, const Geo<Pol>
       for (int m = 0; m < NS; ++m) E.xs[m] = E.ys[m] = T(0);
       E.xb = acc_make<typename Pol::Acc>(0.f, 0.f, 0.0);
       E.yb = acc_make<typename Pol::Acc>(0.f, 0.f, 0.0);
-    } else if (hmin + tol < H0 && Hb > H0 * T(1.00001)) {
+    } else if (wet_mean) {
       // case 3, partially wet: the lowest vertex is raised to H0 and the deficit taken from the
       // others (M Pi^d); no vertex ends dry, so the momentum is unchanged (M Pi^f) and the element
       // is wet.  Formed as vertex changes dH_i (summing to zero: the mean is kept) and added to the
