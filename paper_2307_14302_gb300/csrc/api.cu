@@ -610,6 +610,10 @@ static int build_layout(dgswe_h h) {
     const double gr[6] = {S.gx0, S.gy0, 1.0 / S.gdx, 1.0 / S.gdy, S.gt0, 1.0 / S.gdt};
     const double ps[4] = {S.ps.x0, S.ps.y0, S.ps.sigma, S.ps.peak};
     for (int k = 0; k < 8; ++k) { D.d.storm[k] = st[k]; D.f.storm[k] = (float)st[k]; }
+    D.d.storm[8] = st[5] != 0.0 ? 1.0 / st[5] : 0.0;
+    D.d.storm[9] = st[6] != 0.0 ? 1.4426950408889634 / st[6] : 0.0;
+    D.f.storm[8] = (float)D.d.storm[8];
+    D.f.storm[9] = (float)D.d.storm[9];
     for (int k = 0; k < 6; ++k) { D.d.grid[k] = gr[k]; D.f.grid[k] = (float)gr[k]; }
     for (int k = 0; k < 4; ++k) { D.d.ps[k] = ps[k]; D.f.ps[k] = (float)ps[k]; }
     for (size_t k = 0; k < S.tamp.size() && k < (size_t)MAXSEG; ++k) {

@@ -77,7 +77,8 @@ struct RefTab {
 template <typename T>
 struct ForcingT {
   T t0, dt;                        // stage time = t0 + (step + c) dt
-  T storm[8];                      // x0, y0, speed cos(heading), speed sin(heading), rpeak, rm, re, t0
+  T storm[10];                     // x0, y0, speed cos(heading), speed sin(heading), rpeak, rm, re, t0,
+                                   // then 1 / rm and log2(e) / re
   T tide[MAXSEG][3];               // amplitude, 2 pi / period, phase
   T grid[6];                       // x0, y0, 1/dx, 1/dy, t0, 1/dt_rec
   T ps[4];                         // pressure set-up x0, y0, sigma, peak

@@ -90,6 +90,9 @@ __device__ __forceinline__ ff acc_addf(ff a, ff b) {
   ff s = two_sum(a.hi, b.hi);
   return quick_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
 }
+// a - b rounded to the working precision (float: within an ulp, from the words' differences)
+__device__ __forceinline__ double acc_sub_r(double a, double b) { return a - b; }
+__device__ __forceinline__ float acc_sub_r(ff a, ff b) { return __fadd_rn(__fsub_rn(a.hi, b.hi), __fsub_rn(a.lo, b.lo)); }
 // a + b rounded to the working precision (float: within an ulp, without the float-float sum)
 __device__ __forceinline__ double acc_sum_r(double a, double b) { return a + b; }
 __device__ __forceinline__ float acc_sum_r(ff a, ff b) { return __fadd_rn(__fadd_rn(a.hi, b.hi), __fadd_rn(a.lo, b.lo)); }
@@ -447,6 +450,19 @@ __device__ __forceinline__ Trace<typename Pol::T> trace_at(const Elem<P, Pol>& E
   t.H = E.Hb + (d + hdev);
   t.qx = qx;
   t.qy = qy;
+  return t;
+}
+
+// trace of a degree-1 element at a point with basis values phi_1, phi_2 (as trace_at)
+template <class Pol>
+__device__ __forceinline__ Trace<typename Pol::T> trace_p1(const Elem<1, Pol>& E, typename Pol::T p1,
+                                                            typename Pol::T p2) {
+  using T = typename Pol::T;
+  Trace<T> t;
+  t.d = fma(E.zs[1], p2, E.zs[0] * p1);
+  t.qx = fma(E.xs[1], p2, fma(E.xs[0], p1, acc_r(E.xb)));
+  t.qy = fma(E.ys[1], p2, fma(E.ys[0], p1, acc_r(E.yb)));
+  t.H = E.Hb + (t.d + fma(E.hb1, p1, E.hb2 * p2));
   return t;
 }
 

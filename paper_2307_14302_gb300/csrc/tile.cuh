@@ -220,6 +220,21 @@ __device__ __forceinline__ f2 vsqrt0(f2 a) { return make_float2(fsqrt0(a.x), fsq
 __device__ __forceinline__ float vpowm43(float a) { return fpowm43(a); }
 __device__ __forceinline__ double vpowm43(double a) { return fpowm43(a); }
 __device__ __forceinline__ f2 vpowm43(f2 a) { return make_float2(fpowm43(a.x), fpowm43(a.y)); }
+// friction coefficient tau (source -tau q): Manning g n^2 |u| / Hs^(4/3) (friction 0) or
+// cf |u| / Hs (friction 1).  In FP32 as cfm 2^(lg2|q|^2 / 2 - c lg2 Hs) with c = 7/3 or 2, three
+// special-function operations and no square root (|q| = 0 gives 2^-inf = 0).
+__device__ __forceinline__ float vtau(float qx, float qy, float, float, float Hs, float, float cfm, int friction) {
+  const float c = friction == 0 ? 2.3333333f : 2.0f;
+  return cfm * mufu_ex2(fmaf(0.5f, mufu_lg2(fmaf(qx, qx, qy * qy)), -c * mufu_lg2(Hs)));
+}
+__device__ __forceinline__ f2 vtau(f2 qx, f2 qy, f2 u, f2 v, f2 Hs, f2 iH, f2 cfm, int friction) {
+  return make_float2(vtau(qx.x, qy.x, u.x, v.x, Hs.x, iH.x, cfm.x, friction),
+                     vtau(qx.y, qy.y, u.y, v.y, Hs.y, iH.y, cfm.y, friction));
+}
+__device__ __forceinline__ double vtau(double, double, double u, double v, double Hs, double iH, double cfm,
+                                       int friction) {
+  return cfm * (fsqrt0(fma(u, u, v * v)) * (friction == 0 ? fpowm43(Hs) : iH));
+}
 template <class V>
 __device__ __forceinline__ V vbc(float x);
 template <>
@@ -264,10 +279,7 @@ __device__ __forceinline__ void area_points_p1(AreaP1<V>& A, const RefTab<T>& ta
   const V u = vmul(qx, iH), v = vmul(qy, iH);
   const V pp = vmul(vmul(hg, d), vfma(vbc<V>(2.f), H, vneg(d)));  // g/2 d (2H - d)
   V tau = vbc<V>(0.f);
-  if (friction <= 1) {
-    const V sp = vsqrt0(vfma(u, u, vmul(v, v)));
-    tau = vmul(cfm, vmul(sp, friction == 0 ? vpowm43(Hs) : iH));
-  }
+  if (friction <= 1) tau = vtau(qx, qy, u, v, Hs, iH, cfm, friction);
   const V sx = vfma(ghbx, d, vfma(vneg(tau), qx, Fxs));
   const V sy = vfma(ghby, d, vfma(vneg(tau), qy, Fys));
   const V w = vtab<V, T>(tab.qwT, q);
@@ -400,8 +412,7 @@ __device__ __forceinline__ void tile_area(const Elem<P, Pol>& E, const Geo<Pol>&
       const T u = tq.qx * iH, v = tq.qy * iH;
       const T pp = pdev(tq.d, tq.H, g);
       T tau = 0;
-      if (friction == 0) tau = cfm * fsqrt0(u * u + v * v) * fpowm43(Hs);
-      else if (friction == 1) tau = cfm * fsqrt0(u * u + v * v) * iH;
+      if (friction <= 1) tau = vtau(tq.qx, tq.qy, u, v, Hs, iH, cfm, friction);
       T Fxs = 0, Fys = 0;
       if (press) {
         const T px = tab.ql[q][0] * vx[0] + tab.ql[q][1] * vx[1] + tab.ql[q][2] * vx[2];
@@ -506,7 +517,8 @@ __device__ __forceinline__ T wall_coef(const Trace<T>& t, T nx, T ny, T g, T H0)
 template <int P, int FLUX, class Pol, int FT>
 __device__ __forceinline__ void tile_edge(const StageArgs<Pol>& a, const ScenDev& S, const uint4* own,
                                           const uint4* halo, const EdgeDesc<typename Pol::T>* desc, void* flx, int i,
-                                          const typename Pol::T (*ephi)[P + 1][np_of(P)], double t64,
+                                          const typename Pol::T (*ephi)[P + 1][np_of(P)], const float4* ephi4,
+                                          double t64,
                                           typename Pol::Acc& bdry_acc) {
   using T = typename Pol::T;
   using L = TileLayout<P, Pol>;
@@ -522,12 +534,26 @@ __device__ __forceinline__ void tile_edge(const StageArgs<Pol>& a, const ScenDev
   fetch_side<RV>(own, halo, a.in, srcL, rl);
   Elem<P, Pol> EL;
   unpack<P>(rl, EL);
-  const T len = fsqrt_pos(lnx * lnx + lny * lny);
-  const T il = frcp(len);
+  T len, il;  // edge length and its inverse
+  if constexpr (sizeof(T) == 4) {
+    const T l2 = lnx * lnx + lny * lny;
+    il = mufu_rsqrt(l2);
+    len = l2 * il;
+  } else {
+    len = fsqrt_pos(lnx * lnx + lny * lny);
+    il = frcp(len);
+  }
   const T nx = lnx * il, ny = lny * il;
+  constexpr bool P1F = P == 1 && sizeof(T) == 4;  // basis values of both points in one 16-byte read
   Trace<T> tl[NG], tr[NG];
+  if constexpr (P1F) {
+    const float4 b = ephi4[jL];
+    tl[0] = trace_p1(EL, b.x, b.y);
+    tl[NG - 1] = trace_p1(EL, b.z, b.w);
+  } else {
 #pragma unroll
-  for (int k = 0; k < NG; ++k) tl[k] = trace_at<P, Pol>(EL, ephi[jL][k]);
+    for (int k = 0; k < NG; ++k) tl[k] = trace_at<P, Pol>(EL, ephi[jL][k]);
+  }
   // boundary kind (an instantiation without a kind treats such an edge as a wall; the host never
   // selects it for a run that has one)
   const bool interior = sR >= 0;
@@ -545,10 +571,16 @@ __device__ __forceinline__ void tile_edge(const StageArgs<Pol>& a, const ScenDev
     fetch_side<RV>(own, halo, a.in, srcR, rr);
     Elem<P, Pol> ER;
     unpack<P>(rr, ER);
-    dcRL = acc_diff(ER.zb, EL.zb);
+    dcRL = acc_sub_r(ER.zb, EL.zb);
     dryR = (ER.flags & FLAG_DRY) != 0;
+    if constexpr (P1F) {  // R's point 1 - k is L's point k
+      const float4 b = ephi4[jR];
+      tr[0] = trace_p1(ER, b.z, b.w);
+      tr[NG - 1] = trace_p1(ER, b.x, b.y);
+    } else {
 #pragma unroll
-    for (int k = 0; k < NG; ++k) tr[k] = trace_at<P, Pol>(ER, ephi[jR][NG - 1 - k]);  // the same points
+      for (int k = 0; k < NG; ++k) tr[k] = trace_at<P, Pol>(ER, ephi[jR][NG - 1 - k]);  // the same points
+    }
   } else if (river_e) {  // river: interior elevation, prescribed normal discharge
     const int rs = min(-2 - MAXSEG - sR, MAXRIV - 1);
     qr = river_at<T>(S, rs, t64);
@@ -693,13 +725,19 @@ __global__ void DG_TILE_BOUNDS tile_kernel(const StageArgs<Pol> a) {
   constexpr int NP = np_of(P), NS = NP - 1, NG = P + 1, RV = L::RV, GV = L::GV, NPR = L::NPR, NV = L::NV;
   const RefTab<T>& tab = ctab<T, P>();
 
-  __shared__ T s_ephi[3][NG][NP];  // edge basis values, read at edge-dependent indices
+  // edge basis values, read at edge-dependent indices; at p = 1 in FP32 also one 16-byte row per
+  // edge {phi_1, phi_2 at point 0, phi_1, phi_2 at point 1} (phi_0 is constant and not read)
+  __shared__ T s_ephi[3][NG][NP];
+  __shared__ float4 s_ephi4[3];
   extern __shared__ uint4 tsm[];
   const int tid = threadIdx.x;
   for (int i = tid; i < 3 * NG * NP; i += blockDim.x) {
     const int j = i / (NG * NP), k = (i / NP) % NG, m = i % NP;
     s_ephi[j][k][m] = tab.ephi[j][k][m];
   }
+  if (P == 1 && tid < 3)
+    s_ephi4[tid] = make_float4((float)tab.ephi[tid][0][1], (float)tab.ephi[tid][0][2],
+                               (float)tab.ephi[tid][NG - 1][1], (float)tab.ephi[tid][NG - 1][2]);
   __syncthreads();
   const int lane = tid & 31;
   uint4* Wm = tsm + (size_t)(tid >> 5) * L::VEC;
@@ -880,7 +918,10 @@ __global__ void DG_TILE_BOUNDS tile_kernel(const StageArgs<Pol> a) {
         for (int i = 0; i < 3; ++i) {
           const T dx = vx[i] - cx, dy = vy[i] - cy;
           const T r = fsqrt0(dx * dx + dy * dy);
-          acc += (r < rm) ? rp * (T(0.5) + T(0.5) * fdiv(r, rm)) : rp * fexp(-fdiv(r - rm, re));
+          if constexpr (sizeof(T) == 4)  // with 1 / rm and log2(e) / re formed once on the host
+            acc += (r < rm) ? rp * fmaf(0.5f * F.storm[8], r, 0.5f) : rp * mufu_ex2((rm - r) * F.storm[9]);
+          else
+            acc += (r < rm) ? rp * (T(0.5) + T(0.5) * fdiv(r, rm)) : rp * fexp(-fdiv(r - rm, re));
         }
         Re = acc * T(1.0 / 3.0);
       } else if (rain_kind == 3) {  // gridded: nodal rates interpolated by the node kernel of this stage
@@ -893,7 +934,7 @@ __global__ void DG_TILE_BOUNDS tile_kernel(const StageArgs<Pol> a) {
     // ---- edge phase: each edge touching the tile once, one per lane and round
     for (int r = 0; r * 32 < nedge; ++r) {
       const int i = r * 32 + lane;
-      if (i < nedge) tile_edge<P, FLUX, Pol, FT>(a, S, own, halo, desc, flx, i, s_ephi, t64, bdry_acc);
+      if (i < nedge) tile_edge<P, FLUX, Pol, FT>(a, S, own, halo, desc, flx, i, s_ephi, s_ephi4, t64, bdry_acc);
     }
     fence_proxy_async();  // the slots' generic writes before the TMA batch that later refills the buffer
     __syncwarp();
