@@ -166,7 +166,8 @@ def step_bytes_per_element(precision: str, p: int) -> float:
     return (400.0 if precision == "mixed" else 680.0) * (2.0 if p == 2 else 1.0)
 
 
-FORM_KERNEL = {0: "stage_kernel (fused)", 1: "edge_kernel + stage_kernel (split)", 2: "tile_kernel"}
+FORM_KERNEL = {0: "stage_kernel (fused)", 1: "edge_kernel + stage_kernel (split)",
+               2: "tile_kernel (instantiation specialised to the run's features where one covers them)"}
 FORM_PROFILE = {0: "stage_kernel", 1: "stage_kernel", 2: "tile_kernel"}
 
 
@@ -676,7 +677,7 @@ def kernel_hash():
     import hashlib
 
     h = hashlib.sha256()
-    for f in ("stage.cuh", "tile.cuh", "args.h", "layout.h"):
+    for f in ("stage.cuh", "tile.cuh", "tile_spec.cu", "args.h", "layout.h"):
         h.update(open(os.path.join(ROOT, "paper_2307_14302_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
