@@ -565,9 +565,14 @@ struct Trace2 {
 // square root per side: with r = 1/sqrt(Hs), 1/Hs = r^2, sqrt(Hs) = Hs r, the Roe velocity is
 // (q_L r_L + q_R r_R) / (sqrt(Hs_L) + sqrt(Hs_R)), u.n = (q.n)/Hs, and the jump of q.n is the
 // difference of the sides' q.n (the same quantities as edge_flux, fewer operations)
+// per-side quantities of edge_flux_pair that the wall flux of a closed edge reuses: q.n, 1/Hs and
+// sqrt(Hs) of both sides
+struct FluxAux2 {
+  f2 mL, mR, iL, iR, sL, sR;
+};
 template <int FLUX>
 __device__ __forceinline__ void edge_flux_pair(const Trace2& L, const Trace2& R, f2 dcRL, f2 nx, f2 ny, float g,
-                                               float H0, f2& fz, f2& fx, f2& fy) {
+                                               float H0, f2& fz, f2& fx, f2& fy, FluxAux2& ax) {
   const f2 half = p2(0.5f), mhalf = p2(-0.5f);
   const f2 HsL = max2(L.H, p2(H0)), HsR = max2(R.H, p2(H0));
   const f2 rL = rsqrt2(HsL), rR = rsqrt2(HsR);
@@ -580,6 +585,7 @@ __device__ __forceinline__ void edge_flux_pair(const Trace2& L, const Trace2& R,
   const f2 cy = mul2(half, fma2(L.qy, unL, mul2(R.qy, unR)));
   const f2 cz = mul2(half, add2(mL, mR));
   const f2 sL = mul2(HsL, rL), sR = mul2(HsR, rR);
+  ax = {mL, mR, iL, iR, sL, sR};
   if (FLUX == 1) {  // local Lax-Friedrichs: sqrt(g Hs) = sqrt(g) sqrt(Hs)
     const f2 sg = p2(fsqrt_pos(g));
     const f2 lam = max2(fma2(sg, sL, abs2(unL)), fma2(sg, sR, abs2(unR)));
@@ -1598,7 +1604,8 @@ __global__ void DG_STAGE_BOUNDS stage_kernel(const StageArgs<Pol> a) {
           const Trace2 R2{make_float2(b0.d, b1.d), make_float2(b0.H, b1.H), make_float2(b0.qx, b1.qx),
                           make_float2(b0.qy, b1.qy)};
           f2 fz2, fx2, fy2;
-          edge_flux_pair<FLUX>(L2, R2, p2(dcRL), p2(sgn * nx), p2(sgn * ny), g, H0, fz2, fx2, fy2);
+          FluxAux2 ax;
+          edge_flux_pair<FLUX>(L2, R2, p2(dcRL), p2(sgn * nx), p2(sgn * ny), g, H0, fz2, fx2, fy2, ax);
           fzc[0] = fz2.x; fzc[1] = fz2.y;
           fxc[0] = fx2.x; fxc[1] = fx2.y;
           fyc[0] = fy2.x; fyc[1] = fy2.y;

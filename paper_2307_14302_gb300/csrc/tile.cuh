@@ -602,21 +602,30 @@ __device__ __forceinline__ void tile_edge(const StageArgs<Pol>& a, const ScenDev
       tr[k].d = dgh;
     }
   }
+  constexpr bool PK = DG_PACKED_FLUX && P == 1 && sizeof(T) == 4;  // both points in packed FP32x2
   T fz[NG], fx[NG], fy[NG];
   T ec = T(0);  // mass flux integral along n (L's outward normal)
   bool closed = land;
+  FluxAux2 ax;  // packed path: per-side quantities for the wall flux
+  if constexpr (PK) {
+    // every edge takes the flux evaluation (a land edge against its own trace: the wall below needs
+    // only the left side's quantities), so that no lane takes a separate wall path
+    if (land) {
+#pragma unroll
+      for (int k = 0; k < NG; ++k) tr[k] = tl[k];
+    }
+    const Trace2 L2{make_float2(tl[0].d, tl[1].d), make_float2(tl[0].H, tl[1].H), make_float2(tl[0].qx, tl[1].qx),
+                    make_float2(tl[0].qy, tl[1].qy)};
+    const Trace2 R2{make_float2(tr[0].d, tr[1].d), make_float2(tr[0].H, tr[1].H), make_float2(tr[0].qx, tr[1].qx),
+                    make_float2(tr[0].qy, tr[1].qy)};
+    f2 fz2, fx2, fy2;
+    edge_flux_pair<FLUX>(L2, R2, p2(dcRL), p2(nx), p2(ny), g, H0, fz2, fx2, fy2, ax);
+    fz[0] = fz2.x; fz[1] = fz2.y;
+    fx[0] = fx2.x; fx[1] = fx2.y;
+    fy[0] = fy2.x; fy[1] = fy2.y;
+  }
   if (!land) {
-    if constexpr (DG_PACKED_FLUX && P == 1 && sizeof(T) == 4) {
-      const Trace2 L2{make_float2(tl[0].d, tl[1].d), make_float2(tl[0].H, tl[1].H), make_float2(tl[0].qx, tl[1].qx),
-                      make_float2(tl[0].qy, tl[1].qy)};
-      const Trace2 R2{make_float2(tr[0].d, tr[1].d), make_float2(tr[0].H, tr[1].H), make_float2(tr[0].qx, tr[1].qx),
-                      make_float2(tr[0].qy, tr[1].qy)};
-      f2 fz2, fx2, fy2;
-      edge_flux_pair<FLUX>(L2, R2, p2(dcRL), p2(nx), p2(ny), g, H0, fz2, fx2, fy2);
-      fz[0] = fz2.x; fz[1] = fz2.y;
-      fx[0] = fx2.x; fx[1] = fx2.y;
-      fy[0] = fy2.x; fy[1] = fy2.y;
-    } else {
+    if constexpr (!PK) {
 #pragma unroll
       for (int k = 0; k < NG; ++k) edge_flux<FLUX, T>(tl[k], tr[k], dcRL, nx, ny, g, H0, fz[k], fx[k], fy[k]);
     }
@@ -632,7 +641,6 @@ __device__ __forceinline__ void tile_edge(const StageArgs<Pol>& a, const ScenDev
   }
   const T hl = T(0.5) * len;
   T vals[NV + 1];
-  constexpr bool PK = DG_PACKED_FLUX && P == 1 && sizeof(T) == 4;  // both points in packed FP32x2
   if (srcL < TILE) {  // L's slot, in L's point order
     if (!closed) {
       if constexpr (PK) {
@@ -656,6 +664,14 @@ __device__ __forceinline__ void tile_edge(const StageArgs<Pol>& a, const ScenDev
         }
       }
       if (MASSV) vals[3 * NG] = ec;
+    } else if constexpr (PK) {  // wall: q.n (q.n / Hs + c) + pressure relative to L's mean (LLF: (q.n + |q.n|) / Hs)
+      const f2 Ld = make_float2(tl[0].d, tl[1].d), LH = make_float2(tl[0].H, tl[1].H);
+      const f2 un = (FLUX == 1) ? mul2(add2(ax.mL, abs2(ax.mL)), ax.iL) : mul2(ax.mL, ax.iL);
+      const f2 wl = fma2(ax.mL, fma2(p2(fsqrt_pos(g)), ax.sL, un), mul2(p2(0.5f * g), mul2(Ld, fma2(p2(2.f), LH, neg2(Ld)))));
+      const f2 cw = mul2(mul2(make_float2(tab.gw[0], tab.gw[1]), p2(hl)), wl);
+      const f2 vx = mul2(cw, p2(nx)), vy = mul2(cw, p2(ny));
+      vals[0] = vals[1] = T(0);
+      vals[2] = vx.x; vals[3] = vx.y; vals[4] = vy.x; vals[5] = vy.y;
     } else {
 #pragma unroll
       for (int k = 0; k < NG; ++k) {
@@ -693,6 +709,16 @@ __device__ __forceinline__ void tile_edge(const StageArgs<Pol>& a, const ScenDev
         }
       }
       if (MASSV) vals[3 * NG] = -ec;
+    } else if constexpr (PK) {  // wall seen from R along -n: q.n_R = -mR
+      const f2 mR = neg2(ax.mR);
+      const f2 Rd = make_float2(tr[0].d, tr[1].d), RH = make_float2(tr[0].H, tr[1].H);
+      const f2 un = (FLUX == 1) ? mul2(add2(mR, abs2(mR)), ax.iR) : mul2(mR, ax.iR);
+      const f2 wr = fma2(mR, fma2(p2(fsqrt_pos(g)), ax.sR, un), mul2(p2(0.5f * g), mul2(Rd, fma2(p2(2.f), RH, neg2(Rd)))));
+      // R's point kr is L's point 1 - kr
+      const f2 cw = mul2(mul2(make_float2(tab.gw[0], tab.gw[1]), p2(-hl)), make_float2(wr.y, wr.x));
+      const f2 vx = mul2(cw, p2(nx)), vy = mul2(cw, p2(ny));
+      vals[0] = vals[1] = T(0);
+      vals[2] = vx.x; vals[3] = vx.y; vals[4] = vy.x; vals[5] = vy.y;
     } else {
 #pragma unroll
       for (int kr = 0; kr < NG; ++kr) {
