@@ -424,14 +424,18 @@ __device__ __forceinline__ void tile_area(const Elem<P, Pol>& E, const Geo<Pol>&
       const T fxx = tq.qx * u + pp, fyx = tq.qx * v;
       const T fxy = tq.qy * u, fyy = tq.qy * v + pp;
       const T wq = tab.qw[q] * detJ;
+      // each flux rotated once into the reference directions (grad phi_m = qdr grad r + qds grad s),
+      // with the weight: then two products per mode and variable
+      const T zr = wq * (rx * tq.qx + ry * tq.qy), zs = wq * (sx * tq.qx + sy * tq.qy);
+      const T xr = wq * (rx * fxx + ry * fyx), xs2 = wq * (sx * fxx + sy * fyx);
+      const T yr = wq * (rx * fxy + ry * fyy), ys2 = wq * (sx * fxy + sy * fyy);
+      const T wsx = wq * sx_, wsy = wq * sy_;
 #pragma unroll
       for (int m = 0; m < NP; ++m) {
-        const T dxm = tab.qdr[q][m] * rx + tab.qds[q][m] * sx;
-        const T dym = tab.qdr[q][m] * ry + tab.qds[q][m] * sy;
-        const T ph = tab.qphi[q][m];
-        if (m > 0) Rz[m] = fma(wq, dxm * tq.qx + dym * tq.qy, Rz[m]);
-        Rx[m] = fma(wq, dxm * fxx + dym * fyx + ph * sx_, Rx[m]);
-        Ry[m] = fma(wq, dxm * fxy + dym * fyy + ph * sy_, Ry[m]);
+        const T dr = tab.qdr[q][m], ds = tab.qds[q][m], ph = tab.qphi[q][m];
+        if (m > 0) Rz[m] = fma(dr, zr, fma(ds, zs, Rz[m]));
+        Rx[m] = fma(dr, xr, fma(ds, xs2, fma(ph, wsx, Rx[m])));
+        Ry[m] = fma(dr, yr, fma(ds, ys2, fma(ph, wsy, Ry[m])));
       }
     }
   }
