@@ -629,7 +629,19 @@ __device__ __forceinline__ void tile_edge(const StageArgs<Pol>& a, const ScenDev
     fy[0] = fy2.x; fy[1] = fy2.y;
   }
   if (!land) {
-    if constexpr (!PK) {
+    if constexpr (!PK && P == 2 && sizeof(T) == 4 && DG_PACKED_FLUX) {  // points 0 and 1 packed, point 2 alone
+      const Trace2 L2{make_float2(tl[0].d, tl[1].d), make_float2(tl[0].H, tl[1].H), make_float2(tl[0].qx, tl[1].qx),
+                      make_float2(tl[0].qy, tl[1].qy)};
+      const Trace2 R2{make_float2(tr[0].d, tr[1].d), make_float2(tr[0].H, tr[1].H), make_float2(tr[0].qx, tr[1].qx),
+                      make_float2(tr[0].qy, tr[1].qy)};
+      f2 fz2, fx2, fy2;
+      FluxAux2 ax2;
+      edge_flux_pair<FLUX>(L2, R2, p2(dcRL), p2(nx), p2(ny), g, H0, fz2, fx2, fy2, ax2);
+      fz[0] = fz2.x; fz[1] = fz2.y;
+      fx[0] = fx2.x; fx[1] = fx2.y;
+      fy[0] = fy2.x; fy[1] = fy2.y;
+      edge_flux<FLUX, T>(tl[NG - 1], tr[NG - 1], dcRL, nx, ny, g, H0, fz[NG - 1], fx[NG - 1], fy[NG - 1]);
+    } else if constexpr (!PK) {
 #pragma unroll
       for (int k = 0; k < NG; ++k) edge_flux<FLUX, T>(tl[k], tr[k], dcRL, nx, ny, g, H0, fz[k], fx[k], fy[k]);
     }
