@@ -71,6 +71,8 @@ struct RefTab {
   T qwT[MAXNQP];                   // qw, padded
   T qphiT[MAXNP][MAXNQP];          // qphi transposed
   T qwphiT[MAXNP][MAXNQP];         // qw[q] * qphi[q][m], same order
+  T qdrT[MAXNP][MAXNQP];           // qdr transposed
+  T qdsT[MAXNP][MAXNQP];           // qds transposed
 };
 
 // per-scenario forcing constants in the arithmetic type of a path

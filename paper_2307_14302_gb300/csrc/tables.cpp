@@ -177,6 +177,8 @@ void build_tables(int p, RefTab<double>& t) {
     for (int q = 0; q < t.nq; ++q) {
       t.qphiT[m][q] = t.qphi[q][m];
       t.qwphiT[m][q] = t.qw[q] * t.qphi[q][m];
+      t.qdrT[m][q] = t.qdr[q][m];
+      t.qdsT[m][q] = t.qds[q][m];
     }
 }
 

@@ -401,6 +401,69 @@ __device__ __forceinline__ void tile_area(const Elem<P, Pol>& E, const Geo<Pol>&
       Rx[m] = detJ * (gx[m] * SF[1] + gy[m] * SF[4] + SS[m][0]);
       Ry[m] = detJ * (gx[m] * SF[2] + gy[m] * SF[5] + SS[m][1]);
     }
+  } else if constexpr (sizeof(T) == 4 && DG_PACKED_FLUX) {
+    // FP32: the points in packed pairs (0,1), (2,3), (4,5), (6,7); point 7 has zero weight and zero
+    // basis values (the mean state, finite) and adds exact zeros
+    static_assert(NQ + 1 == MAXNQP, "one padding point");
+    constexpr int NS = NP - 1;
+    f2 Rz2[NP], Rx2[NP], Ry2[NP];
+#pragma unroll
+    for (int m = 0; m < NP; ++m) Rz2[m] = Rx2[m] = Ry2[m] = p2(0.f);
+    const f2 rx2 = p2(rx), ry2 = p2(ry), sx2 = p2(sx), sy2 = p2(sy), detJ2 = p2(detJ);
+    const f2 H02 = p2(H0), hg = p2(0.5f * g), ghbx = p2(g * hbx), ghby = p2(g * hby), cfm2 = p2(cfm);
+    const f2 xb2 = p2(acc_r(E.xb)), yb2 = p2(acc_r(E.yb)), Hb2 = p2(E.Hb), hb12 = p2(E.hb1), hb22 = p2(E.hb2);
+#pragma unroll
+    for (int q = 0; q < NQ + 1; q += 2) {
+      f2 d = p2(0.f), qx = xb2, qy = yb2;
+#pragma unroll
+      for (int m = 0; m < NS; ++m) {
+        const f2 ph = vtab<f2, float>(tab.qphiT[m + 1], q);
+        d = fma2(p2(E.zs[m]), ph, d);
+        qx = fma2(p2(E.xs[m]), ph, qx);
+        qy = fma2(p2(E.ys[m]), ph, qy);
+      }
+      const f2 H = add2(Hb2, add2(d, fma2(hb12, vtab<f2, float>(tab.qphiT[1], q),
+                                          mul2(hb22, vtab<f2, float>(tab.qphiT[2], q)))));
+      const f2 Hs = max2(H, H02);
+      const f2 iH = rcp2(Hs);
+      const f2 u = mul2(qx, iH), v = mul2(qy, iH);
+      const f2 pp = mul2(mul2(hg, d), fma2(p2(2.f), H, neg2(d)));  // g/2 d (2H - d)
+      f2 tau = p2(0.f);
+      if (friction <= 1) tau = vtau(qx, qy, u, v, Hs, iH, cfm2, friction);
+      float Fx0 = 0.f, Fy0 = 0.f, Fx1 = 0.f, Fy1 = 0.f;
+      if (press) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          if (q + k >= NQ) continue;
+          const float px = tab.ql[q + k][0] * vx[0] + tab.ql[q + k][1] * vx[1] + tab.ql[q + k][2] * vx[2];
+          const float py = tab.ql[q + k][0] * vy[0] + tab.ql[q + k][1] * vy[1] + tab.ql[q + k][2] * vy[2];
+          setup_force<float>(F, px, py, k ? H.y : H.x, g, k ? Fx1 : Fx0, k ? Fy1 : Fy0);
+        }
+      }
+      const f2 sxs = fma2(ghbx, d, fma2(neg2(tau), qx, make_float2(Fx0, Fx1)));
+      const f2 sys = fma2(ghby, d, fma2(neg2(tau), qy, make_float2(Fy0, Fy1)));
+      const f2 fxx = fma2(qx, u, pp), fyx = mul2(qx, v), fxy = mul2(qy, u), fyy = fma2(qy, v, pp);
+      const f2 wq = mul2(vtab<f2, float>(tab.qwT, q), detJ2);
+      // fluxes rotated into the reference directions, with the weight
+      const f2 zr = mul2(wq, fma2(rx2, qx, mul2(ry2, qy))), zs = mul2(wq, fma2(sx2, qx, mul2(sy2, qy)));
+      const f2 xr = mul2(wq, fma2(rx2, fxx, mul2(ry2, fyx))), xs2 = mul2(wq, fma2(sx2, fxx, mul2(sy2, fyx)));
+      const f2 yr = mul2(wq, fma2(rx2, fxy, mul2(ry2, fyy))), ys2 = mul2(wq, fma2(sx2, fxy, mul2(sy2, fyy)));
+      const f2 wsx = mul2(wq, sxs), wsy = mul2(wq, sys);
+#pragma unroll
+      for (int m = 0; m < NP; ++m) {
+        const f2 dr = vtab<f2, float>(tab.qdrT[m], q), ds = vtab<f2, float>(tab.qdsT[m], q);
+        const f2 ph = vtab<f2, float>(tab.qphiT[m], q);
+        if (m > 0) Rz2[m] = fma2(dr, zr, fma2(ds, zs, Rz2[m]));
+        Rx2[m] = fma2(dr, xr, fma2(ds, xs2, fma2(ph, wsx, Rx2[m])));
+        Ry2[m] = fma2(dr, yr, fma2(ds, ys2, fma2(ph, wsy, Ry2[m])));
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < NP; ++m) {
+      Rz[m] = Rz2[m].x + Rz2[m].y;
+      Rx[m] = Rx2[m].x + Rx2[m].y;
+      Ry[m] = Ry2[m].x + Ry2[m].y;
+    }
   } else {
 #pragma unroll
     for (int m = 0; m < NP; ++m) Rz[m] = Rx[m] = Ry[m] = T(0);
