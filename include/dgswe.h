@@ -270,6 +270,15 @@ int dgswe_ensemble_get_ledger(dgswe_h ens, int32_t member, dgswe_ledger* out);
 int dgswe_set_launch(dgswe_h, int32_t block, int32_t waves, int32_t split);
 int dgswe_get_launch(dgswe_h, int32_t* block, int32_t* waves, int32_t* split);
 
+/* Feature sets (diagnostics and tests).  *run: the features of this run as a bit set (1 river
+ * boundary edges, 2 tidal boundary edges, 4 pressure set-up, 8 nodal rain, 16 storm rain,
+ * 32 gridded rain, 64 Manning friction, 128 quadratic friction, 256 no friction, 512 stages whose
+ * Shu-Osher weights are powers of two, 1024 other stage weights, 2048 a scenario without rain).
+ * *kernel: the features compiled into the tile-form kernel that a stage launches: the narrowest
+ * specialised instantiation that covers the run, else the generic one (4095, every feature).
+ * Either pointer may be NULL.  DGSWE_ESTATE before the state is set. */
+int dgswe_get_tile_features(dgswe_h, int32_t* run, int32_t* kernel);
+
 /* How dgswe_step enqueues its work: 1 (default) replays whole steps from CUDA graphs captured
  * once (1-step and 8-step graphs); 0 launches every kernel of every stage directly on the
  * stream.  Results are bit-identical; the direct form exists to measure what the graphs save

@@ -1539,6 +1539,17 @@ int dgswe_get_launch(dgswe_h h, int32_t* block, int32_t* waves, int32_t* split) 
   return 0;
 }
 
+int dgswe_get_tile_features(dgswe_h h, int32_t* run, int32_t* kernel) {
+  if (int rc = check_handle(h)) return rc;
+  if (!h->ready) return fail(DGSWE_ESTATE, "no state");
+  if (run) *run = h->feat;
+  if (kernel) {
+    const int ft = mixed(h) ? tile_spec_features(h->prm.p, h->prm.flux, h->feat) : -1;
+    *kernel = ft >= 0 ? ft : FT_ALL;
+  }
+  return 0;
+}
+
 int64_t dgswe_launch_count(dgswe_h h) { return h ? h->launches : 0; }
 
 }  // extern "C"

@@ -126,6 +126,8 @@ int tile_blocks_per_sm(int p, int flux, int feat, int block);
 cudaError_t launch_tile_spec(int p, int flux, int feat, const StageArgs<Mixed>& a, int grid, int block,
                              cudaStream_t s);
 int tile_spec_blocks_per_sm(int p, int flux, int feat, int block);
+// Feature bits of the specialised instantiation that covers feat, or -1 when none does
+int tile_spec_features(int p, int flux, int feat);
 // reference tables and shared-memory limits of the specialised instantiations' translation unit
 cudaError_t upload_tile_spec_tables(int p, const RefTab<float>& tf, const RefTab<double>& td);
 // edge kernel of the split path: one thread per interior edge, writes both sides' slots

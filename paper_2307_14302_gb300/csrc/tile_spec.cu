@@ -58,6 +58,11 @@ cudaError_t launch_tile_spec(int p, int flux, int feat, const StageArgs<Mixed>& 
   return cudaGetLastError();
 }
 
+int tile_spec_features(int p, int flux, int feat) {
+  const Spec* sp = find_spec(p, flux, feat);
+  return sp ? sp->ft : -1;
+}
+
 int tile_spec_blocks_per_sm(int p, int flux, int feat, int block) {
   const Spec* sp = find_spec(p, flux, feat);
   if (!sp) return -1;

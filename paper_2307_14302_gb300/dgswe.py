@@ -61,7 +61,7 @@ EXPORTS = [
     "dgswe_set_rain_parametric", "dgswe_set_rain_grid", "dgswe_set_tide", "dgswe_set_river", "dgswe_set_pressure_setup",
     "dgswe_set_state", "dgswe_load_state", "dgswe_step", "dgswe_sync", "dgswe_get_dt", "dgswe_get_state", "dgswe_get_state_device",
     "dgswe_get_dry", "dgswe_get_ledger", "dgswe_volume", "dgswe_record_bytes", "dgswe_bind_device", "dgswe_volume_sum_noalloc", "dgswe_ensemble_create", "dgswe_ensemble_step",
-    "dgswe_ensemble_get_state", "dgswe_ensemble_get_ledger", "dgswe_set_launch", "dgswe_get_launch",
+    "dgswe_ensemble_get_state", "dgswe_ensemble_get_ledger", "dgswe_set_launch", "dgswe_get_launch", "dgswe_get_tile_features",
     "dgswe_set_graphs", "dgswe_launch_count", "dgswe_destroy", "dgswe_last_error",
 ]
 
@@ -113,6 +113,7 @@ def lib():
         "dgswe_ensemble_get_ledger": ([_h, C.c_int32, C.POINTER(Ledger)], C.c_int),
         "dgswe_set_launch": ([_h, C.c_int32, C.c_int32, C.c_int32], C.c_int),
         "dgswe_get_launch": ([_h, _i, _i, _i], C.c_int),
+        "dgswe_get_tile_features": ([_h, _i, _i], C.c_int),
         "dgswe_launch_count": ([_h], C.c_int64),
         "dgswe_set_graphs": ([_h, C.c_int32], C.c_int),
         "dgswe_destroy": ([_h], None),
@@ -275,6 +276,12 @@ class Solver:
         b, w, sp = C.c_int32(), C.c_int32(), C.c_int32()
         _check(lib().dgswe_get_launch(self.h, C.byref(b), C.byref(w), C.byref(sp)))
         return b.value, w.value, sp.value
+
+    def tile_features(self):
+        """(features of the run, features compiled into the tile kernel it launches) as bit sets."""
+        r, k = C.c_int32(), C.c_int32()
+        _check(lib().dgswe_get_tile_features(self.h, C.byref(r), C.byref(k)))
+        return r.value, k.value
 
     def launch_count(self) -> int:
         return int(lib().dgswe_launch_count(self.h))
