@@ -31,8 +31,12 @@
 // the 16-byte reads of a warp, at its own slots or at any mix of neighbour slots, spread over
 // the banks.  Shared memory per warp: the two buffers, the halo records [RV][32], the edge
 // descriptors [96] {left side, right side, left normal} and the edge slots [3][pairs][32], which
-// overlay the consumed static part of the current buffer (about 12 KB in the mixed p = 1 path).  Neighbours beyond 32 halo slots (none on Hilbert-ordered
-// meshes; kept for generality) are read from global memory.
+// overlay the consumed static part of the current buffer (about 12 KB in the mixed p = 1 path).
+// Neighbours beyond 32 halo slots (none on Hilbert-ordered meshes; kept for generality) are read
+// from global memory.
+//
+// The kernel takes a set of Feature bits (args.h): the generic instantiation has all of them;
+// the specialised ones (tile_spec.cu) leave out the code of the features a run does not have.
 #pragma once
 #include "stage.cuh"
 
