@@ -167,10 +167,8 @@ def step_bytes_per_element(precision: str, p: int) -> float:
 
 
 FORM_KERNEL = {0: "stage_kernel (fused)", 1: "edge_kernel + stage_kernel (split)",
-               2: "tile_kernel (instantiation specialised to the run's features where one covers them)",
-               3: "tile_step_kernel (every stage of a step in one cooperative launch; instantiation specialised "
-                  "to the run's features where one covers them)"}
-FORM_PROFILE = {0: "stage_kernel", 1: "stage_kernel", 2: "tile_kernel", 3: "tile_step_kernel"}
+               2: "tile_kernel (instantiation specialised to the run's features where one covers them)"}
+FORM_PROFILE = {0: "stage_kernel", 1: "stage_kernel", 2: "tile_kernel"}
 
 
 def load_peaks():
@@ -402,11 +400,9 @@ def our_arm(args, ws, rank, local):
     clocks = clk.summary()
 
     # roofline of the stage kernel: algorithmic bytes per launch (scope-table count per element and
-    # step, over the stages, or the whole step for the fused step) / average launch time measured
-    # with the events above
-    per_step = 1 if split == 3 else stages
-    bytes_per_launch = E * step_bytes_per_element("mixed", p) / per_step
-    launch_s = t_mixed / (args.steps * per_step)
+    # step, over the stages) / average stage time measured with the events above
+    bytes_per_launch = E * step_bytes_per_element("mixed", p) / stages
+    launch_s = t_mixed / (args.steps * stages)
     peak, peak_kind = load_peaks()
     achieved = bytes_per_launch / launch_s / 1e9
     summary = f"{FORM_PROFILE[split]}_mixed_p{p}_{args.workload}.md"
@@ -481,7 +477,7 @@ def our_arm(args, ws, rank, local):
                          "peak_source": peak_kind, "kernel": f"{FORM_KERNEL[split]}, p={p}, Roe, mixed",
                          "bytes_per_launch": bytes_per_launch,
                          "bytes_model": f"{step_bytes_per_element('mixed', p):.0f} B per element and step "
-                                        f"(scope table) over {per_step} launch(es) of {stages} stages",
+                                        f"(scope table) over {stages} stages",
                          "traffic_source": summary if traffic is not None else None,
                          "avg_launch_us": 1e6 * launch_s},
             "cpu_baseline": cpu,
@@ -681,7 +677,7 @@ def kernel_hash():
     import hashlib
 
     h = hashlib.sha256()
-    for f in ("stage.cuh", "tile.cuh", "tile_spec.cu", "tile_step.cu", "args.h", "layout.h"):
+    for f in ("stage.cuh", "tile.cuh", "tile_spec.cu", "args.h", "layout.h"):
         h.update(open(os.path.join(ROOT, "paper_2307_14302_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

@@ -265,14 +265,8 @@ int dgswe_ensemble_get_ledger(dgswe_h ens, int32_t member, dgswe_ledger* out);
  * in which both neighbours evaluate an interior edge; 1 a separate edge kernel computes every
  * interior edge flux once and the element kernel gathers it; 2 the tile form, one kernel in which
  * each warp evaluates every edge touching its 32-element tile once from records staged in shared
- * memory; 3 the fused step, the tile form with every Runge-Kutta stage of a step in one
- * cooperative launch (a tile's next stage waits, bounded, for the stage-complete counters of
- * the tiles its edges read instead of for a launch boundary).  Form 3 serves the FP32-mixed
- * path of runs without gridded rain or slope limiter, with waves = 1, and gives the tile form's
- * results bit for bit at the same block size; a wait that runs out is reported by dgswe_sync as
- * DGSWE_ETIMEOUT.  The forms agree to rounding; for a fixed form results do not depend on block
- * or waves.  Returns DGSWE_EINVAL for other values, and (when the state is set, or at set_state)
- * for form 3 where it does not serve the run. */
+ * memory.  The three forms agree to rounding; for a fixed form results do not depend on block or
+ * waves.  Returns DGSWE_EINVAL for other values. */
 int dgswe_set_launch(dgswe_h, int32_t block, int32_t waves, int32_t split);
 int dgswe_get_launch(dgswe_h, int32_t* block, int32_t* waves, int32_t* split);
 

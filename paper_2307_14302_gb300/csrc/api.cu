@@ -127,9 +127,7 @@ struct dgswe_ctx {
   DevBuf rec[3], nbr, geo, nodes, node_xy, xy64, hbn, rain_e, rain_node, node_scen, lim, scen, tile_scen, tile_meta, xy0,
       ledger, ctl,
       einv, grids, rivers, scratch,
-      gather_buf, edges, slots,
-      dep_off, deps, done;                 // fused step: per-tile dependencies and completion counters
-  int dep_max = 0;                         // most dependencies of one tile (the tile included)
+      gather_buf, edges, slots;
   long long nedges = 0;
   int ntiles = 0;                          // 32-element tiles
   int wslots = 0;                          // ledger slots per scenario
@@ -156,7 +154,7 @@ struct dgswe_ctx {
     DevBuf* bufs[] = {&rec[0], &rec[1], &rec[2], &nbr, &geo, &nodes, &node_xy, &xy64, &hbn, &rain_e, &scen,
                       &tile_scen, &tile_meta, &xy0, &ledger, &ctl, &einv, &grids, &rivers, &scratch, &gather_buf,
                       &edges, &slots,
-                      &rain_node, &node_scen, &lim, &dep_off, &deps, &done};
+                      &rain_node, &node_scen, &lim};
     for (DevBuf* b : bufs) b->alloc(0);
     if (g1) cudaGraphExecDestroy(g1);
     if (gK) cudaGraphExecDestroy(gK);
@@ -311,7 +309,6 @@ static int upload_all_tables(int p) {
   CU(upload_tile_tables<Mixed>(p, g_tabf[p], g_tabd[p]));
   CU(upload_tile_spec_tables(p, g_tabf[p], g_tabd[p]));
   CU(upload_tile_tables<Fp64>(p, g_tabf[p], g_tabd[p]));
-  CU(upload_tile_step_tables(p, g_tabf[p], g_tabd[p]));
   return 0;
 }
 
@@ -652,30 +649,6 @@ static int build_layout(dgswe_h h) {
     return fail(DGSWE_ENOMEM, "device allocation failed");
   CU(cudaMemcpy(h->tile_scen.p, ts.data(), 4 * ts.size(), cudaMemcpyHostToDevice));
   CU(cudaMemcpy(h->tile_meta.p, tm.data(), 4 * tm.size(), cudaMemcpyHostToDevice));
-  // fused step: each tile depends on itself and on the tiles that hold its out-of-tile
-  // neighbours; completion counters start at zero with the launch epoch (the control block above)
-  std::vector<int32_t> doff((size_t)h->ntiles + 1, 0), dl;
-  h->dep_max = 0;
-  for (int t = 0; t < h->ntiles; ++t) {
-    const size_t at = dl.size();
-    doff[t] = (int32_t)at;
-    dl.push_back(t);
-    for (int i = 0; i < TILE; ++i)
-      for (int j = 0; j < 3; ++j) {
-        const int32_t c = nbr[4 * ((size_t)t * TILE + i) + j];
-        if (c < 0) continue;
-        const int32_t u = (c >> 2) / TILE;
-        if (std::find(dl.begin() + at, dl.end(), u) == dl.end()) dl.push_back(u);
-      }
-    h->dep_max = std::max(h->dep_max, (int)(dl.size() - at));
-  }
-  doff[h->ntiles] = (int32_t)dl.size();
-  if (h->dep_off.alloc(4 * doff.size()) || h->deps.alloc(4 * std::max<size_t>(1, dl.size())) ||
-      h->done.alloc(4 * std::max<size_t>(1, (size_t)h->ntiles)))
-    return fail(DGSWE_ENOMEM, "device allocation failed");
-  CU(cudaMemcpy(h->dep_off.p, doff.data(), 4 * doff.size(), cudaMemcpyHostToDevice));
-  if (!dl.empty()) CU(cudaMemcpy(h->deps.p, dl.data(), 4 * dl.size(), cudaMemcpyHostToDevice));
-  CU(cudaMemset(h->done.p, 0, 4 * std::max<size_t>(1, (size_t)h->ntiles)));
   CU(cudaMemset(h->ledger.p, 0, 16 * (size_t)h->wslots * ns));
   h->wcur = 0;
   CU(cudaMemcpy(h->scen.p, sd.data(), sizeof(ScenDev) * ns, cudaMemcpyHostToDevice));
@@ -825,51 +798,7 @@ static int launches_per_stage(dgswe_h h) {
   return 1 + ((h->split == 1 && h->nedges > 0) ? 1 : 0) + (h->grid_rain ? 1 : 0) + (h->prm.limiter ? 1 : 0);
 }
 
-// the fused step (split 3) serves the mixed path when no node kernel or limiter runs between the
-// stages, no tile depends on more than 32 tiles (one watching lane each) and the device launches
-// cooperative kernels
-static bool step_form_ok(dgswe_h h) {
-  if (!mixed(h) || h->grid_rain || h->prm.limiter || h->dep_max > 32 || h->stages.size() > (size_t)MAXSTAGE)
-    return false;
-  int coop = 0;
-  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return coop != 0;
-}
-
-static long long launches_per_step(dgswe_h h) {
-  return h->split == 3 ? 1 : (long long)h->stages.size() * launches_per_stage(h);
-}
-
-static StepArgs<Mixed> make_step_args(dgswe_h h, int tune) {
-  StepArgs<Mixed> sa;
-  std::memset(&sa, 0, sizeof sa);
-  const int S = (int)h->stages.size();
-  for (int k = 0; k < S; ++k) sa.st[k] = make_args<Mixed>(h, k, tune);
-  sa.dep_off = h->dep_off.as<int32_t>();
-  sa.deps = h->deps.as<int32_t>();
-  sa.done = h->done.as<unsigned>();
-  sa.nst = S;
-  return sa;
-}
-
-// one Runge-Kutta step: every stage's launches, or the fused step's one launch
-static int launch_step_once(dgswe_h h, int tune, cudaStream_t s) {
-  if (h->split != 3) {
-    for (size_t k = 0; k < h->stages.size(); ++k)
-      if (int rc = launch_stage_once(h, (int)k, tune, s)) return rc;
-    return 0;
-  }
-  const cudaError_t e = launch_tile_step(h->prm.p, h->prm.flux, h->feat, make_step_args(h, tune), h->grid, h->block, s);
-  if (e != cudaSuccess) return fail(DGSWE_ECUDA, "fused step launch: %s", cudaGetErrorString(e));
-  h->launches++;
-  return 0;
-}
-
 static int occupancy(dgswe_h h, int block) {
-  if (h->split == 3) return step_form_ok(h) ? tile_step_blocks_per_sm(h->prm.p, h->prm.flux, h->feat, block) : 0;
   if (h->split == 2)
     return mixed(h) ? tile_blocks_per_sm<Mixed>(h->prm.p, h->prm.flux, h->feat, block)
                     : tile_blocks_per_sm<Fp64>(h->prm.p, h->prm.flux, h->feat, block);
@@ -885,12 +814,6 @@ static int apply_launch(dgswe_h h, int block, int waves, int split) {
   h->block = block;
   h->waves = waves;
   h->split = split;
-  if (split == 3 && !step_form_ok(h))
-    return fail(DGSWE_EINVAL,
-                "the fused step (form 3) needs the mixed path, no gridded rain, no limiter, at most 32 "
-                "dependencies per tile (this run: %d) and cooperative launches",
-                h->dep_max);
-  if (split == 3 && waves != 1) return fail(DGSWE_EINVAL, "the fused step (form 3) runs one wave (all CTAs resident)");
   const int occ = occupancy(h, block);
   if (occ < 1) return fail(DGSWE_EINVAL, "form %d does not fit a block of %d threads on this device", split, block);
   const int want = sms * occ * waves;
@@ -911,18 +834,20 @@ static int autotune(dgswe_h h) {
   int bb = 128, bp = 0;
   const int blocks[3] = {64, 128, 256};
   int bs = 1;
-  for (int sp = 0; sp <= 3; ++sp)
+  for (int sp = 0; sp <= 2; ++sp)
   for (int pi = 1; pi <= 2; ++pi)
     for (int bi = 0; bi < 3; ++bi) {
-      if (sp == 3 && pi != 1) continue;  // the fused step runs one wave
       h->split = sp;
       if (occupancy(h, blocks[bi]) < 1) continue;
       if (int rc = apply_launch(h, blocks[bi], pi, sp)) return rc;
+      const int ns = (int)h->stages.size();
       for (int w = 0; w < 2; ++w)
-        if (int rc = launch_step_once(h, 1, h->stream)) return rc;
+        for (int st = 0; st < ns; ++st)
+          if (int rc = launch_stage_once(h, st, 1, h->stream)) return rc;
       CU(cudaEventRecord(e0, h->stream));
       for (int r = 0; r < 5; ++r)
-        if (int rc = launch_step_once(h, 1, h->stream)) return rc;
+        for (int st = 0; st < ns; ++st)
+          if (int rc = launch_stage_once(h, st, 1, h->stream)) return rc;
       CU(cudaEventRecord(e1, h->stream));
       CU(cudaEventSynchronize(e1));
       float ms = 0.f;
@@ -941,11 +866,12 @@ static int build_graphs(dgswe_h h) {
     cudaGraph_t g;
     CU(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
     int rc = 0;
-    for (int k = 0; k < nsteps && !rc; ++k) rc = launch_step_once(h, 0, h->cap);
+    for (int k = 0; k < nsteps && !rc; ++k)
+      for (size_t s = 0; s < h->stages.size() && !rc; ++s) rc = launch_stage_once(h, (int)s, 0, h->cap);
     cudaError_t ce = cudaStreamEndCapture(h->cap, &g);
     if (rc) return rc;
     if (ce != cudaSuccess) return fail(DGSWE_ECUDA, "graph capture: %s", cudaGetErrorString(ce));
-    h->launches -= nsteps * launches_per_step(h);  // counted when the graph runs
+    h->launches -= nsteps * (long long)h->stages.size() * launches_per_stage(h);  // counted when the graph runs
     cudaGraphExec_t ex;
     ce = cudaGraphInstantiate(&ex, g, 0);
     cudaGraphDestroy(g);
@@ -1266,14 +1192,15 @@ int dgswe_step(dgswe_h h, int64_t n) {
   DeviceGuard dg_(h->device);
   if (h->autotune)
     if (int rc = autotune(h)) return rc;
-  if (!h->graphs) {  // every step's launches made directly
+  if (!h->graphs) {  // every stage launched directly
     for (int64_t i = 0; i < n; ++i)
-      if (int rc = launch_step_once(h, 0, h->stream)) return rc;
+      for (size_t s = 0; s < h->stages.size(); ++s)
+        if (int rc = launch_stage_once(h, (int)s, 0, h->stream)) return rc;
     return 0;
   }
   if (!h->g1)
     if (int rc = build_graphs(h)) return rc;
-  const long long per = launches_per_step(h);
+  const long long per = (long long)h->stages.size() * launches_per_stage(h);
   for (int64_t i = 0; i < n / h->K; ++i) CU(cudaGraphLaunch(h->gK, h->stream));
   for (int64_t i = 0; i < n % h->K; ++i) CU(cudaGraphLaunch(h->g1, h->stream));
   h->launches += n * per;
@@ -1296,8 +1223,7 @@ int dgswe_sync(dgswe_h h) {
   CU(cudaMemcpy(&c, h->ctl.p, sizeof c, cudaMemcpyDeviceToHost));
   if (c.err & ERR_NONFINITE) return fail(DGSWE_ENONFINITE, "a stage produced a non-finite state");
   if (c.err & ERR_NEGDEPTH) return fail(DGSWE_ENEGDEPTH, "an element mean depth fell below zero");
-  if (c.err & ERR_TIMEOUT)
-    return fail(DGSWE_ETIMEOUT, "a bulk copy into shared memory, or a fused step's wait for a neighbouring tile, did not complete");
+  if (c.err & ERR_TIMEOUT) return fail(DGSWE_ETIMEOUT, "a bulk copy into shared memory did not complete");
   return 0;
 }
 
@@ -1592,8 +1518,7 @@ int dgswe_set_launch(dgswe_h h, int32_t block, int32_t waves, int32_t split) {
     return 0;
   }
   if (waves < 1 || waves > 2) return fail(DGSWE_EINVAL, "waves must be 1 or 2");
-  if (split < 0 || split > 3) return fail(DGSWE_EINVAL, "split must be 0, 1, 2 or 3");
-  if (split == 3 && waves != 1) return fail(DGSWE_EINVAL, "the fused step (split 3) runs one wave");
+  if (split < 0 || split > 2) return fail(DGSWE_EINVAL, "split must be 0, 1 or 2");
   h->autotune = false;
   if (!h->ready) {
     h->block = block;

@@ -63,16 +63,6 @@ struct StageArgs {
   T g, H0, cf;
 };
 
-// Arguments of the fused step (every Shu-Osher stage of one step in one launch of the tile form)
-template <class Pol>
-struct StepArgs {
-  StageArgs<Pol> st[MAXSTAGE];  // the stages, in order
-  const int32_t* dep_off;       // [ntiles + 1]: tile t's dependencies are deps[dep_off[t] .. dep_off[t + 1])
-  const int32_t* deps;          // the tile itself and every tile holding an out-of-tile neighbour (at most 32)
-  unsigned* done;               // per tile: stages completed, counted over fused launches (epoch S + k + 1)
-  int nst;                      // stages of the step
-};
-
 }  // namespace dg
 
 namespace dg {
@@ -140,12 +130,6 @@ int tile_spec_blocks_per_sm(int p, int flux, int feat, int block);
 int tile_spec_features(int p, int flux, int feat);
 // reference tables and shared-memory limits of the specialised instantiations' translation unit
 cudaError_t upload_tile_spec_tables(int p, const RefTab<float>& tf, const RefTab<double>& td);
-// fused step (split = 3): all stages of one step in one cooperative launch of the tile form, mixed
-// path, runs without gridded rain or slope limiter; launch, resident CTAs per SM (0: does not
-// fit), and the tables of its translation unit
-cudaError_t launch_tile_step(int p, int flux, int feat, const StepArgs<Mixed>& a, int grid, int block, cudaStream_t s);
-int tile_step_blocks_per_sm(int p, int flux, int feat, int block);
-cudaError_t upload_tile_step_tables(int p, const RefTab<float>& tf, const RefTab<double>& td);
 // edge kernel of the split path: one thread per interior edge, writes both sides' slots
 template <class Pol>
 cudaError_t launch_edges(int p, int flux, const StageArgs<Pol>& a, int grid, int block, cudaStream_t s);

@@ -108,7 +108,7 @@ struct ScenDev {
 // device control block
 struct Ctl {
   unsigned long long step;         // completed steps (all scenarios advance together)
-  unsigned int epoch;              // fused-step launches completed (tile completion counters count in them)
+  unsigned int tile_counter;       // persistent-grid work counter
   unsigned int ticket;             // CTAs finished in the current launch
   int err;                         // ERR_* bits
   int pad;

@@ -509,20 +509,9 @@ __device__ __forceinline__ void tile_area(const Elem<P, Pol>& E, const Geo<Pol>&
 }
 
 // ---------------------------------------------------------------------- edge phase ------
-// A 16-byte vector of a record in global memory.  COH: the launch may itself have written it (a
-// fused step runs every stage in one launch), so it is read coherently at L2 (ld.global.cg),
-// never from a stale L1 line; otherwise through the read-only path.
-template <bool COH>
-__device__ __forceinline__ uint4 ld_rec(const uint4* p) {
-  if constexpr (COH)
-    return __ldcg(p);
-  else
-    return __ldg(p);
-}
-
 // record of a side: own (src < 32: [RV][32]) or staged halo (src < 64: [RV][HALO]) records in
 // shared memory, vector-major, else the global record of element src - 64
-template <int RV, bool COH>
+template <int RV>
 __device__ __forceinline__ void fetch_side(const uint4* own, const uint4* halo, const uint4* __restrict__ gin, int src,
                                            Raw<RV>& r) {
   if (src < 64) {  // shared memory, read as such (not through a generic address)
@@ -532,7 +521,7 @@ __device__ __forceinline__ void fetch_side(const uint4* own, const uint4* halo, 
     for (int v = 0; v < RV; ++v) r.v[v] = lds128(p + stride * v);
   } else {
 #pragma unroll
-    for (int v = 0; v < RV; ++v) r.v[v] = ld_rec<COH>(gin + rec_at<RV>(src - 64, v));
+    for (int v = 0; v < RV; ++v) r.v[v] = __ldg(gin + rec_at<RV>(src - 64, v));
   }
 }
 
@@ -596,7 +585,7 @@ __device__ __forceinline__ T wall_coef(const Trace<T>& t, T nx, T ny, T g, T H0)
   return qn * (un + c) + pdev(t.d, t.H, g);
 }
 
-template <int P, int FLUX, class Pol, int FT, bool COH>
+template <int P, int FLUX, class Pol, int FT>
 __device__ __forceinline__ void tile_edge(const StageArgs<Pol>& a, const ScenDev& S, const uint4* own,
                                           const uint4* halo, const EdgeDesc<typename Pol::T>* desc, void* flx, int i,
                                           const typename Pol::T (*ephi)[P + 1][np_of(P)], const float4* ephi4,
@@ -613,7 +602,7 @@ __device__ __forceinline__ void tile_edge(const StageArgs<Pol>& a, const ScenDev
   get_desc(desc, i, sL, sR, lnx, lny);
   const int jL = sL & 3, srcL = sL >> 2;
   Raw<RV> rl;
-  fetch_side<RV, COH>(own, halo, a.in, srcL, rl);
+  fetch_side<RV>(own, halo, a.in, srcL, rl);
   Elem<P, Pol> EL;
   unpack<P>(rl, EL);
   T len, il;  // edge length and its inverse
@@ -650,7 +639,7 @@ __device__ __forceinline__ void tile_edge(const StageArgs<Pol>& a, const ScenDev
     jR = sR & 3;
     srcR = sR >> 2;
     Raw<RV> rr;
-    fetch_side<RV, COH>(own, halo, a.in, srcR, rr);
+    fetch_side<RV>(own, halo, a.in, srcR, rr);
     Elem<P, Pol> ER;
     unpack<P>(rr, ER);
     dcRL = acc_sub_r(ER.zb, EL.zb);
@@ -837,23 +826,19 @@ __device__ __forceinline__ void tile_edge(const StageArgs<Pol>& a, const ScenDev
 #define DG_TILE_BOUNDS __maxnreg__(DG_TILE_MAXNREG)
 #endif
 
-// 16-byte asynchronous copy of a neighbour record into the halo: through L1 (.ca), or, when the
-// launch may itself have written the record (COH), from L2 only (.cg)
-template <bool COH>
-__device__ __forceinline__ void cp_async_rec(void* smem, const void* gmem) {
-  if constexpr (COH)
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
-  else
-    cp_async16(smem, gmem);
-}
-
-// edge basis values, read at edge-dependent indices; at p = 1 in FP32 also one 16-byte row per
-// edge {phi_1, phi_2 at point 0, phi_1, phi_2 at point 1} (phi_0 is constant and not read)
-template <int P, class Pol>
-__device__ __forceinline__ void tile_tables(typename Pol::T (*s_ephi)[P + 1][np_of(P)], float4* s_ephi4) {
+template <int P, int FLUX, class Pol, int FT = FT_ALL>
+__global__ void DG_TILE_BOUNDS tile_kernel(const StageArgs<Pol> a) {
   using T = typename Pol::T;
-  constexpr int NP = np_of(P), NG = P + 1;
+  using Acc = typename Pol::Acc;
+  using L = TileLayout<P, Pol>;
+  constexpr int NP = np_of(P), NS = NP - 1, NG = P + 1, RV = L::RV, GV = L::GV, NPR = L::NPR, NV = L::NV;
   const RefTab<T>& tab = ctab<T, P>();
+
+  // edge basis values, read at edge-dependent indices; at p = 1 in FP32 also one 16-byte row per
+  // edge {phi_1, phi_2 at point 0, phi_1, phi_2 at point 1} (phi_0 is constant and not read)
+  __shared__ T s_ephi[3][NG][NP];
+  __shared__ float4 s_ephi4[3];
+  extern __shared__ uint4 tsm[];
   const int tid = threadIdx.x;
   for (int i = tid; i < 3 * NG * NP; i += blockDim.x) {
     const int j = i / (NG * NP), k = (i / NP) % NG, m = i % NP;
@@ -863,314 +848,6 @@ __device__ __forceinline__ void tile_tables(typename Pol::T (*s_ephi)[P + 1][np_
     s_ephi4[tid] = make_float4((float)tab.ephi[tid][0][1], (float)tab.ephi[tid][0][2],
                                (float)tab.ephi[tid][NG - 1][1], (float)tab.ephi[tid][NG - 1][2]);
   __syncthreads();
-}
-
-// one TMA batch (lane 0): the tile's records, geometry, neighbour codes, first vertices and
-// metadata into a buffer, completing on its mbarrier
-template <int P, class Pol>
-__device__ __forceinline__ void tile_issue(const StageArgs<Pol>& a, int t, uint4* buf, uint32_t bar) {
-  using L = TileLayout<P, Pol>;
-  constexpr int RV = L::RV, GV = L::GV;
-  fence_proxy_async();
-  mbar_expect_tx(bar, L::TILE_BYTES);
-  bulk_g2s(smem_u32(buf), a.in + (size_t)t * TILE * RV, 16u * TILE * RV, bar);
-  bulk_g2s(smem_u32(buf + L::O_GEO), a.geo + (size_t)t * TILE * GV, 16u * TILE * GV, bar);
-  bulk_g2s(smem_u32(buf + L::O_NBR), a.nbr + (size_t)t * TILE, 16u * TILE, bar);
-  bulk_g2s(smem_u32(buf + L::O_XY), a.xy0 + (size_t)t * L::XV, 16u * L::XV, bar);
-  bulk_g2s(smem_u32(buf + L::O_META), a.tile_meta + t, 16u, bar);
-}
-
-// what a warp carries from tile to tile of a launch: the current scenario's constants and stage
-// time, and its rain and boundary-inflow volume rates not yet booked in the ledger
-template <class Pol>
-struct TileCarry {
-  typename Pol::Acc rain, bdry;
-  const ScenDev* Sp;
-  double t64;
-  int cur, rain_kind, press;
-};
-
-// One Runge-Kutta stage of one 32-element tile whose TMA batch has landed in buf: the three
-// phases of the tile form (area integrals and rain; every edge touching the tile once; lift,
-// inverse mass, Shu-Osher combination, positive-depth operator, store, ledger).  stepd is the
-// completed step count plus the stage's time fraction.  COH: records this launch may have
-// written are read coherently at L2.
-template <int P, int FLUX, class Pol, int FT, bool COH>
-__device__ __forceinline__ void tile_work(const StageArgs<Pol>& a, int tile, int gw, int lane, uint4* buf,
-                                          uint4* halo, EdgeDesc<typename Pol::T>* desc,
-                                          const typename Pol::T (*s_ephi)[P + 1][np_of(P)], const float4* s_ephi4,
-                                          double stepd, TileCarry<Pol>& c) {
-  using T = typename Pol::T;
-  using Acc = typename Pol::Acc;
-  using L = TileLayout<P, Pol>;
-  constexpr int NP = np_of(P), NS = NP - 1, NG = P + 1, RV = L::RV, GV = L::GV, NPR = L::NPR, NV = L::NV;
-  const RefTab<T>& tab = ctab<T, P>();
-  const unsigned lt = (1u << lane) - 1u;
-  const uint4* own = buf;                           // [RV][32] records
-  const uint4* geoS = own + L::O_GEO;               // [32][GV]
-  void* flx = buf + L::O_FLX;                       // [3][NPR][32] pairs, over geoS .. meta
-  const int4* nbrS = reinterpret_cast<const int4*>(own + L::O_NBR);
-  const int4 meta = reinterpret_cast<const int4*>(own + L::O_META)[0];
-  const int sc = meta.x, present = meta.y;
-  if (present == 0) {  // padding tile: no element (uniform over the warp)
-    __syncwarp();
-    return;
-  }
-  if (sc != c.cur) {
-    if (c.cur >= 0 && !a.tune) flush_ledger<P, Pol>(a, c.cur, gw, c.rain, c.bdry);
-    c.cur = sc;
-    c.Sp = a.scen + sc;
-    c.t64 = c.Sp->d.t0 + stepd * c.Sp->d.dt;  // stage time, formed in FP64
-    c.rain_kind = ft_rain(FT) >= 0 ? ft_rain(FT) : c.Sp->rain_kind;
-    c.press = (FT & FT_PRESS) ? c.Sp->press : 0;
-  }
-  const ScenDev& S = *c.Sp;
-  const int rain_kind = c.rain_kind, press = c.press;
-  const double t64 = c.t64;
-  const int e0 = tile * TILE, e = e0 + lane;
-  const bool valid = lane < present;
-  const T t = (T)t64;
-  if (a.has_n && lane == 0) bulk_prefetch_l2(a.wn + (size_t)e0 * RV, 16u * TILE * RV);  // read in phase B
-
-  // ---- edge ownership: boundary edges, edges to out-of-tile neighbours, and in-tile edges to a
-  // higher index belong to this lane; out-of-tile neighbours get a halo slot.  Edge slots: the
-  // interior edges first, then the boundary edges (fewer divergent rounds).
-  const int4 nb = valid ? nbrS[lane] : make_int4(-1, -1, -1, -1);
-  const int code[3] = {nb.x, nb.y, nb.z};
-  bool own_e[3], out[3];
-  int eidx[3], hslot[3];
-  unsigned bi[3], bb[3];
-  int nint = 0, hbase = 0;
-#pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    const int cd = code[j];
-    const int n = cd >> 2;
-    const bool inside = cd >= 0 && n >= e0 && n < e0 + TILE;
-    own_e[j] = valid && (cd < 0 || !inside || e < n);
-    out[j] = valid && cd >= 0 && !inside;
-    bi[j] = __ballot_sync(0xffffffffu, own_e[j] && cd >= 0);
-    bb[j] = __ballot_sync(0xffffffffu, own_e[j] && cd < 0);
-    const unsigned bh = __ballot_sync(0xffffffffu, out[j]);
-    hslot[j] = hbase + __popc(bh & lt);
-    hbase += __popc(bh);
-    nint += __popc(bi[j]);
-  }
-  {
-    int ib = 0, bbase = nint;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      eidx[j] = code[j] >= 0 ? ib + __popc(bi[j] & lt) : bbase + __popc(bb[j] & lt);
-      ib += __popc(bi[j]);
-      bbase += __popc(bb[j]);
-    }
-  }
-  const int nedge = nint + __popc(bb[0]) + __popc(bb[1]) + __popc(bb[2]);
-#pragma unroll
-  for (int j = 0; j < 3; ++j)
-    if (out[j] && hslot[j] < HALO) {
-#pragma unroll
-      for (int v = 0; v < RV; ++v) cp_async_rec<COH>(halo + v * HALO + hslot[j], a.in + rec_at<RV>(code[j] >> 2, v));
-    }
-  cp_async_commit();
-  Geo<Pol> G;
-  if (valid) geo_from(geoS + lane * GV, nb, G);
-  // edge descriptors {left side, right side or boundary code}
-#pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    if (!own_e[j]) continue;
-    const int cd = code[j];
-    const int me = (lane << 2) | j;
-    int sL = me, sR = cd;
-    T lnx = G.lnx[j], lny = G.lny[j];
-    if (cd >= 0) {
-      const int n = cd >> 2, jn = cd & 3;
-      if (!out[j]) {
-        sR = ((n - e0) << 2) | jn;
-      } else {
-        const int other = (((hslot[j] < HALO) ? (32 + hslot[j]) : (64 + n)) << 2) | jn;
-        if (e < n) {
-          sR = other;
-        } else {  // the neighbour has the lower index: it is the left side
-          sL = other;
-          sR = me;
-          lnx = -lnx;
-          lny = -lny;
-        }
-      }
-    }
-    put_desc(desc, eidx[j], sL, sR, lnx, lny);
-  }
-
-  // ---- element phase A: area integrals and rain, while the halo copies are in flight
-  T Rz[NP], Rx[NP], Ry[NP];
-  T Re = 0;
-  if (valid) {
-    // gridded rain: node indices now (coalesced), their nodal rates after the area integrals
-    const int4 nd = (rain_kind == 3) ? __ldg(a.nodes + e) : make_int4(0, 0, 0, 0);
-    Elem<P, Pol> E;
-    {
-      Raw<RV> r;
-#pragma unroll
-      for (int v = 0; v < RV; ++v) r.v[v] = own[v * TILE + lane];
-      unpack<P>(r, E);
-    }
-    // vertex coordinates: the first vertex, then along the edge vectors t_j = (-ln_j.y, ln_j.x)
-    T vx[3] = {0, 0, 0}, vy[3] = {0, 0, 0};
-    if (press || rain_kind == 2) {
-      const T* x0 = reinterpret_cast<const T*>(own + L::O_XY) + 2 * lane;
-      vx[0] = x0[0];
-      vy[0] = x0[1];
-      vx[1] = vx[0] - G.lny[0];
-      vy[1] = vy[0] + G.lnx[0];
-      vx[2] = vx[0] + G.lny[2];
-      vy[2] = vy[0] - G.lnx[2];
-    }
-    tile_area<P, Pol, FT>(E, G, S, a, press, vx, vy, Rz, Rx, Ry);
-    // forcing: element rain = mean of the three nodal rates (Eq. rain)
-    if (rain_kind == 1) {
-      Re = a.rain_e[e];
-    } else if (rain_kind == 2) {  // radial storm profile at the three vertices
-      const ForcingT<T>& F = forcing<T>(S);
-      const T tt = t - F.storm[7];
-      const T cx = F.storm[0] + F.storm[2] * tt, cy = F.storm[1] + F.storm[3] * tt;
-      const T rp = F.storm[4], rm = F.storm[5], re = F.storm[6];
-      T acc = 0;
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const T dx = vx[i] - cx, dy = vy[i] - cy;
-        const T r = fsqrt0(dx * dx + dy * dy);
-        if constexpr (sizeof(T) == 4)  // with 1 / rm and log2(e) / re formed once on the host
-          acc += (r < rm) ? rp * fmaf(0.5f * F.storm[8], r, 0.5f) : rp * mufu_ex2((rm - r) * F.storm[9]);
-        else
-          acc += (r < rm) ? rp * (T(0.5) + T(0.5) * fdiv(r, rm)) : rp * fexp(-fdiv(r - rm, re));
-      }
-      Re = acc * T(1.0 / 3.0);
-    } else if (rain_kind == 3) {  // gridded: nodal rates interpolated by the node kernel of this stage
-      Re = (a.rain_node[nd.x] + a.rain_node[nd.y] + a.rain_node[nd.z]) * T(1.0 / 3.0);
-    }
-  }
-  cp_async_wait_all();
-  __syncwarp();
-
-  // ---- edge phase: each edge touching the tile once, one per lane and round
-  for (int r = 0; r * 32 < nedge; ++r) {
-    const int i = r * 32 + lane;
-    if (i < nedge) tile_edge<P, FLUX, Pol, FT, COH>(a, S, own, halo, desc, flx, i, s_ephi, s_ephi4, t64, c.bdry);
-  }
-  fence_proxy_async();  // the slots' generic writes before the TMA batch that later refills the buffer
-  __syncwarp();
-
-  // ---- element phase B: lift, inverse mass, stage combination, positive-depth operator
-  if (valid) {
-    Elem<P, Pol> E;
-    {
-      Raw<RV> r;
-#pragma unroll
-      for (int v = 0; v < RV; ++v) r.v[v] = own[v * TILE + lane];
-      unpack<P>(r, E);
-    }
-    Acc massout;  // edge mass outflow (volume per second), summed exactly over the three sides
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      T vals[NV + 1];
-      load_side<T, NPR, NV>(flx, lane, j, vals);
-#pragma unroll
-      for (int k = 0; k < NG; ++k) {
-#pragma unroll
-        for (int m = 0; m < NP; ++m) {
-          const T ph_ = tab.ephi[j][k][m];
-          if (m > 0) Rz[m] = fma(-ph_, vals[k], Rz[m]);
-          Rx[m] = fma(-ph_, vals[NG + k], Rx[m]);
-          Ry[m] = fma(-ph_, vals[2 * NG + k], Ry[m]);
-        }
-      }
-      const T ms = side_mass<T, NG, L::MASSV>(vals);
-      massout = (j == 0) ? acc_make<Acc>(ms, T(0), ms) : acc_addr(massout, ms);
-    }
-    if (E.flags & FLAG_DRY) {  // the momentum equations are not advanced on dry elements
-#pragma unroll
-      for (int m = 0; m < NP; ++m) Rx[m] = Ry[m] = 0;
-    }
-    // Shu-Osher combination: out = a_n w^n + a_in w^in + beta dt M^{-1} R
-    const T idetJ = T(2) * acc_r(G.invA);
-    const Acc an = acc_make<Acc>(a.a_n_hi, a.a_n_lo, a.a_n);
-    const Acc ain = acc_make<Acc>(a.a_in_hi, a.a_in_lo, a.a_in);
-    const Acc bdt = acc_make<Acc>(S.bdt_hi[a.stage], S.bdt_lo[a.stage], S.bdt[a.stage]);
-    // mean rates: d(zeta_bar)/dt = R_e - massout / A;  d(q_bar)/dt = phi_0 R_0 / detJ
-    const Acc zrate = acc_addr(acc_neg(acc_mul(massout, G.invA)), Re);
-    const T xrate = tab.phi0 * Rx[0] * idetJ, yrate = tab.phi0 * Ry[0] * idetJ;
-    Elem<P, Pol> O = E;
-    Elem<P, Pol> Wn = E;
-    if (a.has_n) {
-      Raw<RV> rn;
-#pragma unroll
-      for (int v = 0; v < RV; ++v) rn.v[v] = ld_rec<COH>(a.wn + rec_at<RV>(e, v));
-      unpack<P>(rn, Wn);
-    }
-    const T an_r = (sizeof(T) == 4) ? (T)a.a_n_hi : (T)a.a_n, ain_r = (sizeof(T) == 4) ? (T)a.a_in_hi : (T)a.a_in;
-    {
-      Acc z, x, y;
-      constexpr int PW = ft_pow2(FT);
-      if (sizeof(T) == 4 && (PW == 1 || (PW == -1 && a.pow2))) {  // exact scaling of both words by a power of two
-        z = acc_scale2(E.zb, ain_r);
-        x = acc_scale2(E.xb, ain_r);
-        y = acc_scale2(E.yb, ain_r);
-        if (a.has_n) {
-          z = acc_addf(z, acc_scale2(Wn.zb, an_r));
-          x = acc_addf(x, acc_scale2(Wn.xb, an_r));
-          y = acc_addf(y, acc_scale2(Wn.yb, an_r));
-        }
-      } else {
-        z = acc_mul(ain, E.zb);
-        x = acc_mul(ain, E.xb);
-        y = acc_mul(ain, E.yb);
-        if (a.has_n) {
-          z = acc_add(z, acc_mul(an, Wn.zb));
-          x = acc_add(x, acc_mul(an, Wn.xb));
-          y = acc_add(y, acc_mul(an, Wn.yb));
-        }
-      }
-      O.zb = acc_addf(z, acc_mul(bdt, zrate));
-      O.xb = acc_addr(x, acc_r(bdt) * xrate);
-      O.yb = acc_addr(y, acc_r(bdt) * yrate);
-    }
-    const T bdt_r = acc_r(bdt);
-#pragma unroll
-    for (int m = 0; m < NS; ++m) {
-      T z = ain_r * E.zs[m] + bdt_r * (Rz[m + 1] * idetJ);
-      T x = ain_r * E.xs[m] + bdt_r * (Rx[m + 1] * idetJ);
-      T y = ain_r * E.ys[m] + bdt_r * (Ry[m + 1] * idetJ);
-      if (a.has_n) {
-        z = fma(an_r, Wn.zs[m], z);
-        x = fma(an_r, Wn.xs[m], x);
-        y = fma(an_r, Wn.ys[m], y);
-      }
-      O.zs[m] = z;
-      O.xs[m] = x;
-      O.ys[m] = y;
-    }
-    apply_positivity<P, Pol>(O, G, e, a, &a.ctl->err);
-    Raw<RV> ro;
-    pack<P>(O, ro);
-    store_raw<RV>(a.out, e, ro);
-    c.rain = acc_addf(c.rain, acc_mulr(G.A, Re));
-  }
-  __syncwarp();  // this tile's shared data is consumed: its buffers may be refilled
-}
-
-// One Runge-Kutta stage over all tiles: the warps of the grid take the tiles round-robin, each
-// tile's TMA batch issued one tile ahead into the warp's other buffer.
-template <int P, int FLUX, class Pol, int FT = FT_ALL>
-__global__ void DG_TILE_BOUNDS tile_kernel(const StageArgs<Pol> a) {
-  using T = typename Pol::T;
-  using Acc = typename Pol::Acc;
-  using L = TileLayout<P, Pol>;
-  constexpr int NP = np_of(P), NG = P + 1;
-  __shared__ T s_ephi[3][NG][NP];
-  __shared__ float4 s_ephi4[3];
-  extern __shared__ uint4 tsm[];
-  tile_tables<P, Pol>(s_ephi, s_ephi4);
-  const int tid = threadIdx.x;
   const int lane = tid & 31;
   uint4* Wm = tsm + (size_t)(tid >> 5) * L::VEC;
   uint4* halo = Wm + L::HAL;                                       // [HALO][RV]
@@ -1182,34 +859,293 @@ __global__ void DG_TILE_BOUNDS tile_kernel(const StageArgs<Pol> a) {
     mbar_fence_init();
   }
   __syncwarp();
+  const unsigned lt = (1u << lane) - 1u;
   const int gw = blockIdx.x * (blockDim.x >> 5) + (tid >> 5);
   const int W = gridDim.x * (blockDim.x >> 5);
+  // one TMA batch: the tile's records, geometry and neighbour codes into a buffer (lane 0)
+  auto issue = [&](int t, int b) {
+    if (lane == 0) {
+      uint4* buf = Wm + (b ? L::BUF1 : L::BUF0);
+      const uint32_t bar = b ? bar1 : bar0;
+      fence_proxy_async();
+      mbar_expect_tx(bar, L::TILE_BYTES);
+      bulk_g2s(smem_u32(buf), a.in + (size_t)t * TILE * RV, 16u * TILE * RV, bar);
+      bulk_g2s(smem_u32(buf + L::O_GEO), a.geo + (size_t)t * TILE * GV, 16u * TILE * GV, bar);
+      bulk_g2s(smem_u32(buf + L::O_NBR), a.nbr + (size_t)t * TILE, 16u * TILE, bar);
+      bulk_g2s(smem_u32(buf + L::O_XY), a.xy0 + (size_t)t * L::XV, 16u * L::XV, bar);
+      bulk_g2s(smem_u32(buf + L::O_META), a.tile_meta + t, 16u, bar);
+    }
+  };
   const double stepd = (double)a.ctl->step + a.cst;
-  TileCarry<Pol> c;
-  c.rain = acc_make<Acc>(0.f, 0.f, 0.0);
-  c.bdry = acc_make<Acc>(0.f, 0.f, 0.0);
-  c.cur = -1;
-  c.Sp = a.scen;  // constants of the current scenario, reloaded when a tile of another scenario comes
-  c.t64 = 0.0;
-  c.rain_kind = 0;
-  c.press = 0;
+  Acc rain_acc = acc_make<Acc>(0.f, 0.f, 0.0), bdry_acc = acc_make<Acc>(0.f, 0.f, 0.0);
+  int cur = -1;
+  // constants of the current scenario, reloaded when a tile of another scenario comes
+  const ScenDev* Sp = a.scen;
+  double t64 = 0.0;
+  int rain_kind = 0, press = 0;
   uint32_t ph = 0;  // parity of the next completion: bit 0 buffer 0, bit 1 buffer 1
-  if (gw < a.ntiles && lane == 0) tile_issue<P, Pol>(a, gw, Wm + L::BUF0, bar0);
+  if (gw < a.ntiles) issue(gw, 0);
 
   int it = 0;
   for (int tile = gw; tile < a.ntiles; tile += W, ++it) {
     const int b = it & 1;
-    // the other buffer's tile was consumed last iteration
-    if (tile + W < a.ntiles && lane == 0) tile_issue<P, Pol>(a, tile + W, Wm + (b ? L::BUF0 : L::BUF1), b ? bar0 : bar1);
+    if (tile + W < a.ntiles) issue(tile + W, b ^ 1);  // the other buffer's tile was consumed last iteration
     if (!__all_sync(0xffffffffu, mbar_wait(b ? bar1 : bar0, (ph >> b) & 1u))) {
       tile_timeout(a, b ? bar1 : bar0, (ph >> b) & 1u, lane);
       return;
     }
     ph ^= 1u << b;
-    tile_work<P, FLUX, Pol, FT, false>(a, tile, gw, lane, Wm + (b ? L::BUF1 : L::BUF0), halo, desc, s_ephi, s_ephi4,
-                                       stepd, c);
+    uint4* const buf = Wm + (b ? L::BUF1 : L::BUF0);
+    const uint4* own = buf;                           // [RV][32] records
+    const uint4* geoS = own + L::O_GEO;               // [32][GV]
+    void* flx = buf + L::O_FLX;                       // [3][NPR][32] pairs, over geoS .. meta
+    const int4* nbrS = reinterpret_cast<const int4*>(own + L::O_NBR);
+    const int4 meta = reinterpret_cast<const int4*>(own + L::O_META)[0];
+    const int sc = meta.x, present = meta.y;
+    if (present == 0) {  // padding tile: no element (uniform over the warp)
+      __syncwarp();
+      continue;
+    }
+    if (sc != cur) {
+      if (cur >= 0 && !a.tune) flush_ledger<P, Pol>(a, cur, gw, rain_acc, bdry_acc);
+      cur = sc;
+      Sp = a.scen + sc;
+      t64 = Sp->d.t0 + stepd * Sp->d.dt;  // stage time, formed in FP64
+      rain_kind = ft_rain(FT) >= 0 ? ft_rain(FT) : Sp->rain_kind;
+      press = (FT & FT_PRESS) ? Sp->press : 0;
+    }
+    const ScenDev& S = *Sp;
+    const int e0 = tile * TILE, e = e0 + lane;
+    const bool valid = lane < present;
+    const T t = (T)t64;
+    if (a.has_n && lane == 0) bulk_prefetch_l2(a.wn + (size_t)e0 * RV, 16u * TILE * RV);  // read in phase B
+
+    // ---- edge ownership: boundary edges, edges to out-of-tile neighbours, and in-tile edges to a
+    // higher index belong to this lane; out-of-tile neighbours get a halo slot.  Edge slots: the
+    // interior edges first, then the boundary edges (fewer divergent rounds).
+    const int4 nb = valid ? nbrS[lane] : make_int4(-1, -1, -1, -1);
+    const int code[3] = {nb.x, nb.y, nb.z};
+    bool own_e[3], out[3];
+    int eidx[3], hslot[3];
+    unsigned bi[3], bb[3];
+    int nint = 0, hbase = 0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int c = code[j];
+      const int n = c >> 2;
+      const bool inside = c >= 0 && n >= e0 && n < e0 + TILE;
+      own_e[j] = valid && (c < 0 || !inside || e < n);
+      out[j] = valid && c >= 0 && !inside;
+      bi[j] = __ballot_sync(0xffffffffu, own_e[j] && c >= 0);
+      bb[j] = __ballot_sync(0xffffffffu, own_e[j] && c < 0);
+      const unsigned bh = __ballot_sync(0xffffffffu, out[j]);
+      hslot[j] = hbase + __popc(bh & lt);
+      hbase += __popc(bh);
+      nint += __popc(bi[j]);
+    }
+    {
+      int ib = 0, bbase = nint;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        eidx[j] = code[j] >= 0 ? ib + __popc(bi[j] & lt) : bbase + __popc(bb[j] & lt);
+        ib += __popc(bi[j]);
+        bbase += __popc(bb[j]);
+      }
+    }
+    const int nedge = nint + __popc(bb[0]) + __popc(bb[1]) + __popc(bb[2]);
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      if (out[j] && hslot[j] < HALO) {
+#pragma unroll
+        for (int v = 0; v < RV; ++v) cp_async16(halo + v * HALO + hslot[j], a.in + rec_at<RV>(code[j] >> 2, v));
+      }
+    cp_async_commit();
+    Geo<Pol> G;
+    if (valid) geo_from(geoS + lane * GV, nb, G);
+    // edge descriptors {left side, right side or boundary code}
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      if (!own_e[j]) continue;
+      const int c = code[j];
+      const int me = (lane << 2) | j;
+      int sL = me, sR = c;
+      T lnx = G.lnx[j], lny = G.lny[j];
+      if (c >= 0) {
+        const int n = c >> 2, jn = c & 3;
+        if (!out[j]) {
+          sR = ((n - e0) << 2) | jn;
+        } else {
+          const int other = (((hslot[j] < HALO) ? (32 + hslot[j]) : (64 + n)) << 2) | jn;
+          if (e < n) {
+            sR = other;
+          } else {  // the neighbour has the lower index: it is the left side
+            sL = other;
+            sR = me;
+            lnx = -lnx;
+            lny = -lny;
+          }
+        }
+      }
+      put_desc(desc, eidx[j], sL, sR, lnx, lny);
+    }
+
+    // ---- element phase A: area integrals and rain, while the halo copies are in flight
+    T Rz[NP], Rx[NP], Ry[NP];
+    T Re = 0;
+    if (valid) {
+      // gridded rain: node indices now (coalesced), their nodal rates after the area integrals
+      const int4 nd = (rain_kind == 3) ? __ldg(a.nodes + e) : make_int4(0, 0, 0, 0);
+      Elem<P, Pol> E;
+      {
+        Raw<RV> r;
+#pragma unroll
+        for (int v = 0; v < RV; ++v) r.v[v] = own[v * TILE + lane];
+        unpack<P>(r, E);
+      }
+      // vertex coordinates: the first vertex, then along the edge vectors t_j = (-ln_j.y, ln_j.x)
+      T vx[3] = {0, 0, 0}, vy[3] = {0, 0, 0};
+      if (press || rain_kind == 2) {
+        const T* x0 = reinterpret_cast<const T*>(own + L::O_XY) + 2 * lane;
+        vx[0] = x0[0];
+        vy[0] = x0[1];
+        vx[1] = vx[0] - G.lny[0];
+        vy[1] = vy[0] + G.lnx[0];
+        vx[2] = vx[0] + G.lny[2];
+        vy[2] = vy[0] - G.lnx[2];
+      }
+      tile_area<P, Pol, FT>(E, G, S, a, press, vx, vy, Rz, Rx, Ry);
+      // forcing: element rain = mean of the three nodal rates (Eq. rain)
+      if (rain_kind == 1) {
+        Re = a.rain_e[e];
+      } else if (rain_kind == 2) {  // radial storm profile at the three vertices
+        const ForcingT<T>& F = forcing<T>(S);
+        const T tt = t - F.storm[7];
+        const T cx = F.storm[0] + F.storm[2] * tt, cy = F.storm[1] + F.storm[3] * tt;
+        const T rp = F.storm[4], rm = F.storm[5], re = F.storm[6];
+        T acc = 0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          const T dx = vx[i] - cx, dy = vy[i] - cy;
+          const T r = fsqrt0(dx * dx + dy * dy);
+          if constexpr (sizeof(T) == 4)  // with 1 / rm and log2(e) / re formed once on the host
+            acc += (r < rm) ? rp * fmaf(0.5f * F.storm[8], r, 0.5f) : rp * mufu_ex2((rm - r) * F.storm[9]);
+          else
+            acc += (r < rm) ? rp * (T(0.5) + T(0.5) * fdiv(r, rm)) : rp * fexp(-fdiv(r - rm, re));
+        }
+        Re = acc * T(1.0 / 3.0);
+      } else if (rain_kind == 3) {  // gridded: nodal rates interpolated by the node kernel of this stage
+        Re = (a.rain_node[nd.x] + a.rain_node[nd.y] + a.rain_node[nd.z]) * T(1.0 / 3.0);
+      }
+    }
+    cp_async_wait_all();
+    __syncwarp();
+
+    // ---- edge phase: each edge touching the tile once, one per lane and round
+    for (int r = 0; r * 32 < nedge; ++r) {
+      const int i = r * 32 + lane;
+      if (i < nedge) tile_edge<P, FLUX, Pol, FT>(a, S, own, halo, desc, flx, i, s_ephi, s_ephi4, t64, bdry_acc);
+    }
+    fence_proxy_async();  // the slots' generic writes before the TMA batch that later refills the buffer
+    __syncwarp();
+
+    // ---- element phase B: lift, inverse mass, stage combination, positive-depth operator
+    if (valid) {
+      Elem<P, Pol> E;
+      {
+        Raw<RV> r;
+#pragma unroll
+        for (int v = 0; v < RV; ++v) r.v[v] = own[v * TILE + lane];
+        unpack<P>(r, E);
+      }
+      Acc massout;  // edge mass outflow (volume per second), summed exactly over the three sides
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        T vals[NV + 1];
+        load_side<T, NPR, NV>(flx, lane, j, vals);
+#pragma unroll
+        for (int k = 0; k < NG; ++k) {
+#pragma unroll
+          for (int m = 0; m < NP; ++m) {
+            const T ph_ = tab.ephi[j][k][m];
+            if (m > 0) Rz[m] = fma(-ph_, vals[k], Rz[m]);
+            Rx[m] = fma(-ph_, vals[NG + k], Rx[m]);
+            Ry[m] = fma(-ph_, vals[2 * NG + k], Ry[m]);
+          }
+        }
+        const T ms = side_mass<T, NG, L::MASSV>(vals);
+        massout = (j == 0) ? acc_make<Acc>(ms, T(0), ms) : acc_addr(massout, ms);
+      }
+      if (E.flags & FLAG_DRY) {  // the momentum equations are not advanced on dry elements
+#pragma unroll
+        for (int m = 0; m < NP; ++m) Rx[m] = Ry[m] = 0;
+      }
+      // Shu-Osher combination: out = a_n w^n + a_in w^in + beta dt M^{-1} R
+      const T idetJ = T(2) * acc_r(G.invA);
+      const Acc an = acc_make<Acc>(a.a_n_hi, a.a_n_lo, a.a_n);
+      const Acc ain = acc_make<Acc>(a.a_in_hi, a.a_in_lo, a.a_in);
+      const Acc bdt = acc_make<Acc>(S.bdt_hi[a.stage], S.bdt_lo[a.stage], S.bdt[a.stage]);
+      // mean rates: d(zeta_bar)/dt = R_e - massout / A;  d(q_bar)/dt = phi_0 R_0 / detJ
+      const Acc zrate = acc_addr(acc_neg(acc_mul(massout, G.invA)), Re);
+      const T xrate = tab.phi0 * Rx[0] * idetJ, yrate = tab.phi0 * Ry[0] * idetJ;
+      Elem<P, Pol> O = E;
+      Elem<P, Pol> Wn = E;
+      if (a.has_n) {
+        Raw<RV> rn;
+#pragma unroll
+        for (int v = 0; v < RV; ++v) rn.v[v] = __ldg(a.wn + rec_at<RV>(e, v));
+        unpack<P>(rn, Wn);
+      }
+      const T an_r = (sizeof(T) == 4) ? (T)a.a_n_hi : (T)a.a_n, ain_r = (sizeof(T) == 4) ? (T)a.a_in_hi : (T)a.a_in;
+      {
+        Acc z, x, y;
+        constexpr int PW = ft_pow2(FT);
+        if (sizeof(T) == 4 && (PW == 1 || (PW == -1 && a.pow2))) {  // exact scaling of both words by a power of two
+          z = acc_scale2(E.zb, ain_r);
+          x = acc_scale2(E.xb, ain_r);
+          y = acc_scale2(E.yb, ain_r);
+          if (a.has_n) {
+            z = acc_addf(z, acc_scale2(Wn.zb, an_r));
+            x = acc_addf(x, acc_scale2(Wn.xb, an_r));
+            y = acc_addf(y, acc_scale2(Wn.yb, an_r));
+          }
+        } else {
+          z = acc_mul(ain, E.zb);
+          x = acc_mul(ain, E.xb);
+          y = acc_mul(ain, E.yb);
+          if (a.has_n) {
+            z = acc_add(z, acc_mul(an, Wn.zb));
+            x = acc_add(x, acc_mul(an, Wn.xb));
+            y = acc_add(y, acc_mul(an, Wn.yb));
+          }
+        }
+        O.zb = acc_addf(z, acc_mul(bdt, zrate));
+        O.xb = acc_addr(x, acc_r(bdt) * xrate);
+        O.yb = acc_addr(y, acc_r(bdt) * yrate);
+      }
+      const T bdt_r = acc_r(bdt);
+#pragma unroll
+      for (int m = 0; m < NS; ++m) {
+        T z = ain_r * E.zs[m] + bdt_r * (Rz[m + 1] * idetJ);
+        T x = ain_r * E.xs[m] + bdt_r * (Rx[m + 1] * idetJ);
+        T y = ain_r * E.ys[m] + bdt_r * (Ry[m + 1] * idetJ);
+        if (a.has_n) {
+          z = fma(an_r, Wn.zs[m], z);
+          x = fma(an_r, Wn.xs[m], x);
+          y = fma(an_r, Wn.ys[m], y);
+        }
+        O.zs[m] = z;
+        O.xs[m] = x;
+        O.ys[m] = y;
+      }
+      apply_positivity<P, Pol>(O, G, e, a, &a.ctl->err);
+      Raw<RV> ro;
+      pack<P>(O, ro);
+      store_raw<RV>(a.out, e, ro);
+      rain_acc = acc_addf(rain_acc, acc_mulr(G.A, Re));
+    }
+    __syncwarp();  // this tile's shared data is consumed: its buffers may be refilled
   }
-  if (c.cur >= 0 && !a.tune) flush_ledger<P, Pol>(a, c.cur, gw, c.rain, c.bdry);
+  if (cur >= 0 && !a.tune) flush_ledger<P, Pol>(a, cur, gw, rain_acc, bdry_acc);
 
   // launch epilogue: the last CTA to finish advances the step counter after the final stage
   if (a.last && !a.tune) {
@@ -1222,160 +1158,6 @@ __global__ void DG_TILE_BOUNDS tile_kernel(const StageArgs<Pol> a) {
         a.ctl->step += 1ull;
         __threadfence();
       }
-    }
-  }
-}
-
-// ------------------------------------------------------------------- the fused step -----
-// All Runge-Kutta stages of one step in one launch.  Stage k of a tile needs the stage k - 1
-// records of the tile and of its out-of-tile neighbours, so instead of a launch boundary between
-// stages each tile carries a completion counter: after a warp has stored a tile's stage k records
-// it publishes (release) epoch S + k + 1, where the epoch counts fused launches and S is the
-// number of stages; before a warp copies a tile in for stage k >= 1 it waits (acquire) until the
-// tile and every tile holding one of its out-of-tile neighbours show epoch S + k.  A stage k store
-// into a buffer that stage k - 1 read happens only after those readers (the tile's dependencies,
-// a symmetric relation) have finished, and stage 0 reads only the previous launch's output.
-// A warp takes its tiles in the same round-robin order in every stage and waits only for the
-// previous stage: the tiles of stage 0 never wait, and the wait for the first tile of a stage
-// comes after the warp has finished its last tile of the previous one, so every wait is for work
-// that can finish once all warps are resident -- which the cooperative launch guarantees.  Each
-// wait is bounded: one that runs out sets ERR_TIMEOUT and the warp stops after its current tile.
-
-__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-// order this thread's view of global memory (generic proxy) before its later bulk copies
-__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
-
-// wait until tile t and the tiles it depends on have published `need` (wrap-safe comparison);
-// lane i watches the i-th of at most 32 dependencies; false when a lane gave up after 2^22 polls
-template <class Pol>
-__device__ __forceinline__ bool deps_ready(const StepArgs<Pol>& sa, int t, unsigned need, int lane) {
-  const int b = __ldg(sa.dep_off + t), n = __ldg(sa.dep_off + t + 1) - b;
-  bool ok = true;
-  if (lane < n) {
-    const unsigned* f = sa.done + __ldg(sa.deps + b + lane);
-    for (int i = 0; (int)(ld_acquire_gpu(f) - need) < 0; ++i) {
-      if (i >= (1 << 22)) {
-        ok = false;
-        break;
-      }
-      if (i >= 4) __nanosleep(64);
-    }
-  }
-  ok = __all_sync(0xffffffffu, ok);
-  __syncwarp();  // the watching lanes' acquires before the warp's copies of the records
-  return ok;
-}
-
-template <int P, int FLUX, class Pol, int FT = FT_ALL>
-__global__ void DG_TILE_BOUNDS tile_step_kernel(const __grid_constant__ StepArgs<Pol> sa) {
-  using T = typename Pol::T;
-  using Acc = typename Pol::Acc;
-  using L = TileLayout<P, Pol>;
-  constexpr int NP = np_of(P), NG = P + 1;
-  __shared__ T s_ephi[3][NG][NP];
-  __shared__ float4 s_ephi4[3];
-  extern __shared__ uint4 tsm[];
-  tile_tables<P, Pol>(s_ephi, s_ephi4);
-  const int tid = threadIdx.x;
-  const int lane = tid & 31;
-  uint4* Wm = tsm + (size_t)(tid >> 5) * L::VEC;
-  uint4* halo = Wm + L::HAL;
-  EdgeDesc<T>* desc = reinterpret_cast<EdgeDesc<T>*>(Wm + L::DESC);
-  const uint32_t bar0 = smem_u32(Wm + L::BAR), bar1 = bar0 + 8;
-  if (lane == 0) {
-    mbar_init(bar0, 1);
-    mbar_init(bar1, 1);
-    mbar_fence_init();
-  }
-  __syncwarp();
-  const StageArgs<Pol>& a0 = sa.st[0];
-  const int gw = blockIdx.x * (blockDim.x >> 5) + (tid >> 5);
-  const int W = gridDim.x * (blockDim.x >> 5);
-  const int S = sa.nst, ntiles = a0.ntiles;
-  // every CTA reads both counters before the last one to finish advances them
-  const unsigned epoch = *reinterpret_cast<volatile const unsigned*>(&a0.ctl->epoch);
-  const unsigned base = epoch * (unsigned)S;
-  const double step0 = (double)a0.ctl->step;
-  TileCarry<Pol> c;
-  c.rain = acc_make<Acc>(0.f, 0.f, 0.0);
-  c.bdry = acc_make<Acc>(0.f, 0.f, 0.0);
-  c.cur = -1;
-  c.Sp = a0.scen;
-  c.t64 = 0.0;
-  c.rain_kind = 0;
-  c.press = 0;
-  uint32_t ph = 0;
-  int k = 0, tile = gw, b = 0;
-  if (tile < ntiles && lane == 0) tile_issue<P, Pol>(a0, tile, Wm + L::BUF0, bar0);  // stage 0: no wait
-  while (tile < ntiles) {
-    // the warp's next work: its next tile of this stage, else its first tile of the next stage
-    int nk = k, nt = tile + W;
-    if (nt >= ntiles) {
-      nk = k + 1;
-      nt = gw;
-    }
-    bool more = nk < S;
-    if (more && nk == k) {  // same stage: the next tile's copies fly while this tile is computed
-      if (k == 0 || deps_ready(sa, nt, base + (unsigned)nk, lane)) {
-        if (lane == 0) {
-          fence_proxy_async_global();
-          tile_issue<P, Pol>(sa.st[nk], nt, Wm + (b ? L::BUF0 : L::BUF1), b ? bar0 : bar1);
-        }
-      } else {
-        if (lane == 0) atomicOr(&a0.ctl->err, ERR_TIMEOUT);
-        more = false;
-      }
-    }
-    if (!__all_sync(0xffffffffu, mbar_wait(b ? bar1 : bar0, (ph >> b) & 1u))) {
-      tile_timeout(a0, b ? bar1 : bar0, (ph >> b) & 1u, lane);
-      return;
-    }
-    ph ^= 1u << b;
-    const StageArgs<Pol>& a = sa.st[k];
-    tile_work<P, FLUX, Pol, FT, true>(a, tile, gw, lane, Wm + (b ? L::BUF1 : L::BUF0), halo, desc, s_ephi, s_ephi4,
-                                      step0 + a.cst, c);
-    if (lane == 0) st_release_gpu(sa.done + tile, base + (unsigned)k + 1u);  // after the warp's stores (__syncwarp above)
-    if (nk != k) {  // this warp's share of stage k is done: book it, then wait for stage k's dependencies
-      if (c.cur >= 0 && !a.tune) flush_ledger<P, Pol>(a, c.cur, gw, c.rain, c.bdry);
-      c.cur = -1;
-      if (more) {
-        if (deps_ready(sa, nt, base + (unsigned)nk, lane)) {
-          if (lane == 0) {
-            fence_proxy_async_global();
-            tile_issue<P, Pol>(sa.st[nk], nt, Wm + (b ? L::BUF0 : L::BUF1), b ? bar0 : bar1);
-          }
-        } else {
-          if (lane == 0) atomicOr(&a0.ctl->err, ERR_TIMEOUT);
-          more = false;
-        }
-      }
-    }
-    if (!more) {
-      if (c.cur >= 0 && !a.tune) flush_ledger<P, Pol>(a, c.cur, gw, c.rain, c.bdry);
-      break;
-    }
-    k = nk;
-    tile = nt;
-    b ^= 1;
-  }
-
-  // launch epilogue: the last CTA to finish advances the launch epoch and the step counter
-  __syncthreads();
-  if (tid == 0) {
-    __threadfence();
-    const unsigned tk = atomicAdd(&a0.ctl->ticket, 1u);
-    if (tk == gridDim.x - 1) {
-      a0.ctl->ticket = 0;
-      a0.ctl->epoch = epoch + 1u;
-      if (!a0.tune) a0.ctl->step += 1ull;
-      __threadfence();
     }
   }
 }

@@ -1,13 +1,10 @@
-"""Parity of each launch form of the stage (fused, edge kernel + element kernel, tile, and the
-tile form's fused step) with the FP64 CPU oracle, through the C-ABI.
+"""Parity of each launch form of the stage (fused, edge kernel + element kernel, tile) with the
+FP64 CPU oracle, through the C-ABI.
 
 Same bars as the other parity tests: FP64 device path within 1e-11 of the oracle (relative to
 the larger of the variable's maximum magnitude and 1), mixed path within 1e-4 m in zeta and
-1e-4 m^2/s in q, relative mass balance within 1e-12.  Each case runs the oracle once and every
-form on the same seeded inputs and the oracle's dt.  The fused step (form 3: all stages of a
-step in one cooperative launch, mixed path, runs without gridded rain) does per tile exactly the
-arithmetic of the tile form, so with the same launch shape its state and ledger must equal the
-tile form's bit for bit.
+1e-4 m^2/s in q, relative mass balance within 1e-12.  Each case runs the oracle once and all
+three forms on the same seeded inputs and the oracle's dt.
 """
 import functools
 
@@ -22,10 +19,7 @@ pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-11
 MIXED_TOL = 1e-4
-FORMS = (0, 1, 2, 3)
-# cases whose run has gridded rain (the flume's rain stops through its gridded records): the node
-# kernel runs between stages, no fused step
-NO_STEP_FORM = {"gridded_rain_pressure", "hurricane_20k", "flume"}
+FORMS = (0, 1, 2)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -101,17 +95,15 @@ def _oracle(case):
 def test_every_form_matches_the_oracle(case, prec):
     w, dt, want, want_dry, rl = _oracle(case)
     _, steps, opt, check_dry = CASES[case]
-    states, ledgers = {}, {}
+    states = []
     for form in FORMS:
-        if form == 3 and (prec == D.FP64 or case in NO_STEP_FORM):
-            continue
         dev = D.from_workload(w, precision=prec, flux=opt.get("flux", O.ROE), ssp_stages=opt.get("ssp"), dt=dt,
                               block=128, waves=1, split=form)
         dev.step(steps)
         dev.sync()
         assert dev.launch() == (128, 1, form)
         got = dev.state()
-        states[form] = got
+        states.append(got)
         if prec == D.FP64:
             err = max(np.abs(got[:, v] - want[:, v]).max() / max(1.0, np.abs(want[:, v]).max()) for v in range(3))
             assert err <= FP64_TOL, (case, form, err)
@@ -122,7 +114,6 @@ def test_every_form_matches_the_oracle(case, prec):
             eq = np.abs(got[:, 1:] - want[:, 1:]).max()
             assert ez <= MIXED_TOL and eq <= MIXED_TOL, (case, form, ez, eq)
         led = dev.ledger()
-        ledgers[form] = led
         if case == "flume":  # initially dry: the balance is judged in absolute volume (m^3)
             assert abs(led["V"] - led["V0"] - led["rain_in"] - led["bdry_in"]) < 1e-12, (case, form, led)
         else:
@@ -134,42 +125,3 @@ def test_every_form_matches_the_oracle(case, prec):
             tol = 1e-9 if prec == D.FP64 else 1e-6
             assert abs(led["bdry_in"] - rl["bdry_in"]) <= tol * max(abs(rl["bdry_in"]), abs(rl["rain_in"])), (case, form)
         dev.close()
-    if 3 in states:  # the fused step: the tile form's arithmetic, scheduled differently
-        assert np.array_equal(states[3], states[2]), case
-        for key in ("V", "rain_in", "bdry_in", "t", "steps"):
-            assert ledgers[3][key] == ledgers[2][key], (case, key)
-
-
-@pytest.mark.parametrize("case", ["coastal_wet_dry", "basin_p2_ssp3", "ssp5_llf"])
-def test_fused_step_direct_launches_and_shapes(case):
-    """The fused step launched directly (no graph) and with other block sizes gives the tile
-    form's state for the same block size bit for bit."""
-    w, dt, want, _, _ = _oracle(case)
-    _, steps, opt, _ = CASES[case]
-    for block in (64, 256):
-        got = {}
-        for form, graphs in ((2, True), (3, False), (3, True)):
-            dev = D.from_workload(w, precision=D.MIXED, flux=opt.get("flux", O.ROE), ssp_stages=opt.get("ssp"),
-                                  dt=dt, block=block, waves=1, split=form)
-            dev.set_graphs(graphs)
-            l0 = dev.launch_count()
-            dev.step(steps)
-            dev.sync()
-            if form == 3:
-                assert dev.launch_count() - l0 == steps  # one launch per step, not one per stage
-            got[(form, graphs)] = dev.state()
-            assert dev.ledger()["rel_err"] < 1e-12
-            dev.close()
-        assert np.array_equal(got[(3, False)], got[(2, True)]), (case, block)
-        assert np.array_equal(got[(3, True)], got[(2, True)]), (case, block)
-
-
-def test_fused_step_is_refused_where_it_does_not_apply():
-    """Form 3 needs the mixed path, one wave and no node kernel between stages."""
-    w = W.basin_c1()
-    with pytest.raises(D.DgsweError):
-        D.from_workload(w, precision=D.FP64, block=128, waves=1, split=3)
-    with pytest.raises(D.DgsweError):
-        D.from_workload(w, precision=D.MIXED, block=128, waves=2, split=3)
-    with pytest.raises(D.DgsweError):
-        D.from_workload(_coastal_grid_press(), precision=D.MIXED, block=128, waves=1, split=3)

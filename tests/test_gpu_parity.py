@@ -369,16 +369,14 @@ def test_quadratic_friction_bathtub_short():
 @pytest.mark.parametrize("prec", [D.FP64, D.MIXED])
 def test_launch_shapes_give_identical_bits(prec):
     """Block size and waves do not change a single bit; the fused, split and tile forms agree to
-    rounding (the fused step, mixed path, one wave, equals the tile form)."""
+    rounding."""
     w = W.coastal_c2(n_tri=5000, seed=5, steps=30)
     both = []
-    for split in (0, 1, 2, 3) if prec == D.MIXED else (0, 1, 2):
+    for split in (0, 1, 2):
         outs = []
         for block, waves in ((64, 1), (128, 2), (256, 1), (256, 2)):
             if split == 2 and block == 256 and prec == D.FP64:
                 continue  # the FP64 tile form's shared memory does not fit 8 warps in one block
-            if split == 3 and waves == 2:
-                continue  # the fused step runs one wave
             dev = D.from_workload(w, precision=prec, block=block, waves=waves, split=split)
             dev.step(30)
             dev.sync()
@@ -448,8 +446,8 @@ def test_negative_mean_depth_is_reported_not_trapped():
 
 
 # --------------------------------------------------------------------------- ensemble ----
-@pytest.mark.parametrize("prec,split", [(D.FP64, 0), (D.FP64, 1), (D.FP64, 2), (D.MIXED, 0), (D.MIXED, 1),
-                                        (D.MIXED, 2), (D.MIXED, 3)])
+@pytest.mark.parametrize("prec", [D.FP64, D.MIXED])
+@pytest.mark.parametrize("split", [0, 1, 2])
 def test_ensemble_members_match_solo_runs(prec, split):
     """Batching does not change a bit: each member of an ensemble, run with the same kernels
     (launch shape fixed on both sides), ends bit-identical to its solo run."""
