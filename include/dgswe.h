@@ -185,6 +185,18 @@ int dgswe_set_state(dgswe_h, const double* zeta, const double* qx, const double*
  * staged through a device buffer and the call returns after the stream has consumed it. */
 int dgswe_load_state(dgswe_h, const double* zeta, const double* qx, const double* qy);
 
+/* The exchange of a coupling loop in one call: the current state goes out to (zeta_out, qx_out,
+ * qy_out) exactly as dgswe_get_state writes it, then (zeta_in, qx_in, qy_in) becomes the state
+ * exactly as dgswe_load_state takes it; all six arrays modal [Np][n_tri] in caller order, in and
+ * out not overlapping.  Equivalent to dgswe_get_state followed by dgswe_load_state, bit for bit
+ * (the problem statement's state in, state out, Sec. 2.1).  When all six are page-locked (pinned)
+ * host arrays one kernel reads each element record once, writes its old coefficients out and
+ * its new ones in, so both directions of the host link are in use at the same time; otherwise the
+ * two calls run in turn through their staged paths.  Returns after the stream has finished the
+ * exchange (the outputs are complete and the inputs may change). */
+int dgswe_exchange_state(dgswe_h, const double* zeta_in, const double* qx_in, const double* qy_in, double* zeta_out,
+                         double* qx_out, double* qy_out);
+
 /* Enqueues n_steps SSP-RK steps on the context's stream (CUDA graph replay) and returns
  * without waiting.  Device errors surface in dgswe_sync. */
 int dgswe_step(dgswe_h, int64_t n_steps);

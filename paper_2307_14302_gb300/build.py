@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 INC = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdgswe.so")
-SOURCES = ["stage_mixed.cu", "stage_fp64.cu", "tile_mixed.cu", "tile_spec.cu", "tile_fp64.cu", "api.cu", "noalloc.cu", "mesh.cpp",
+SOURCES = ["stage_mixed.cu", "stage_fp64.cu", "tile_mixed.cu", "tile_spec.cu", "tile_fp64.cu", "api.cu", "exchange.cu", "noalloc.cu", "mesh.cpp",
            "tables.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "args.h"
+#include "exchange.h"
 #include "dgswe.h"
 #include "host.h"
 #include "layout.h"
@@ -1272,6 +1273,21 @@ static int gather_state(dgswe_h h, size_t s, double* z, double* x, double* y, bo
   return 0;
 }
 
+// after records [b, b + n) received a state: their mean depths and wet/dry flags from it, the
+// state kept as given (positive-depth pass in classify mode)
+static cudaError_t classify_loaded(dgswe_h h, long long b, long long n) {
+  if (mixed(h)) {
+    StageArgs<Mixed> a = make_args<Mixed>(h, 0, 1);
+    a.in = a.out = h->rec[0].as<uint4>();
+    a.classify_only = 1;
+    return launch_prepare<Mixed>(h->prm.p, a, b, b + n, h->stream);
+  }
+  StageArgs<Fp64> a = make_args<Fp64>(h, 0, 1);
+  a.in = a.out = h->rec[0].as<uint4>();
+  a.classify_only = 1;
+  return launch_prepare<Fp64>(h->prm.p, a, b, b + n, h->stream);
+}
+
 int dgswe_get_state(dgswe_h h, double* z, double* x, double* y) {
   if (int rc = check_handle(h)) return rc;
   if (!h->ready) return fail(DGSWE_ESTATE, "no state");
@@ -1286,6 +1302,35 @@ int dgswe_get_state_device(dgswe_h h, double* z, double* x, double* y) {
   if (!z || !x || !y) return fail(DGSWE_EINVAL, "null output");
   if (h->ensemble) return fail(DGSWE_EINVAL, "use dgswe_ensemble_get_state");
   return gather_state(h, 0, z, x, y, true);
+}
+
+int dgswe_exchange_state(dgswe_h h, const double* zi, const double* xi, const double* yi, double* zo, double* xo,
+                         double* yo) {
+  if (int rc = check_handle(h)) return rc;
+  if (!h->ready) return fail(DGSWE_ESTATE, "set_state must precede exchange_state");
+  if (!zi || !xi || !yi || !zo || !xo || !yo) return fail(DGSWE_EINVAL, "null state array");
+  if (h->ensemble) return fail(DGSWE_EINVAL, "not available on an ensemble");
+  DeviceGuard dg_(h->device);
+  const void* m[6] = {host_mapped(zi), host_mapped(xi), host_mapped(yi), host_mapped(zo), host_mapped(xo), host_mapped(yo)};
+  bool direct = true;
+  for (const void* q : m) direct = direct && q != nullptr;
+  if (!direct) {  // some array is not page-locked: the state out, then in, through the staged paths
+    if (int rc = gather_state(h, 0, zo, xo, yo, false)) return rc;
+    if (int rc = dgswe_load_state(h, zi, xi, yi)) return rc;
+    CU(cudaStreamSynchronize(h->stream));
+    return 0;
+  }
+  const long long n = h->sc[0].m.ne, b = h->eoff[0];
+  const double *dzi = (const double*)m[0], *dxi = (const double*)m[1], *dyi = (const double*)m[2];
+  double *dzo = (double*)m[3], *dxo = (double*)m[4], *dyo = (double*)m[5];
+  const int32_t* inv = h->einv.as<int32_t>() + b;
+  cudaError_t ce = mixed(h) ? launch_exchange<Mixed>(h->prm.p, h->rec[0].as<uint4>(), b, n, inv, dzi, dxi, dyi, dzo, dxo, dyo, h->stream)
+                            : launch_exchange<Fp64>(h->prm.p, h->rec[0].as<uint4>(), b, n, inv, dzi, dxi, dyi, dzo, dxo, dyo, h->stream);
+  if (ce == cudaSuccess) ce = classify_loaded(h, b, n);
+  if (ce != cudaSuccess) return fail(DGSWE_ECUDA, "exchange_state launch: %s", cudaGetErrorString(ce));
+  h->launches += 2;
+  CU(cudaStreamSynchronize(h->stream));
+  return 0;
 }
 
 int dgswe_load_state(dgswe_h h, const double* z, const double* x, const double* y) {
@@ -1316,24 +1361,9 @@ int dgswe_load_state(dgswe_h h, const double* z, const double* x, const double* 
     sx = dz + cnt;
     sy = dz + 2 * cnt;
   }
-  cudaError_t ce;
-  if (mixed(h)) {
-    ce = launch_scatter<Mixed>(h->prm.p, h->rec[0].as<uint4>(), b, n, h->einv.as<int32_t>() + b, sz, sx, sy, h->stream);
-    if (ce == cudaSuccess) {
-      StageArgs<Mixed> a = make_args<Mixed>(h, 0, 1);
-      a.in = a.out = h->rec[0].as<uint4>();
-      a.classify_only = 1;
-      ce = launch_prepare<Mixed>(h->prm.p, a, b, b + n, h->stream);
-    }
-  } else {
-    ce = launch_scatter<Fp64>(h->prm.p, h->rec[0].as<uint4>(), b, n, h->einv.as<int32_t>() + b, sz, sx, sy, h->stream);
-    if (ce == cudaSuccess) {
-      StageArgs<Fp64> a = make_args<Fp64>(h, 0, 1);
-      a.in = a.out = h->rec[0].as<uint4>();
-      a.classify_only = 1;
-      ce = launch_prepare<Fp64>(h->prm.p, a, b, b + n, h->stream);
-    }
-  }
+  cudaError_t ce = mixed(h) ? launch_scatter<Mixed>(h->prm.p, h->rec[0].as<uint4>(), b, n, h->einv.as<int32_t>() + b, sz, sx, sy, h->stream)
+                            : launch_scatter<Fp64>(h->prm.p, h->rec[0].as<uint4>(), b, n, h->einv.as<int32_t>() + b, sz, sx, sy, h->stream);
+  if (ce == cudaSuccess) ce = classify_loaded(h, b, n);
   if (ce != cudaSuccess) return fail(DGSWE_ECUDA, "load_state launch: %s", cudaGetErrorString(ce));
   h->launches += 2;
   if (!direct) CU(cudaStreamSynchronize(h->stream));

@@ -59,7 +59,7 @@ class Ledger(C.Structure):
 EXPORTS = [
     "dgswe_create", "dgswe_set_params", "dgswe_set_mesh", "dgswe_set_fields", "dgswe_set_rain_nodal",
     "dgswe_set_rain_parametric", "dgswe_set_rain_grid", "dgswe_set_tide", "dgswe_set_river", "dgswe_set_pressure_setup",
-    "dgswe_set_state", "dgswe_load_state", "dgswe_step", "dgswe_sync", "dgswe_get_dt", "dgswe_get_state", "dgswe_get_state_device",
+    "dgswe_set_state", "dgswe_load_state", "dgswe_exchange_state", "dgswe_step", "dgswe_sync", "dgswe_get_dt", "dgswe_get_state", "dgswe_get_state_device",
     "dgswe_get_dry", "dgswe_get_ledger", "dgswe_volume", "dgswe_record_bytes", "dgswe_bind_device", "dgswe_volume_sum_noalloc", "dgswe_ensemble_create", "dgswe_ensemble_step",
     "dgswe_ensemble_get_state", "dgswe_ensemble_get_ledger", "dgswe_set_launch", "dgswe_get_launch", "dgswe_get_tile_features",
     "dgswe_set_graphs", "dgswe_launch_count", "dgswe_destroy", "dgswe_last_error",
@@ -96,6 +96,7 @@ def lib():
         "dgswe_set_pressure_setup": ([_h, C.POINTER(GaussSetup)], C.c_int),
         "dgswe_set_state": ([_h, _d, _d, _d, C.c_int32, C.c_double], C.c_int),
         "dgswe_load_state": ([_h, _d, _d, _d], C.c_int),
+        "dgswe_exchange_state": ([_h, _d, _d, _d, _d, _d, _d], C.c_int),
         "dgswe_step": ([_h, C.c_int64], C.c_int),
         "dgswe_sync": ([_h], C.c_int),
         "dgswe_get_dt": ([_h, _d], C.c_int),
@@ -217,6 +218,14 @@ class Solver:
     def load_state(self, z, x, y):
         """Modal arrays [Np][E] (caller order), e.g. from state_arrays()."""
         _check(lib().dgswe_load_state(self.h, _p(z), _p(x), _p(y)))
+
+    def exchange(self, zi, xi, yi, zo=None, xo=None, yo=None):
+        """The current modal state out (filled in place when given, e.g. pinned) and (zi, xi, yi)
+        in as the new state, in one call; returns the outputs."""
+        if zo is None:
+            zo, xo, yo = (np.empty((self.np_, self.ne)) for _ in range(3))
+        _check(lib().dgswe_exchange_state(self.h, _p(zi), _p(xi), _p(yi), _p(zo), _p(xo), _p(yo)))
+        return zo, xo, yo
 
     def step(self, n):
         _check(lib().dgswe_step(self.h, int(n)))

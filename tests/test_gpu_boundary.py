@@ -87,3 +87,54 @@ def test_pinned_state_exchange_matches_the_staged_path(prec):
     assert np.array_equal(a.state(), b.state())
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("prec", [D.FP64, D.MIXED])
+@pytest.mark.parametrize("pinned", [True, False])
+def test_exchange_equals_get_then_load(prec, pinned):
+    """dgswe_exchange_state (state out, new state in, one call) gives the arrays dgswe_get_state
+    gives and leaves the state dgswe_load_state leaves, bit for bit; the following steps agree
+    bit for bit too.  Page-locked arrays take the one-pass kernel, pageable ones the two staged
+    calls."""
+    import torch
+
+    w = W.coastal_c2(n_tri=5000, seed=7, steps=20)
+    a = D.from_workload(w, precision=prec, block=128, split=2)
+    b = D.from_workload(w, precision=prec, dt=a.dt(), block=128, split=2)
+    a.step(6)
+    b.step(6)
+    c = D.from_workload(w, precision=prec, dt=a.dt(), block=128, split=2)
+    c.step(3)
+    new = c.state_arrays()  # another valid state of the same mesh
+    c.close()
+
+    def arrays(src=None):
+        shape = new[0].shape
+        if pinned:
+            out = [torch.empty(shape, dtype=torch.float64).pin_memory().numpy() for _ in range(3)]
+        else:
+            out = [np.empty(shape) for _ in range(3)]
+        if src is not None:
+            for o, s_ in zip(out, src):
+                o[...] = s_
+        return out
+
+    zi, xi, yi = arrays(new)
+    zo, xo, yo = arrays()
+    a.exchange(zi, xi, yi, zo, xo, yo)
+    want = b.state_arrays()
+    b.load_state(*new)
+    for got, ref in zip((zo, xo, yo), want):
+        assert np.array_equal(got, ref)
+    assert np.array_equal(a.state(), b.state())
+    assert np.array_equal(a.dry(), b.dry())
+    for s in (a, b):
+        s.step(5)
+        s.sync()
+    assert np.array_equal(a.state(), b.state())
+    # a second exchange hands back what the first put in, advanced by the five steps
+    zo2, xo2, yo2 = arrays()
+    a.exchange(zi, xi, yi, zo2, xo2, yo2)
+    assert np.array_equal(np.stack([zo2.T, xo2.T, yo2.T], axis=1), b.state())
+    a.close()
+    b.close()
