@@ -99,3 +99,26 @@ def test_dry_element_keeps_its_water_against_a_low_tide():
     o2 = run(2 * H0)
     assert list(o2.dry()) == [0, 0]
     assert o2.rhs()[0, 0, 0] < -1e-6
+
+
+def test_rain_on_a_dry_flat_floodplain_wets_it_at_the_threshold():
+    """A flat floodplain 2 m above the datum under a 5 mm film (below H0, every element dry) and
+    uniform rain R, walls all round: rain falls on dry elements too (Sec. 2.3), nothing moves, so
+    the depth is 5 mm + R t exactly, the elements stay dry while it is below H0 and are all wet
+    once it is above, and the mass ledger balances."""
+    mesh = W.structured_mesh(4000.0, 2000.0, 10, 5)
+    hb = np.full(mesh.n_nodes, -2.0)
+    R, film, dt = 1.0e-5, 0.005, 10.0  # the film reaches H0 at t = 500 s
+    o = O.Oracle(mesh, hb, np.full(mesh.n_tri, 0.03), p=1, h0=H0)
+    o.set_rain_nodal(np.full(mesh.n_nodes, R))
+    o.set_state_nodal(np.full(mesh.n_nodes, film + 2.0))
+    o.set_dt(dt)
+    for n, wet in ((49, False), (2, True)):  # t = 490 s, then 510 s
+        o.step(n)
+        t = o.ledger()["t"]
+        s = o.state()
+        H = s[:, 0, 0] / math.sqrt(2) - 2.0
+        assert np.abs(H - (film + R * t)).max() <= 1e-13, t
+        assert np.abs(s[:, 0, 1:]).max() <= 1e-13 and np.abs(s[:, 1:]).max() <= 1e-12  # flat, at rest
+        assert (o.dry() == (0 if wet else 1)).all(), t
+        assert o.ledger()["rel_err"] < 1e-12
