@@ -117,13 +117,15 @@ typedef struct {
   double V0, V, rain_in, bdry_in, VH0, rel_err, wet_frac;
 } dgswe_ledger;
 
-/* Creates a context on CUDA device `device`; `cuda_stream` is a cudaStream_t on which all device
+/* No counterpart in the paper (lifetime).  Creates a context on CUDA device `device`;
+ * `cuda_stream` is a cudaStream_t on which all device
  * work of this context is enqueued (NULL: the library creates a private non-blocking stream).
  * *out receives the handle.  Errors: EINVAL (null out), ENOLIB (no device, or a device other
  * than sm_103a), ECUDA. */
 int dgswe_create(dgswe_h* out, int device, void* cuda_stream);
 
-/* Sets the run parameters (copied).  EINVAL on values outside the ranges above. */
+/* Sets the run parameters of the method (Sec. 2.2-2.4, fields listed above; copied).  EINVAL on
+ * values outside the ranges above. */
 int dgswe_set_params(dgswe_h, const dgswe_params* params);
 
 /* Sets the triangulation (Sec. 2.1, ADCIRC-style arrays).
@@ -136,21 +138,25 @@ int dgswe_set_params(dgswe_h, const dgswe_params* params);
 int dgswe_set_mesh(dgswe_h, int32_t n_nodes, const double* xy, int32_t n_tri, const int32_t* tri, int32_t n_bedge,
                    const int32_t* bedge, const int32_t* btype, const int32_t* bseg);
 
-/* Sets nodal bathymetry hb [n_nodes] (positive downward, m; continuous piecewise linear) and
- * Manning n, per element [n_tri] (manning_nodal = 0) or per node [n_nodes] (element value = mean
- * of its nodes).  manning may be NULL when friction is not Manning. */
+/* Sets nodal bathymetry hb [n_nodes] (the h_b of Eq. SWE: positive downward, m; continuous
+ * piecewise linear) and Manning n (the bottom friction tau_b of Eq. SWE), per element [n_tri]
+ * (manning_nodal = 0) or per node [n_nodes] (element value = mean of its nodes).  manning may be
+ * NULL when friction is not Manning. */
 int dgswe_set_fields(dgswe_h, const double* hb_nodal, const double* manning, int32_t manning_nodal);
 
 /* Rain sources (Sec. 2.3, Eq. rain): the element rate is the mean of its three nodal rates and
  * is added to every element, wet or dry.  Each setter replaces the previous rain source. */
 int dgswe_set_rain_nodal(dgswe_h, const double* r_nodal); /* constant in time [n_nodes] m/s */
+/* The moving rain cell of dgswe_storm (the parametric rainfall of Sec. 2.5), copied. */
 int dgswe_set_rain_parametric(dgswe_h, const dgswe_storm* storm);
 /* Gridded records [nt][ny][nx] float32 in mm/h on x0 + i dx, y0 + j dy, times t0 + k dt_rec:
  * bilinear in space, linear in time, clamped at the grid and record ends (Sec. 2.5). */
 int dgswe_set_rain_grid(dgswe_h, int32_t nx, int32_t ny, int32_t nt, double x0, double y0, double dx, double dy,
                         double t0, double dt_rec, const float* mm_per_h);
 
-/* Tidal elevation on ocean edges of segment s: amp[s] sin(2 pi t / period[s] + phase[s]). */
+/* Tidal elevation on ocean edges of segment s (the specified-elevation boundary of Sec. 2.1):
+ * amp[s] sin(2 pi t / period[s] + phase[s]); the ghost state takes it with the interior
+ * discharge.  Copied; n_seg in [1, 8]. */
 int dgswe_set_tide(dgswe_h, int32_t n_seg, const double* amp, const double* period, const double* phase);
 
 /* River (specified normal flow) boundaries, Sec. 2.1 Eq. river_bc: edges of type
@@ -167,7 +173,8 @@ int dgswe_set_river(dgswe_h, int32_t n_seg, int32_t n_t, double t0, double dt_re
 /* Gaussian pressure set-up forcing (F_x, F_y of Eq. SWE); NULL removes it. */
 int dgswe_set_pressure_setup(dgswe_h, const dgswe_gauss_setup* setup);
 
-/* Sets the state at t = t0.  layout MODAL: zeta, qx, qy are [Np][n_tri] modal coefficients;
+/* Sets the state (zeta, q) of Eq. SWE at t = t0 (the initial condition of the problem of
+ * Sec. 2.1).  layout MODAL: zeta, qx, qy are [Np][n_tri] modal coefficients;
  * NODAL: [n_nodes] nodal values, interpolated linearly on each element.  The positive-depth
  * operator is applied once (it defines the wet/dry flags), the ledger is reset (V0, VH0) and,
  * when params.dt <= 0, dt is fixed from the CFL condition. */
@@ -197,31 +204,38 @@ int dgswe_load_state(dgswe_h, const double* zeta, const double* qx, const double
 int dgswe_exchange_state(dgswe_h, const double* zeta_in, const double* qx_in, const double* qy_in, double* zeta_out,
                          double* qx_out, double* qy_out);
 
-/* Enqueues n_steps SSP-RK steps on the context's stream (CUDA graph replay) and returns
- * without waiting.  Device errors surface in dgswe_sync. */
+/* Enqueues n_steps steps of the SSP Runge-Kutta scheme (Eq. RKSSP; each stage the DG right-hand
+ * side of Eq. elem_weak_form and the positive-depth operator of Sec. 2.4) on the context's stream
+ * (CUDA graph replay) and returns without waiting.  Device errors surface in dgswe_sync. */
 int dgswe_step(dgswe_h, int64_t n_steps);
 
-/* Waits for the stream and returns the first device error word (ENONFINITE, ENEGDEPTH) or 0. */
+/* No counterpart in the paper (stream plumbing): waits for the stream and returns the first
+ * device error word (ENONFINITE, ENEGDEPTH, ETIMEOUT) or 0. */
 int dgswe_sync(dgswe_h);
 
-/* The fixed time step [s] in *dt. */
+/* The fixed time step [s] in *dt (the runs of Sec. 3 use a fixed dt; here from the CFL
+ * condition of dgswe_params unless given). */
 int dgswe_get_dt(dgswe_h, double* dt);
 
-/* Copies the modal state to host arrays [Np][n_tri] (synchronises the stream).  Page-locked
+/* Copies the modal state (zeta, q) of Eq. SWE, in the basis of Eq. dubiner, to host arrays
+ * [Np][n_tri] (synchronises the stream).  Page-locked
  * (pinned) arrays are written by the unpacking kernel itself over the host link; other host
  * memory is staged through a device buffer. */
 int dgswe_get_state(dgswe_h, double* zeta, double* qx, double* qy);
 
-/* Copies the modal state into caller-owned device memory: each pointer to Np*n_tri doubles,
- * written on the context's stream (no host round trip). */
+/* Copies the modal state (as dgswe_get_state: (zeta, q) of Eq. SWE, basis of Eq. dubiner) into
+ * caller-owned device memory: each pointer to
+ * Np*n_tri doubles, written on the context's stream (no host round trip). */
 int dgswe_get_state_device(dgswe_h, double* zeta_dev, double* qx_dev, double* qy_dev);
 
-/* Device memory that the element records need (the state w^n and the two Runge-Kutta stage
+/* No counterpart in the paper (memory plumbing).  Device memory that the element records need
+ * (the state w^n and the two Runge-Kutta stage
  * buffers, each rounded up to 256 bytes), in *bytes.  Valid after dgswe_set_state or
  * dgswe_ensemble_create. */
 int dgswe_record_bytes(dgswe_h, uint64_t* bytes);
 
-/* Places the element records in caller-owned device memory (for example a framework's tensor
+/* No counterpart in the paper (memory plumbing).  Places the element records in caller-owned
+ * device memory (for example a framework's tensor
  * storage), so that the caller's allocator provides the solver's largest arrays: dev must be
  * device memory of the context's device, 256-byte aligned, at least dgswe_record_bytes long.  The
  * current state is copied there and every later step reads and writes it in place; the library
@@ -235,10 +249,12 @@ int dgswe_bind_device(dgswe_h, void* dev, uint64_t bytes);
 /* Per-element dry flags (Sec. 2.4) [n_tri] as 0/1 bytes. */
 int dgswe_get_dry(dgswe_h, uint8_t* dry);
 
-/* Mass ledger (synchronises the stream). */
+/* Mass ledger of dgswe_ledger: Eq. SWE's mass equation integrated over the domain and the
+ * steps, water volume against rain and boundary inflow (synchronises the stream). */
 int dgswe_get_ledger(dgswe_h, dgswe_ledger* out);
 
-/* Total water volume sum_e A_e mean(zeta_e) of the current state, reduced on the device in
+/* Total water volume sum_e A_e mean(zeta_e) of the current state (the V of the mass balance of
+ * Eq. SWE, above the datum), reduced on the device in
  * FP64 with Neumaier compensation over per-block partial sums held in library-allocated scratch
  * memory; *out receives the value (synchronises the stream). */
 int dgswe_volume(dgswe_h, double* out);
@@ -261,17 +277,24 @@ int dgswe_volume(dgswe_h, double* out);
 int dgswe_volume_sum_noalloc(const double* w0_dev, const double* area_dev, int64_t n, double* out_dev,
                              void* cuda_stream);
 
-/* Ensemble of independent scenarios (different meshes, forcing, Manning fields) advanced
- * together: one persistent launch per RK stage, the whole step captured in a CUDA graph.  The
- * members must share p, flux, ssp_stages, precision, g and H0 and have their state set; their
- * data is copied (members keep ownership and are not modified).  Each scenario keeps its own
- * dt and time. */
+/* No counterpart in the paper (the paper runs one scenario at a time): an ensemble of
+ * independent scenarios (different meshes, forcing, Manning fields), each the problem of
+ * Sec. 2.1 advanced by the method of dgswe_step, advanced together: one persistent launch per RK
+ * stage over all scenarios' tiles, the whole step captured in a CUDA graph.  The members must
+ * share p, flux, ssp_stages, precision, g and H0 and have their state set; their data is copied
+ * (members keep ownership and are not modified).  Each scenario keeps its own dt and time. */
 int dgswe_ensemble_create(dgswe_h* out, int32_t n, const dgswe_h* members, int device, void* cuda_stream);
+/* n_steps SSP Runge-Kutta steps (Eq. RKSSP) of every scenario, enqueued (as dgswe_step). */
 int dgswe_ensemble_step(dgswe_h ens, int64_t n_steps);
+/* Scenario `member` (0-based, creation order): its modal state (as dgswe_get_state: (zeta, q) of
+ * Eq. SWE); synchronises the stream.  EINVAL for a bad index. */
 int dgswe_ensemble_get_state(dgswe_h ens, int32_t member, double* zeta, double* qx, double* qy);
+/* Scenario `member`'s own mass ledger (as dgswe_get_ledger: the mass balance of Eq. SWE);
+ * synchronises the stream.  EINVAL for a bad index. */
 int dgswe_ensemble_get_ledger(dgswe_h ens, int32_t member, dgswe_ledger* out);
 
-/* Launch shape of a stage: block size of the element kernel (64, 128, 256, or 0 = autotune on
+/* No counterpart in the paper (device scheduling).  Launch shape of a stage: block size of the
+ * element kernel (64, 128, 256, or 0 = autotune on
  * the next step), waves (1 or 2: the grid holds waves x CTAs resident per SM x SMs CTAs whose
  * warps take the 32-element tiles round-robin), and the form, argument split: 0 one fused kernel
  * in which both neighbours evaluate an interior edge; 1 a separate edge kernel computes every
@@ -280,9 +303,12 @@ int dgswe_ensemble_get_ledger(dgswe_h ens, int32_t member, dgswe_ledger* out);
  * memory.  The three forms agree to rounding; for a fixed form results do not depend on block or
  * waves.  Returns DGSWE_EINVAL for other values. */
 int dgswe_set_launch(dgswe_h, int32_t block, int32_t waves, int32_t split);
+/* No counterpart in the paper (device scheduling): the launch shape in use (after autotuning,
+ * the one it chose); NULL pointers are skipped. */
 int dgswe_get_launch(dgswe_h, int32_t* block, int32_t* waves, int32_t* split);
 
-/* Feature sets (diagnostics and tests).  *run: the features of this run as a bit set (1 river
+/* No counterpart in the paper (diagnostics and tests).  Feature sets: *run, the features of this
+ * run as a bit set (1 river
  * boundary edges, 2 tidal boundary edges, 4 pressure set-up, 8 nodal rain, 16 storm rain,
  * 32 gridded rain, 64 Manning friction, 128 quadratic friction, 256 no friction, 512 stages whose
  * Shu-Osher weights are powers of two, 1024 other stage weights, 2048 a scenario without rain).
@@ -291,19 +317,23 @@ int dgswe_get_launch(dgswe_h, int32_t* block, int32_t* waves, int32_t* split);
  * Either pointer may be NULL.  DGSWE_ESTATE before the state is set. */
 int dgswe_get_tile_features(dgswe_h, int32_t* run, int32_t* kernel);
 
-/* How dgswe_step enqueues its work: 1 (default) replays whole steps from CUDA graphs captured
+/* No counterpart in the paper (device scheduling).  How dgswe_step enqueues its work: 1
+ * (default) replays whole steps from CUDA graphs captured
  * once (1-step and 8-step graphs); 0 launches every kernel of every stage directly on the
  * stream.  Results are bit-identical; the direct form exists to measure what the graphs save
  * on small, launch-bound meshes.  Returns DGSWE_EINVAL for other values. */
 int dgswe_set_graphs(dgswe_h, int32_t on);
 
-/* Number of kernel launches this context enqueued so far (all kinds). */
+/* No counterpart in the paper (diagnostics): number of kernel launches this context enqueued so
+ * far (all kinds). */
 int64_t dgswe_launch_count(dgswe_h);
 
-/* Releases the context and its device memory (NULL is ignored). */
+/* No counterpart in the paper (lifetime): releases the context and its device memory (NULL is
+ * ignored). */
 void dgswe_destroy(dgswe_h);
 
-/* Message of the last error on the calling thread ("" if none). */
+/* No counterpart in the paper (error reporting): message of the last error on the calling
+ * thread ("" if none). */
 const char* dgswe_last_error(void);
 
 #ifdef __cplusplus
