@@ -60,3 +60,15 @@ def test_binding_fails_loudly_when_library_missing(monkeypatch, tmp_path):
     monkeypatch.setattr(D, "_lib", None)
     with pytest.raises(D.DgsweUnavailable):
         D.lib()
+
+
+def test_every_declaration_names_its_passage():
+    """Each entry point's own comment names the passage of the paper that defines what it does
+    (a section or equation), or says that the paper has no counterpart."""
+    src = open(os.path.join(ROOT, "include", "dgswe.h")).read()
+    documented = {}
+    for m in re.finditer(r"(/\*(?:.|\n)*?\*/)\s*(?:int|void|int64_t|const\s+char\s*\*)\s+(dgswe_\w+)\s*\(", src):
+        documented[m.group(2)] = m.group(1)
+    assert set(documented) == _declared()
+    for name, comment in documented.items():
+        assert re.search(r"Sec\. \d|Eq\. \w|no counterpart in the paper|paper has no counterpart", comment, re.I), name
