@@ -108,6 +108,8 @@ struct orc {
   double V0, VH0, rain_s, rain_c, bd_s, bd_c, stage_bdry;
 };
 
+/* Neumaier-compensated addition of v to the pair (sum s, compensation c): the mass ledger's sums
+ * (the volume balance of Eq. SWE over the domain) kept free of cancellation */
 static void neu_add(double* s, double* c, double v) {
   double t = *s + v;
   if (fabs(*s) >= fabs(v))
@@ -121,7 +123,8 @@ static void neu_add(double* s, double* c, double v) {
 /* phi_ij = sqrt((2i+1)(i+j+1)/2) * P_i(a) ((1-b)/2)^i * P_j^{(2i+1,0)}(b) on the reference triangle
  * (-1,-1),(1,-1),(-1,1) with collapsed coordinates a = 2(1+r)/(1-s) - 1, b = s.  The factor
  * P_i(a) ((1-s)/2)^i is evaluated as a polynomial in (r,s) by the Legendre recurrence written in
- * homogeneous form, so the vertex s = 1 needs no special case.  Ordering: total degree, then j. */
+ * homogeneous form, so the vertex s = 1 needs no special case.  Ordering: total degree, then j
+ * (the paper fixes no ordering of the modes of Eq. dubiner). */
 static void legendre_hom(int n, double r, double s, double* Q, double* Qr, double* Qs) {
   double A = r + 0.5 * (1.0 + s), u = 0.5 * (1.0 - s);
   Q[0] = 1.0; Qr[0] = 0.0; Qs[0] = 0.0;
@@ -133,6 +136,8 @@ static void legendre_hom(int n, double r, double s, double* Q, double* Qr, doubl
   }
 }
 
+/* Jacobi polynomials P_k^(al,0)(x), k = 0..n, and their derivatives by the three-term recurrence:
+ * the factor in s of the Dubiner basis (Eq. dubiner) */
 static void jacobi_a0(int n, double al, double x, double* P, double* dP) {
   P[0] = 1.0; dP[0] = 0.0;
   if (n >= 1) { P[1] = 0.5 * ((al + 2.0) * x + al); dP[1] = 0.5 * (al + 2.0); }
@@ -146,6 +151,7 @@ static void jacobi_a0(int n, double al, double x, double* P, double* dP) {
   }
 }
 
+/* The orthonormal Dubiner basis of Eq. dubiner at (r, s) and its derivatives in r and s */
 void orc_basis(int p, double r, double s, double* phi, double* dr, double* ds) {
   double Q[NGMAX + 1], Qr[NGMAX + 1], Qs[NGMAX + 1];
   legendre_hom(p, r, s, Q, Qr, Qs);
@@ -164,12 +170,14 @@ void orc_basis(int p, double r, double s, double* phi, double* dr, double* ds) {
 }
 
 /* ------------------------------------------------------------------------- quadrature --- */
+/* barycentric coordinates -> (r, s) on the reference triangle (-1,-1), (1,-1), (-1,1) of Eq. dubiner */
 static void bary_to_rs(const double l[3], double* r, double* s) {
   *r = -l[0] + l[1] - l[2];
   *s = -l[0] - l[1] + l[2];
 }
 
-/* Symmetric area rules, weights summing to the reference area 2:
+/* Symmetric area rules for the element integrals of Eq. elem_weak_form (the paper names no rule), weights
+ * summing to the reference area 2:
  *  p=0: centroid (degree 1);
  *  p=1: centroid 27/60, edge midpoints 8/60, vertices 3/60 (degree 3, Stroud);
  *  p=2: centroid 9/40, orbits (a,a,1-2a) with a = (6 -/+ sqrt 15)/21 and weights
@@ -196,6 +204,7 @@ static int area_rule_bary(int p, double l[NQMAX][3], double* w) {
   return n;
 }
 
+/* the area rule of the element integrals of Eq. elem_weak_form in (r, s) (test hook) */
 int orc_area_rule(int p, double* r, double* s, double* w) {
   double l[NQMAX][3];
   int n = area_rule_bary(p, l, w);
@@ -203,7 +212,7 @@ int orc_area_rule(int p, double* r, double* s, double* w) {
   return n;
 }
 
-/* Gauss-Legendre on [-1,1] with p+1 points. */
+/* Gauss-Legendre on [-1,1] with p+1 points: the edge integrals of Sec. 2.3 (the paper names no rule). */
 int orc_edge_rule(int p, double* xi, double* w) {
   if (p <= 0) { xi[0] = 0.0; w[0] = 2.0; return 1; }
   if (p == 1) { double a = 1.0 / sqrt(3.0); xi[0] = -a; xi[1] = a; w[0] = w[1] = 1.0; return 2; }
@@ -213,6 +222,9 @@ int orc_edge_rule(int p, double* xi, double* w) {
 }
 
 /* --------------------------------------------------------------------------- setup --- */
+/* A solver of the method of Sec. 2.2-2.4 with degree p (Eq. dubiner), the Roe or LLF flux
+ * (Sec. 2.3), the Shu-Osher SSP scheme of Eq. RKSSP with ssp_stages stages, gravity g, the
+ * thin-layer threshold H0 (Sec. 2.4) and the friction law of Eq. SWE's tau_b (Manning, or the quadratic law of Sec. 3.1) */
 orc_t* orc_create(int p, int flux, int ssp_stages, double g, double H0, int friction, double cf) {
   if (p < 0 || p > 2 || ssp_stages < 1 || ssp_stages > 5 || ssp_stages == 4) return NULL;
   orc_t* o = (orc_t*)calloc(1, sizeof(orc_t));
@@ -272,8 +284,10 @@ orc_t* orc_create(int p, int flux, int ssp_stages, double g, double H0, int fric
   return o;
 }
 
+/* memory release helper (no counterpart in the paper) */
 static void freep(void* p) { free(p); }
 
+/* releases the solver (no counterpart in the paper) */
 void orc_destroy(orc_t* o) {
   if (!o) return;
   void* ptrs[] = {o->x, o->y, o->tri, o->edn, o->ede, o->edj, o->edt, o->eds, o->order, o->det, o->rx, o->ry,
@@ -286,6 +300,8 @@ void orc_destroy(orc_t* o) {
 
 typedef struct { int64_t key; int e, j; } halfedge;
 
+/* order of half edges by node pair, then element and local edge: pairs the two sides of each
+ * interior edge of the triangulation (Sec. 2.1) */
 static int cmp_he(const void* a, const void* b) {
   const halfedge *x = (const halfedge*)a, *y = (const halfedge*)b;
   if (x->key != y->key) return x->key < y->key ? -1 : 1;
@@ -293,11 +309,15 @@ static int cmp_he(const void* a, const void* b) {
   return x->j - y->j;
 }
 
+/* key of an undirected node pair (mesh connectivity, Sec. 2.1) */
 static int64_t pair_key(int a, int b, int nn) {
   int lo = a < b ? a : b, hi = a < b ? b : a;
   return (int64_t)lo * nn + hi;
 }
 
+/* The triangulation of the domain and its boundary parts (Sec. 2.1: ocean, land, river edges;
+ * internal river edges of Sec. 2.3): element geometry, edges with both sides, edge order of
+ * Sec. 2.3 (boundary edges before inner edges) */
 int orc_set_mesh(orc_t* o, int nn, const double* xy, int ne, const int32_t* tri, int nb, const int32_t* bedge,
                  const int32_t* btype, const int32_t* bseg) {
   o->nn = nn; o->ne = ne;
@@ -419,12 +439,14 @@ int orc_set_mesh(orc_t* o, int nn, const double* xy, int ne, const int32_t* tri,
   return ned;
 }
 
+/* nodal bathymetry h_b and element Manning coefficients of Eq. SWE */
 int orc_set_fields(orc_t* o, const double* hb, const double* man) {
   memcpy(o->hb, hb, sizeof(double) * o->nn);
   if (man) memcpy(o->man, man, sizeof(double) * o->ne);
   return 0;
 }
 
+/* constant nodal rain rates (Eq. rain) */
 void orc_set_rain_nodal(orc_t* o, const double* r) {
   o->rain_kind = 1;
   free(o->rain_nodal);
@@ -432,6 +454,7 @@ void orc_set_rain_nodal(orc_t* o, const double* r) {
   memcpy(o->rain_nodal, r, sizeof(double) * o->nn);
 }
 
+/* the moving radial rain cell standing in for the parametric rainfall of Sec. 2.5 (whose own profile is not available) */
 void orc_set_rain_parametric(orc_t* o, double x0, double y0, double heading, double speed, double rpeak, double rm,
                              double re, double t0) {
   o->rain_kind = 2;
@@ -439,6 +462,7 @@ void orc_set_rain_parametric(orc_t* o, double x0, double y0, double heading, dou
   memcpy(o->st, v, sizeof v);
 }
 
+/* gridded rainfall records in mm/h, interpolated to the nodes (Sec. 2.5: bilinear in space, linear in time) */
 void orc_set_rain_grid(orc_t* o, int nx, int ny, int nt, double x0, double y0, double dx, double dy, double t0,
                        double dt_rec, const float* mmh) {
   o->rain_kind = 3;
@@ -449,6 +473,7 @@ void orc_set_rain_grid(orc_t* o, int nx, int ny, int nt, double x0, double y0, d
   memcpy(o->grid, mmh, sizeof(float) * (size_t)nx * ny * nt);
 }
 
+/* tidal constituents of the specified-elevation (ocean) boundary segments (Sec. 2.1) */
 void orc_set_tide(orc_t* o, int nseg, const double* amp, const double* per, const double* pha) {
   o->ntide = nseg;
   free(o->tamp); free(o->tper); free(o->tpha);
@@ -460,22 +485,28 @@ void orc_set_tide(orc_t* o, int nseg, const double* amp, const double* per, cons
   memcpy(o->tpha, pha, sizeof(double) * nseg);
 }
 
+/* the Gaussian set-up eta_p whose forcing F = g H grad(eta_p) enters Eq. SWE (a storm-surge set-up forcing) */
 void orc_set_pressure(orc_t* o, double x0, double y0, double sigma, double peak) {
   o->press = 1;
   o->pr[0] = x0; o->pr[1] = y0; o->pr[2] = sigma; o->pr[3] = peak;
 }
 
+/* verification only: the travelling-wave manufactured solution (exact ghost states and its
+ * momentum residual as forcing; the convergence pin of the method's order) */
 void orc_set_exact_wave(orc_t* o, double a, double k, double l, double c, double h0) {
   o->exact = 1;
   o->ex[0] = a; o->ex[1] = k; o->ex[2] = l; o->ex[3] = c; o->ex[4] = h0;
 }
 
+/* verification only: a linear exact field for the ghost states (hand-integral pin of the weak
+ * form, Eq. elem_weak_form) */
 void orc_set_exact_linear(orc_t* o, const double* c9) {
   o->exact = 2;
   memcpy(o->ex, c9, sizeof(double) * 9);
 }
 
 /* ------------------------------------------------------------------- point functions --- */
+/* verification only: the exact field of the manufactured or linear modes at (x, y, t) */
 static void exact_state(const orc_t* o, double x, double y, double t, double w[3]) {
   if (o->exact == 1) { /* zeta = a sin(k(x - ct)) cos(l y), q = (c zeta, 0) */
     double z = o->ex[0] * sin(o->ex[1] * (x - o->ex[3] * t)) * cos(o->ex[2] * y);
@@ -485,7 +516,8 @@ static void exact_state(const orc_t* o, double x, double y, double t, double w[3
   }
 }
 
-/* momentum residual of the travelling-wave manufactured solution on a flat bottom h0 */
+/* verification only: momentum residual of Eq. SWE for the travelling-wave manufactured solution on
+ * a flat bottom h0 (entered as the forcing F) */
 static void exact_forcing(const orc_t* o, double x, double y, double t, double f[2]) {
   f[0] = f[1] = 0.0;
   if (o->exact != 1) return;
@@ -500,6 +532,8 @@ static void exact_forcing(const orc_t* o, double x, double y, double t, double f
   f[1] = o->g * H * zy;
 }
 
+/* rain rate at node n and time t (m/s): constant nodal, moving radial cell (Sec. 2.5)
+ * or gridded records (Sec. 2.5); the element rate is the mean of its nodes (Eq. rain) */
 static double rain_at(const orc_t* o, int n, double t) {
   if (o->rain_kind == 1) return o->rain_nodal[n];
   if (o->rain_kind == 2) {
@@ -534,7 +568,7 @@ static double rain_at(const orc_t* o, int n, double t) {
   return 0.0;
 }
 
-/* river discharge of segment seg at time t (m^2/s into the domain) */
+/* river discharge of segment seg at time t (m^2/s into the domain; Eq. river_bc, linear in time between records) */
 static double river_at(const orc_t* o, int seg, double t) {
   if (seg < 0 || seg >= o->nriv || o->rnt < 1) return 0.0;
   if (o->rnt == 1) return o->rq[seg];
@@ -546,6 +580,7 @@ static double river_at(const orc_t* o, int seg, double t) {
   return (1.0 - a) * o->rq[(size_t)i * o->nriv + seg] + a * o->rq[(size_t)(i + 1) * o->nriv + seg];
 }
 
+/* discharge series of the river boundary segments (Sec. 2.1, Eq. river_bc) */
 void orc_set_river(orc_t* o, int nseg, int nt, double t0, double dt, const double* q) {
   free(o->rq);
   o->rq = NULL;
@@ -559,6 +594,7 @@ void orc_set_river(orc_t* o, int nseg, int nt, double t0, double dt, const doubl
   o->rdt = dt > 0.0 ? dt : 1.0;
 }
 
+/* elevation of ocean segment seg at time t (Sec. 2.1: A sin(2 pi t / T + phase), no ramp) */
 static double tide_at(const orc_t* o, int seg, double t) {
   if (seg < 0 || seg >= o->ntide) return 0.0;
   return o->tamp[seg] * sin(2.0 * M_PI * t / o->tper[seg] + o->tpha[seg]);
@@ -579,6 +615,8 @@ static void phys_flux(const orc_t* o, const double* w, double hb, double nx, dou
   *Hs_out = Hs;
 }
 
+/* the numerical flux Fhat.n of Sec. 2.3 between traces wl and wr along the unit normal n: LLF, or
+ * Roe with Roe averages and no entropy fix, the jump taken in (zeta, q) */
 static void numflux_o(const orc_t* o, int flux, const double* wl, double hbl, const double* wr, double hbr, double nx,
                       double ny, double* f) {
   double FL[3], FR[3], unL, unR, HsL, HsR;
@@ -611,6 +649,7 @@ static void numflux_o(const orc_t* o, int flux, const double* wl, double hbl, co
   f[2] = 0.5 * (FL[2] + FR[2]) - 0.5 * D2;
 }
 
+/* the numerical flux of Sec. 2.3 alone (test hook) */
 void orc_numflux(int flux, double g, double H0, const double* wl, double hbl, const double* wr, double hbr, double nx,
                  double ny, double* f) {
   orc_t tmp;
@@ -619,7 +658,8 @@ void orc_numflux(int flux, double g, double H0, const double* wl, double hbl, co
   numflux_o(&tmp, flux, wl, hbl, wr, hbr, nx, ny, f);
 }
 
-/* reflective wall seen from the inside state w: ghost mirrors q.n; the wall carries no mass */
+/* reflective wall seen from the inside state w (land boundary of Sec. 2.1): ghost
+ * mirrors q.n; the wall carries no mass */
 static void wall_flux(const orc_t* o, const double* w, double hb, double nx, double ny, double* f) {
   double qn = w[1] * nx + w[2] * ny;
   double wr[3] = {w[0], w[1] - 2.0 * qn * nx, w[2] - 2.0 * qn * ny};
@@ -628,6 +668,7 @@ static void wall_flux(const orc_t* o, const double* w, double hb, double nx, dou
 }
 
 /* ---------------------------------------------------------------- right-hand side L_h --- */
+/* the trace of element e's modal state at a point with basis values phi (Eq. dubiner expansion) */
 static void eval_w(const orc_t* o, const double* W, int e, const double* phi, double out[3]) {
   const double* we = W + (size_t)e * 3 * o->np;
   for (int v = 0; v < 3; ++v) {
@@ -637,11 +678,14 @@ static void eval_w(const orc_t* o, const double* W, int e, const double* phi, do
   }
 }
 
+/* a nodal field (bathymetry, coordinates) interpolated linearly at barycentrics l of element e
+ * (continuous piecewise linear h_b) */
 static double interp_nodal(const orc_t* o, const double* f, int e, const double l[3]) {
   const int32_t* v = o->tri + 3 * e;
   return l[0] * f[v[0]] + l[1] * f[v[1]] + l[2] * f[v[2]];
 }
 
+/* unit outward normal and length of local edge j of element e (the n of Sec. 2.3's edge integrals) */
 static void edge_geom(const orc_t* o, int e, int j, double* nx, double* ny, double* len) {
   int a = o->tri[3 * e + j], b = o->tri[3 * e + (j + 1) % 3];
   double tx = o->x[b] - o->x[a], ty = o->y[b] - o->y[a];
@@ -649,8 +693,9 @@ static void edge_geom(const orc_t* o, int e, int j, double* nx, double* ny, doub
   *nx = ty / l; *ny = -tx / l; *len = l;
 }
 
-/* L_h(W) at time t: fills o->Lw = M^{-1} rhs, returns the boundary mass outflow in *bdry_out
- * and the rain volume rate in *rain_out. */
+/* L_h(W) of Eq. RKSSP at time t (Eq. elem_weak_form in the order of Sec. 2.3: edge integrals,
+ * forcing, area integrals; the wet/dry edge closure of Sec. 2.4): fills o->Lw = M^{-1} rhs, returns
+ * the boundary mass outflow in *bdry_out and the rain volume rate in *rain_out. */
 static void compute_L(orc_t* o, const double* W, double t, double* rain_out, double* bdry_out) {
   const int np = o->np, ng = o->ng;
   const double g = o->g;
@@ -797,6 +842,7 @@ static void compute_L(orc_t* o, const double* W, double t, double* rain_out, dou
   *bdry_out = bd_s + bd_c;
 }
 
+/* L_h of Eq. RKSSP (the DG right-hand side of Eq. elem_weak_form after M^-1) on the current state */
 void orc_rhs(orc_t* o, double* L) {
   double r, b;
   compute_L(o, o->w, o->t, &r, &b);
@@ -845,7 +891,8 @@ int orc_positivity_vertex(double H0, const double* H, double* Ho, const double* 
 }
 
 /* rebuild modes 1..2 of one variable from three vertex values (the linear interpolant projected
- * on the orthonormal basis with the exact area rule); mode 0 is left as it is */
+ * on the orthonormal basis with the exact area rule); mode 0 is left as it is (the vertex-value
+ * form of M Pi_h, Sec. 2.4) */
 static void set_linear_part(int p, double* we, const double f[3]) {
   double l[NQMAX][3], qw[NQMAX];
   int nq = area_rule_bary(p < 1 ? 1 : p, l, qw);
@@ -861,7 +908,8 @@ static void set_linear_part(int p, double* we, const double f[3]) {
   }
 }
 
-/* M Pi_h on one element's modes we[3][np] (zeta, qx, qy) with nodal bathymetry hbv at its
+/* M Pi_h of Sec. 2.4 (as read at the top of this file) on one element's modes we[3][np] (zeta, qx, qy) with nodal
+ * bathymetry hbv at its
  * vertices and phv the basis at the vertices; returns 1 if the element is dry */
 static int element_positivity(int p, const double phv[3][NPMAX], double H0, const double hbv[3], double* we) {
   const int np = (p + 1) * (p + 2) / 2;
@@ -910,12 +958,14 @@ static int element_positivity(int p, const double phv[3][NPMAX], double H0, cons
  * not sum to zero, scale the positive and negative parts to balance; rebuild the linear part
  * from the midpoint deviations.  Means are untouched.  Limited: wet elements with three
  * neighbours whose edges all have a valid pair; others are left as they are. */
+/* switches the optional limiter of Sec. 2.3 (the Cockburn-Shu form below) on or off, with its weight and constant */
 void orc_set_limiter(orc_t* o, int on, double nu, double M) {
   o->lim_on = on;
   o->lim_nu = nu;
   o->lim_M = M;
 }
 
+/* neighbour across each local edge, for the limiter's barycentric pairs (Sec. 2.3's optional limiter) */
 static void build_nb3(orc_t* o) {
   o->nb3 = (int*)malloc(sizeof(int) * 3 * (size_t)o->ne);
   for (int k = 0; k < 3 * o->ne; ++k) o->nb3[k] = -1;
@@ -927,12 +977,14 @@ static void build_nb3(orc_t* o) {
   }
 }
 
+/* minmod of two values (Sec. 2.3's optional limiter) */
 static double minmod2(double a, double b) {
   if (a > 0.0 && b > 0.0) return a < b ? a : b;
   if (a < 0.0 && b < 0.0) return a > b ? a : b;
   return 0.0;
 }
 
+/* the optional slope limiter of Sec. 2.3 on state W, in place (the Cockburn-Shu form described above) */
 static void limiter(orc_t* o, double* W) {
   if (!o->lim_on || o->p != 1) return;
   if (!o->nb3) build_nb3(o);
@@ -1018,8 +1070,10 @@ static void limiter(orc_t* o, double* W) {
 }
 
 static void positivity(orc_t* o, double* W);
+/* the limiter alone on the current state (test hook of Sec. 2.3's optional limiter) */
 void orc_apply_limiter(orc_t* o) { limiter(o, o->w); }
 
+/* M Pi_h of Sec. 2.4 on every element of W, setting the element dry flags */
 static void positivity(orc_t* o, double* W) {
   for (int e = 0; e < o->ne; ++e) {
     const int32_t* vt = o->tri + 3 * e;
@@ -1028,6 +1082,7 @@ static void positivity(orc_t* o, double* W) {
   }
 }
 
+/* M Pi_h of Sec. 2.4 on one element's modes (test hook) */
 int orc_positivity_modal(int p, double H0, const double* hbv, double* w) {
   if (p < 0 || p > 2) return -1;
   double phv[3][NPMAX];
@@ -1041,6 +1096,8 @@ int orc_positivity_modal(int p, double H0, const double* hbv, double* w) {
 }
 
 /* ------------------------------------------------------------------- state and time --- */
+/* water volume of the mass balance of Eq. SWE: sum_e A_e mean(zeta_e), or of the depth with_hb
+ * (the volume above the bed), compensated */
 static double ledger_V(const orc_t* o, const double* W, int with_hb) {
   double s = 0.0, c = 0.0;
   for (int e = 0; e < o->ne; ++e) {
@@ -1054,6 +1111,7 @@ static double ledger_V(const orc_t* o, const double* W, int with_hb) {
   return s + c;
 }
 
+/* after a new state: M Pi_h (Sec. 2.4) defines the dry flags; the ledger's V0, VH0 and sums restart */
 static void reset_ledger(orc_t* o) {
   positivity(o, o->w);
   o->V0 = ledger_V(o, o->w, 0);
@@ -1062,6 +1120,8 @@ static void reset_ledger(orc_t* o) {
   o->nstep = 0;
 }
 
+/* the initial state (zeta, q) of Eq. SWE from nodal values, L2-projected on the basis of
+ * Eq. dubiner (exact for the linear interpolant at p >= 1) */
 int orc_set_state_nodal(orc_t* o, const double* zeta, const double* qx, const double* qy) {
   const double* f[3] = {zeta, qx, qy};
   for (int e = 0; e < o->ne; ++e) {
@@ -1080,14 +1140,17 @@ int orc_set_state_nodal(orc_t* o, const double* zeta, const double* qx, const do
   return 0;
 }
 
+/* the state (zeta, q) of Eq. SWE as modal coefficients (Eq. dubiner) */
 int orc_set_state_modal(orc_t* o, const double* w) {
   memcpy(o->w, w, sizeof(double) * (size_t)o->ne * 3 * o->np);
   reset_ledger(o);
   return 0;
 }
 
+/* the modal state (zeta, q) of Eq. SWE (Eq. dubiner coefficients) */
 void orc_get_state(const orc_t* o, double* w) { memcpy(w, o->w, sizeof(double) * (size_t)o->ne * 3 * o->np); }
 
+/* the state at the three vertices of every element (the values M Pi_h of Sec. 2.4 acts on) */
 void orc_get_vertex_values(const orc_t* o, double* out) {
   for (int e = 0; e < o->ne; ++e)
     for (int v = 0; v < 3; ++v)
@@ -1098,8 +1161,11 @@ void orc_get_vertex_values(const orc_t* o, double* out) {
       }
 }
 
+/* the element dry flags of Sec. 2.4 (dry when any vertex is dry) */
 void orc_get_dry(const orc_t* o, uint8_t* dry) { memcpy(dry, o->dry, o->ne); }
 
+/* the fixed time step of the runs (Sec. 3 uses a fixed dt) from the CFL condition at the current
+ * state: cfl min_e 2 r_in / ((2p+1) max_vertices(|u| + sqrt(g Hs))) */
 double orc_cfl_dt(const orc_t* o, double cfl) {
   double best = 1e300;
   for (int e = 0; e < o->ne; ++e) {
@@ -1125,9 +1191,14 @@ double orc_cfl_dt(const orc_t* o, double cfl) {
   return best;
 }
 
+/* time step and time of the SSP scheme (Eq. RKSSP) */
 void orc_set_dt(orc_t* o, double dt) { o->dt = dt; }
+/* the current time t of Eq. RKSSP (forcing and tide are evaluated at stage times) */
 void orc_set_time(orc_t* o, double t) { o->t = t; }
 
+/* n steps of the Shu-Osher SSP scheme of Eq. RKSSP: per stage L_h (Eq. elem_weak_form) at the
+ * stage time, the combination, then M Pi_h (Sec. 2.4, after every stage) and the
+ * optional limiter; rain and boundary volumes booked with the stage's final weight */
 void orc_step(orc_t* o, long n) {
   size_t nw = (size_t)o->ne * 3 * o->np;
   for (long it = 0; it < n; ++it) {
@@ -1156,6 +1227,8 @@ void orc_step(orc_t* o, long n) {
   }
 }
 
+/* the mass ledger: t, V0, V, rain in, boundary in, VH0, the relative balance error |V - V0 - rain - bdry| / VH0
+ * (Eq. SWE's mass equation integrated over domain and time) and the wet fraction */
 void orc_get_ledger(const orc_t* o, double* out) {
   double V = ledger_V(o, o->w, 0);
   double rain = o->rain_s + o->rain_c, bd = o->bd_s + o->bd_c;
@@ -1166,6 +1239,8 @@ void orc_get_ledger(const orc_t* o, double* out) {
   out[7] = (double)wet / o->ne;
 }
 
+/* verification only: L2 error of variable var against the manufactured solution (the method's
+ * order p + 1) */
 double orc_l2_error_exact(const orc_t* o, int var) {
   double s = 0.0;
   for (int e = 0; e < o->ne; ++e)
@@ -1179,7 +1254,7 @@ double orc_l2_error_exact(const orc_t* o, int var) {
   return sqrt(s);
 }
 
-/* amplification factor of the stepper's Shu-Osher table on y' = lambda y, z = lambda dt */
+/* amplification factor of the stepper's Shu-Osher table (Eq. RKSSP) on y' = lambda y, z = lambda dt */
 double orc_ssp_amplification(int stages, double z) {
   orc_t* o = orc_create(1, 0, stages, 9.81, 0.01, 2, 0.0);
   double y[6] = {1.0, 0, 0, 0, 0, 0};
